@@ -1,0 +1,24 @@
+"""FP64 CPU oracle for the batched Lax / PDHG Hamilton-Jacobi solver.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path imports, calls or links
+anything in this directory: only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use it.  It shares no code with the CUDA path;
+the only thing both sides read is ``paper_1803_01215_gb300.workloads`` (seeded
+input draws, no arithmetic of the method).
+
+Contents
+  counter_rng  splitmix64 used as a counter-based generator for the random
+               initial guess (Section 6: x^0 within 0.1 of the target in the
+               max-norm, p^0 within 0.1 of zero).
+  families     the Hamiltonians H(x, p), their p-proximal maps, gradients and
+               the quadratic terminal cost g (Section 2, H = max_u{<f,p> - L}).
+  lax_pdhg     Algorithm 1 (Lax formula, backward Euler) with the concrete
+               updates of Section 5.3 and the loop of Appendix Algorithm A.1,
+               and the value fval of Eq. (disclaxBE).
+
+Pins: see tests/test_oracle_pins.py.  Closed form (quadratic H), discrete
+Riccati (linear drift), direct collocation (tanh drift), the discrete
+characteristic (KKT) equations with complex-step derivatives of an H written
+independently from the quadcopter dynamics, the primal/dual value identity, and
+brute-force search for tiny cases.
+"""

@@ -1,0 +1,201 @@
+"""Hamiltonians and terminal cost for the oracle (FP64, numpy, batched).
+
+The paper's convention (Section 2): the control problem runs backwards in
+time, x'(s) = f(x, u, s), x(t) = x_target, cost g(x(0)) + int L, so that
+H(x, p) = max_u { <f(x, u), p> - L(x, u) } and phi_t + H(x, grad phi) = 0,
+phi(x, 0) = g(x).  All three families below have L = |u|^2 / 2 and
+control-affine dynamics f = f0(x) + B(x) u, so H = <p, f0> + |B^T p|^2 / 2.
+
+Every array argument has the coordinate axis last: x, p have shape [..., d].
+prox_p(x, v, lam) returns argmin_p { lam * H(x, p) + |p - v|^2 / 2 }, the
+dual proximal map of Algorithm 1 with lam = sigma * delta.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+"""
+import numpy as np
+
+
+class Quadratic:
+    """H(x, p) = |p|^2 / 2  (f = u, L = |u|^2/2): the closed-form case."""
+
+    def __init__(self, d):
+        self.d = d
+
+    def H(self, x, p):
+        return 0.5 * np.sum(p * p, axis=-1)
+
+    def grad_p(self, x, p):
+        return p.copy()
+
+    def grad_x(self, x, p):
+        return np.zeros_like(p)
+
+    def prox_p(self, x, v, lam):
+        # lam * p + (p - v) = 0
+        return v / (1.0 + lam[..., None])
+
+
+class TanhDrift:
+    """H(x, p) = <p, tanh(A x)> + |p|^2 / 2  (f = tanh(Ax) + u, L = |u|^2/2).
+
+    `activation="identity"` gives the linear drift f = Ax + u used by the
+    discrete Riccati pin; the tanh form is the high-dimensional workload.
+    """
+
+    def __init__(self, A, activation="tanh"):
+        self.A = np.asarray(A, dtype=np.float64)
+        self.d = self.A.shape[0]
+        self.activation = activation
+
+    def _act(self, x):
+        y = x @ self.A.T                      # (A x)_i = sum_k A_ik x_k
+        if self.activation == "identity":
+            return y, np.ones_like(y)
+        a = np.tanh(y)
+        return a, 1.0 - a * a                 # value and derivative of tanh
+
+    def H(self, x, p):
+        a, _ = self._act(x)
+        return np.sum(p * a, axis=-1) + 0.5 * np.sum(p * p, axis=-1)
+
+    def grad_p(self, x, p):
+        a, _ = self._act(x)
+        return a + p
+
+    def grad_x(self, x, p):
+        _, da = self._act(x)
+        return (da * p) @ self.A              # A^T (tanh'(Ax) * p)
+
+    def prox_p(self, x, v, lam):
+        # lam * (a + p) + (p - v) = 0
+        a, _ = self._act(x)
+        lam = lam[..., None]
+        return (v - lam * a) / (1.0 + lam)
+
+
+class Quadcopter:
+    """12-D quadcopter (Section 6.4 dynamics, thrust measured from hover).
+
+    H(x, p) = <p, f0(x)> + |B(x)^T p|^2 / 2 + eps |p|^2 / 2.
+    The last term is an additive full-state disturbance input w with cost
+    |w|^2 / (2 eps).  With eps = 0, B has rank 4 in R^12 and H is not bounded
+    below in p, which Section 5.1.1 names as the case where the Lax form does
+    not converge; eps > 0 makes H strongly convex in p.
+
+    State order follows the paper: (x, y, z, psi, theta, phi) positions and
+    Euler angles, then their rates.  With thrust m*a_h + u (a_h = hover gain)
+    and torques tau_psi, tau_theta, tau_phi as the four controls:
+        f0(x) = (v_pos, v_ang, a_h * a(psi, theta, phi) - g_z e3, 0)
+        B(x)  = [ (0_6; a/m; 0_3) | e_10 | e_11 | e_12 ]            (12 x 4)
+    with the thrust direction
+        a = ( s_phi s_psi + c_phi c_psi s_theta,
+             -c_psi s_phi + c_phi s_theta s_psi,
+              c_theta c_phi ).
+    """
+
+    def __init__(self, m, a_h, g_z, eps):
+        self.m, self.a_h, self.g_z = float(m), float(a_h), float(g_z)
+        self.eps = float(eps)
+        self.d = 12
+
+    @staticmethod
+    def thrust_dir(x):
+        psi, th, ph = x[..., 3], x[..., 4], x[..., 5]
+        sps, cps = np.sin(psi), np.cos(psi)
+        sth, cth = np.sin(th), np.cos(th)
+        sph, cph = np.sin(ph), np.cos(ph)
+        a = np.stack([sph * sps + cph * cps * sth,
+                      -cps * sph + cph * sth * sps,
+                      cth * cph], axis=-1)
+        # J[..., r, c] = d a_r / d (psi, theta, phi)_c
+        J = np.empty(x.shape[:-1] + (3, 3))
+        J[..., 0, 0] = sph * cps - cph * sps * sth
+        J[..., 0, 1] = cph * cps * cth
+        J[..., 0, 2] = cph * sps - sph * cps * sth
+        J[..., 1, 0] = sps * sph + cph * sth * cps
+        J[..., 1, 1] = cph * cth * sps
+        J[..., 1, 2] = -cps * cph - sph * sth * sps
+        J[..., 2, 0] = 0.0
+        J[..., 2, 1] = -sth * cph
+        J[..., 2, 2] = -cth * sph
+        return a, J
+
+    def f0(self, x):
+        a, _ = self.thrust_dir(x)
+        out = np.zeros_like(x)
+        out[..., 0:3] = x[..., 6:9]
+        out[..., 3:6] = x[..., 9:12]
+        out[..., 6:9] = self.a_h * a
+        out[..., 8] -= self.g_z
+        return out
+
+    def Bmat(self, x):
+        a, _ = self.thrust_dir(x)
+        Bm = np.zeros(x.shape[:-1] + (12, 4))
+        Bm[..., 6:9, 0] = a / self.m
+        Bm[..., 9, 1] = 1.0
+        Bm[..., 10, 2] = 1.0
+        Bm[..., 11, 3] = 1.0
+        return Bm
+
+    def H(self, x, p):
+        u = np.einsum("...ik,...i->...k", self.Bmat(x), p)
+        return (np.sum(p * self.f0(x), axis=-1) + 0.5 * np.sum(u * u, axis=-1)
+                + 0.5 * self.eps * np.sum(p * p, axis=-1))
+
+    def grad_p(self, x, p):
+        Bm = self.Bmat(x)
+        u = np.einsum("...ik,...i->...k", Bm, p)
+        return self.f0(x) + np.einsum("...ik,...k->...i", Bm, u) + self.eps * p
+
+    def grad_x(self, x, p):
+        a, J = self.thrust_dir(x)
+        q = p[..., 6:9]
+        u0 = np.sum(a * q, axis=-1) / self.m              # thrust control B_0 . p
+        g = np.zeros_like(p)
+        # d/d(angles) of  a_h <a, q>  +  (<a, q>/m)^2 / 2
+        g[..., 3:6] = (self.a_h + u0 / self.m)[..., None] \
+            * np.einsum("...rc,...r->...c", J, q)
+        g[..., 6:9] = p[..., 0:3]                          # d/dv_pos of <p_pos, v_pos>
+        g[..., 9:12] = p[..., 3:6]                         # d/dv_ang of <p_ang, v_ang>
+        return g
+
+    def prox_p(self, x, v, lam):
+        # lam (f0 + B B^T p + eps p) + (p - v) = 0
+        #   ->  ((1 + lam eps) I + lam B B^T) p = v - lam f0
+        Bm = self.Bmat(x)
+        lam = lam[..., None]
+        M = (1.0 + lam[..., None] * self.eps) * np.eye(12) \
+            + lam[..., None] * np.einsum("...ik,...jk->...ij", Bm, Bm)
+        rhs = v - lam * self.f0(x)
+        return np.linalg.solve(M, rhs[..., None])[..., 0]
+
+
+class QuadCost:
+    """g(x) = 1/2 sum_i W_i^2 (x_i - c_i)^2 (terminal / initial cost)."""
+
+    def __init__(self, W, c):
+        self.w2 = np.asarray(W, dtype=np.float64) ** 2
+        self.c = np.asarray(c, dtype=np.float64)
+
+    def g(self, x):
+        return 0.5 * np.sum(self.w2 * (x - self.c) ** 2, axis=-1)
+
+    def grad(self, x):
+        return self.w2 * (x - self.c)
+
+    def prox(self, v, tau):
+        # argmin_x tau*g(x) + |x - v|^2/2  ->  tau w2 (x - c) + x - v = 0
+        return (v + tau * self.w2 * self.c) / (1.0 + tau * self.w2)
+
+
+def make_family(w, activation="tanh"):
+    """Oracle Hamiltonian for a workload dict (see workloads.py)."""
+    fam, d, dyn = w["family"], w["d"], np.asarray(w["dyn"], dtype=np.float64)
+    if fam == "quadratic":
+        return Quadratic(d)
+    if fam == "tanh_drift":
+        return TanhDrift(dyn.reshape(d, d), activation=activation)
+    if fam == "quadcopter":
+        return Quadcopter(*dyn[:4])
+    raise ValueError(fam)

@@ -1,0 +1,100 @@
+"""Seeded synthetic workloads for the batched Lax/PDHG Hamilton-Jacobi solver.
+
+This module only draws numbers: problem parameters and query points shaped
+like the paper's examples (Section 6: quadcopter-class 12-D control, Eq. for
+the eikonal dimension-scaling study, the quadratic closed-form case).  It
+holds none of the method's arithmetic, so both the CUDA path and the FP64
+oracle may take their inputs from here.  It imports nothing else from this
+package.
+
+Every workload is a plain dict:
+
+    family      "quadratic" | "quadcopter" | "tanh_drift"
+    d           state dimension
+    dyn         dynamics parameters (float64 ndarray)
+                  quadratic : empty
+                  quadcopter: [m, a_h, g_z, eps]  (mass, hover thrust gain,
+                              gravity, weight of the full-state disturbance input)
+                  tanh_drift: A, d*d row-major
+    W, c        terminal cost g(x) = 1/2 sum_i W_i^2 (x_i - c_i)^2
+    xq          [B, d] float64 query points
+    t           [B] float64 horizons
+    N           int (uniform) or [B] int32 (ragged) number of time steps
+    sigma, tau  PDHG step sizes (tau * sigma * 4 < 1, the bound ||D||^2 < 4)
+    tol, max_iter, check_every, seed, init_radius
+"""
+import numpy as np
+
+FAMILIES = {"quadratic": 0, "quadcopter": 1, "tanh_drift": 2}
+
+# Quadcopter constants: unit mass, hover thrust gain equal to gravity so that
+# the level-attitude state is an equilibrium of the drift.
+QC_MASS = 1.0
+QC_GRAVITY = 9.81
+QC_HOVER = 9.81
+# H gains eps |p|^2 / 2 (disturbance input with cost |w|^2 / (2 eps)); with the
+# rank-4 thrust/torque input alone the Lax saddle problem does not converge.
+QC_EPS = 1.0
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def quadratic_closed_form(B=64, seed=1):
+    """H = |p|^2/2, g = |x|^2/2, d = 2, x ~ U[-2,2]^2, t = 1, N = 20."""
+    r = _rng(seed)
+    d = 2
+    return dict(family="quadratic", d=d, dyn=np.zeros(0),
+                W=np.ones(d), c=np.zeros(d),
+                xq=r.uniform(-2.0, 2.0, size=(B, d)), t=np.ones(B), N=20,
+                sigma=0.5, tau=0.48, tol=1e-8, max_iter=2000, check_every=1,
+                seed=seed, init_radius=0.1)
+
+
+def quadcopter(B=4096, seed=2, N=64, t=1.0):
+    """12-D quadcopter-class control, x ~ N(0, 0.5^2 I), W = diag U[0.5, 2], x* = 0."""
+    r = _rng(seed)
+    d = 12
+    W = r.uniform(0.5, 2.0, size=d)
+    xq = 0.5 * r.standard_normal((B, d))
+    return dict(family="quadcopter", d=d,
+                dyn=np.array([QC_MASS, QC_HOVER, QC_GRAVITY, QC_EPS]),
+                W=W, c=np.zeros(d), xq=xq, t=np.full(B, float(t)), N=N,
+                sigma=QC_SIGMA, tau=0.24 / QC_SIGMA, tol=1e-8, max_iter=20000,
+                check_every=16, seed=seed, init_radius=0.1)
+
+
+def tanh_drift(d, B=16384, seed=3, N=32):
+    """H = <p, tanh(Ax)> + |p|^2/2, A ~ N(0,1)/sqrt(d), g = |x - c|^2/2, c ~ N(0, I),
+    x ~ N(0, I), t ~ U[0.5, 2]."""
+    r = _rng(seed)
+    A = r.standard_normal((d, d)) / np.sqrt(d)
+    c = r.standard_normal(d)
+    xq = r.standard_normal((B, d))
+    t = r.uniform(0.5, 2.0, size=B)
+    return dict(family="tanh_drift", d=d, dyn=A.reshape(-1).copy(),
+                W=np.ones(d), c=c, xq=xq, t=t, N=N,
+                sigma=TD_SIGMA, tau=0.24 / TD_SIGMA, tol=1e-8, max_iter=20000,
+                check_every=16, seed=seed, init_radius=0.1)
+
+
+# Step sizes chosen on the oracle (sigma sweep at tau = 0.24 / sigma); the fixed
+# point does not depend on them, only the iteration count does.
+QC_SIGMA = 1.0
+TD_SIGMA = 1.0
+
+
+def subset(w, idx):
+    """The same workload restricted to the points `idx` (global point indices
+    are kept in 'point_index' so the counter-based initial guess is unchanged)."""
+    idx = np.asarray(idx)
+    out = dict(w)
+    out["xq"] = w["xq"][idx]
+    out["t"] = w["t"][idx]
+    if not np.isscalar(w["N"]):
+        out["N"] = np.asarray(w["N"])[idx]
+    base = w.get("point_index")
+    out["point_index"] = (np.asarray(base)[idx] if base is not None
+                          else idx.astype(np.int64))
+    return out
