@@ -1,0 +1,296 @@
+"""Benchmark: converged Hamilton-Jacobi solves per second on the 12-D quadcopter
+workload (4096 query points, N = 64, t = 1), FP32 iterations with FP64
+residual/value, next to the all-FP64 GPU path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one hj_solve_batch call over the whole batch (initial guess, the
+PDHG iterations to convergence, the FP64 value, trajectories written to HBM).
+A solve counts when its status is CONVERGED and |V - V_fp64| <= 1e-4 max(1, |V_fp64|),
+V_fp64 from the all-FP64 GPU path on the same inputs (computed once, untimed).
+Between timed steps a 512 MB buffer is written to flush L2.  Under torchrun
+every rank solves its own 4096 points (point_offset = rank * 4096): weak scaling.
+
+`--impl reference` times the FP64 CPU oracle (the reference arm) on a bounded
+sample of the same workload and prints the same JSON line with "impl": "reference".
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1803_01215_gb300 import workloads as W  # noqa: E402
+
+METRIC = "converged HJ solves/sec (V at 1e-4 rel vs FP64) and % FP32 peak, FP32 vs FP64 GPU"
+UNIT = "solves/s"
+# FP32 flops of one (node, iteration) of the quadcopter update (FMA = 2): the
+# dual prox with its Sherman-Morrison solve, the thrust direction and Jacobian
+# from the three sin/cos pairs, the x-gradient, the x step and the relaxation.
+# sin/cos are transcendental and not counted.  Derivation in the design doc.
+QC_FLOPS_PER_NODE_ITER = 240
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def workload_config():
+    return W.quadcopter()
+
+
+def _clock_sampler(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "100"], stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except (FileNotFoundError, OSError):
+        return None
+
+
+def _clock_summary(path, gpu_index):
+    sm, mx, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+    except OSError:
+        pass
+    if not sm:
+        return None
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def run_cpu_oracle(w, n_points, budget_s=20.0):
+    """Time the FP64 oracle (same stopping rule) on the first points of the
+    workload, growing the sample until about budget_s of CPU work."""
+    from oracle import lax_pdhg as O
+    n, total_t, total_pts = max(1, n_points), 0.0, 0
+    start = 0
+    while total_t < budget_s and start < len(w["xq"]):
+        idx = np.arange(start, min(start + n, len(w["xq"])))
+        t0 = time.perf_counter()
+        res = O.solve(W.subset(w, idx))
+        total_t += time.perf_counter() - t0
+        total_pts += int(np.sum(res["status"] == O.CONVERGED))
+        start += len(idx)
+    return total_pts / total_t, total_pts, total_t
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload_config()
+    for _ in range(args.warmup):
+        run_cpu_oracle(w, 8, budget_s=0.0)
+    vals = []
+    pts = 0
+    tt = 0.0
+    for _ in range(args.steps):
+        v, n, t = run_cpu_oracle(w, 16, budget_s=10.0)
+        vals.append(v); pts += n; tt += t
+    value = pts / tt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "quadcopter12d_B4096_N64_t1", "global_batch": 4096,
+                       "N": 64, "d": 12},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{pts} points of the 4096-point workload over "
+                                       f"{args.steps} steps, same stopping rule (tol 1e-8)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1803_01215_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = workload_config()
+    B, N, d = len(w["xq"]), int(w["N"]), w["d"]
+    prob = binding.Problem.from_workload(w)
+    base = dict(sigma=w["sigma"], tau=w["tau"], tol=w["tol"], max_iter=w["max_iter"],
+                check_every=w["check_every"], seed=w["seed"], init_radius=w["init_radius"],
+                point_offset=rank * B)
+    o32 = binding.make_opts(precision="fp32", **base)
+    o64 = binding.make_opts(precision="fp64", **base)
+    xq = torch.as_tensor(w["xq"], device=dev)
+    t = torch.as_tensor(w["t"], device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out32 = dict(V=torch.empty(B, dtype=torch.float64, device=dev),
+                 iters=torch.empty(B, dtype=torch.int32, device=dev),
+                 status=torch.empty(B, dtype=torch.int8, device=dev),
+                 traj_x=torch.empty(B, N + 1, d, dtype=torch.float32, device=dev),
+                 traj_p=torch.empty(B, N + 1, d, dtype=torch.float32, device=dev))
+    out64 = dict(V=torch.empty(B, dtype=torch.float64, device=dev),
+                 iters=torch.empty(B, dtype=torch.int32, device=dev),
+                 status=torch.empty(B, dtype=torch.int8, device=dev),
+                 traj_x=torch.empty(B, N + 1, d, dtype=torch.float64, device=dev),
+                 traj_p=torch.empty(B, N + 1, d, dtype=torch.float64, device=dev))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(opts, out):
+        binding.solve_batch(prob, xq, t, N, opts, out=out, stream=stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # accuracy reference: the all-FP64 GPU path (untimed)
+    step(o64, out64)
+    torch.cuda.synchronize()
+    V64 = out64["V"].clone()
+    st64 = out64["status"].clone()
+
+    def timed(opts, out, steps, warmup):
+        for _ in range(warmup):
+            step(opts, out)
+        barrier()
+        ms = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(opts, out)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        barrier()
+        return ms / steps
+
+    clocks_path = os.path.join(tempfile.gettempdir(), f"hj_clocks_{os.getpid()}.csv")
+    sampler = _clock_sampler(clocks_path)
+    ms32 = timed(o32, out32, args.steps, args.warmup)
+    if sampler is not None:
+        sampler.terminate()
+        sampler.wait()
+    ms64 = timed(o64, out64, args.fp64_steps, 1)
+
+    ok32 = ((out32["status"] == 0) & (st64 == 0) &
+            ((out32["V"] - V64).abs() <= 1e-4 * V64.abs().clamp_min(1.0)))
+    n_ok32 = int(ok32.sum().item())
+    n_ok64 = int((out64["status"] == 0).sum().item())
+    iters_sum = int(out32["iters"].to(torch.int64).sum().item())
+
+    # e2e through the public API: pinned host inputs -> device -> solve -> host V/status
+    xq_h = torch.as_tensor(w["xq"]).pin_memory()
+    t_h = torch.as_tensor(w["t"]).pin_memory()
+    V_h = torch.empty(B, dtype=torch.float64).pin_memory()
+    st_h = torch.empty(B, dtype=torch.int8).pin_memory()
+    xq_d = torch.empty_like(xq)
+    t_d = torch.empty_like(t)
+    e2e_ms = 0.0
+    for k in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xq_d.copy_(xq_h, non_blocking=True)
+        t_d.copy_(t_h, non_blocking=True)
+        binding.solve_batch(prob, xq_d, t_d, N, o32, out=out32, stream=stream)
+        V_h.copy_(out32["V"], non_blocking=True)
+        st_h.copy_(out32["status"], non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            e2e_ms += e0.elapsed_time(e1)
+    e2e_ms /= args.steps
+
+    # max over ranks of the per-step time; total solves over ranks
+    tens = torch.tensor([ms32, ms64, e2e_ms], dtype=torch.float64, device=dev)
+    cnt = torch.tensor([n_ok32, n_ok64, iters_sum], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tens, op=dist.ReduceOp.MAX)
+        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
+    ms32, ms64, e2e_ms = [float(v) for v in tens.tolist()]
+    n_ok32, n_ok64, iters_sum = [float(v) for v in cnt.tolist()]
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    value = n_ok32 / (ms32 * 1e-3)
+    value64 = n_ok64 / (ms64 * 1e-3)
+    flops = iters_sum / world * N * QC_FLOPS_PER_NODE_ITER           # per launch, per rank
+    achieved_tflops = flops / (ms32 * 1e-3) / 1e12
+    clocks = _clock_summary(clocks_path, local)
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "quadcopter12d_B4096_N64_t1", "global_batch": B * world,
+                   "N": N, "d": d, "precision": "fp32 iterates, fp64 residual/value",
+                   "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas{world}", "sigma": w["sigma"], "tau": w["tau"],
+                   "tol": w["tol"], "check_every": w["check_every"]},
+        "fp64_gpu": {"value": value64, "unit": UNIT, "ms_per_step": ms64,
+                     "converged": n_ok64},
+        "fp32_over_fp64": value / value64 if value64 > 0 else None,
+        "converged_accurate": n_ok32, "mean_iters": iters_sum / (B * world),
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / peak, "traffic": None,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)"},
+        "gpu_launches": args.steps,
+        "e2e": {"value": n_ok32 / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(xq_h.numel() * 8 + t_h.numel() * 8),
+                "d2h_bytes_per_step": int(V_h.numel() * 8 + st_h.numel())},
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        v, n, tsec = run_cpu_oracle(w, 16, budget_s=15.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {n} points of the workload, same stopping "
+                                          f"rule, {tsec:.1f} s of CPU time"}
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,157 @@
+"""ctypes binding of libhjpdhg.so (include/hjpdhg.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module turns
+torch tensors into pointers and status codes into exceptions.  If the library
+is not built, loading fails loudly: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build_lib
+from .workloads import FAMILIES
+
+HJ_OK, HJ_ERR_INVALID_ARG, HJ_ERR_UNSUPPORTED, HJ_ERR_STEP_SIZE, HJ_ERR_CUDA, HJ_ERR_OOM = range(6)
+PREC = {"fp32": 0, "fp64": 1}
+POINT_CONVERGED, POINT_MAX_ITER, POINT_NONFINITE = 0, 1, 2
+
+
+class HJError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {_lib().hj_status_str(code).decode()} (status {code})")
+        self.code = code
+
+
+class SolverOpts(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("tau", ctypes.c_double),
+                ("theta", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("inner_steps", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("init_radius", ctypes.c_double),
+                ("point_offset", ctypes.c_int64)]
+
+
+_LIB = None
+EXPORTED = ("hj_problem_create", "hj_problem_destroy", "hj_solve_batch",
+            "hj_status_str", "hj_version")
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = build_lib.lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "`python -m paper_1803_01215_gb300.build_lib` (no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+        lib.hj_problem_create.argtypes = [ctypes.POINTER(P), I32, I32, D, I64, D, D]
+        lib.hj_problem_destroy.argtypes = [P]
+        lib.hj_solve_batch.argtypes = [P, I64, P, P, I32, ctypes.POINTER(SolverOpts),
+                                       P, P, P, P, P, P, P, P]
+        lib.hj_status_str.restype = ctypes.c_char_p
+        lib.hj_status_str.argtypes = [ctypes.c_int]
+        lib.hj_version.restype = ctypes.c_int32
+        for name in ("hj_problem_create", "hj_problem_destroy", "hj_solve_batch"):
+            getattr(lib, name).restype = ctypes.c_int
+        _LIB = lib
+    return _LIB
+
+
+def _dptr(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Problem:
+    """A Hamiltonian family plus terminal cost g = 1/2 sum W^2 (x - c)^2, on the
+    current CUDA device (hj_problem_create)."""
+
+    def __init__(self, family, d, dyn, W, c):
+        self.family = FAMILIES[family] if isinstance(family, str) else int(family)
+        self.d = int(d)
+        dyn_a, dyn_p = _dptr(dyn if dyn is not None else [])
+        w_a, w_p = _dptr(W)
+        c_a, c_p = _dptr(c)
+        h = ctypes.c_void_p()
+        r = _lib().hj_problem_create(ctypes.byref(h), self.family, self.d,
+                                     dyn_p if dyn_a.size else None, dyn_a.size, w_p, c_p)
+        if r != HJ_OK:
+            raise HJError(r, "hj_problem_create")
+        self.handle = h
+
+    @classmethod
+    def from_workload(cls, w):
+        return cls(w["family"], w["d"], w["dyn"], w["W"], w["c"])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib().hj_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def make_opts(*, sigma, tau, theta=1.0, tol=1e-8, max_iter=20000, check_every=16,
+              inner_steps=1, precision="fp32", seed=0, init_radius=0.1, point_offset=0):
+    return SolverOpts(float(sigma), float(tau), float(theta), float(tol), int(max_iter),
+                      int(check_every), int(inner_steps), PREC[precision], int(seed),
+                      float(init_radius), int(point_offset))
+
+
+def solve_batch(problem, xq, t, N, opts, *, return_traj=False, warm_x=None, warm_p=None,
+                out=None, stream=None):
+    """hj_solve_batch on device tensors.  xq [B, d] float64 cuda, t [B] float64 cuda.
+    Returns dict(V, iters, status[, traj_x, traj_p]) of device tensors."""
+    if not (xq.is_cuda and t.is_cuda):
+        raise ValueError("xq and t must be CUDA tensors")
+    xq = xq.contiguous()
+    t = t.contiguous()
+    if xq.dtype != torch.float64 or t.dtype != torch.float64:
+        raise ValueError("xq and t must be float64")
+    B, d = xq.shape
+    dev = xq.device
+    it_dtype = torch.float32 if opts.precision == 0 else torch.float64
+    if out is None:
+        out = dict(V=torch.empty(B, dtype=torch.float64, device=dev),
+                   iters=torch.empty(B, dtype=torch.int32, device=dev),
+                   status=torch.empty(B, dtype=torch.int8, device=dev))
+        if return_traj:
+            out["traj_x"] = torch.empty(B, N + 1, d, dtype=it_dtype, device=dev)
+            out["traj_p"] = torch.empty(B, N + 1, d, dtype=it_dtype, device=dev)
+    for key in ("warm_x", "warm_p"):
+        w = warm_x if key == "warm_x" else warm_p
+        if w is not None and (w.dtype != it_dtype or tuple(w.shape) != (B, N + 1, d)
+                              or not w.is_contiguous()):
+            raise ValueError(f"{key} must be a contiguous [B, N+1, d] {it_dtype} tensor")
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    r = _lib().hj_solve_batch(problem.handle, B, _ptr(xq), _ptr(t), int(N), ctypes.byref(opts),
+                              _ptr(out["V"]), _ptr(out["iters"]), _ptr(out["status"]),
+                              _ptr(out.get("traj_x")), _ptr(out.get("traj_p")),
+                              _ptr(warm_x), _ptr(warm_p), ctypes.c_void_p(s.cuda_stream))
+    if r != HJ_OK:
+        raise HJError(r, "hj_solve_batch")
+    return out
+
+
+def solve_workload(w, *, precision="fp32", return_traj=False, problem=None, device="cuda",
+                   **overrides):
+    """Convenience: run a workload dict (workloads.py) end to end on the GPU."""
+    prob = problem if problem is not None else Problem.from_workload(w)
+    o = dict(sigma=w["sigma"], tau=w["tau"], tol=w["tol"], max_iter=w["max_iter"],
+             check_every=w["check_every"], seed=w["seed"], init_radius=w["init_radius"])
+    o.update(overrides)
+    opts = make_opts(precision=precision, **o)
+    xq = torch.as_tensor(np.asarray(w["xq"], dtype=np.float64), device=device)
+    t = torch.as_tensor(np.asarray(w["t"], dtype=np.float64), device=device)
+    return solve_batch(prob, xq, t, int(w["N"]), opts, return_traj=return_traj)

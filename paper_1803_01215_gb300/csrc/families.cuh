@@ -1,0 +1,212 @@
+// Per-node Hamiltonian kernels for the register-resident solver.
+//
+// Each family provides, for one time node j with state x_j (D values):
+//   context(x, ctx)         quantities of H at x_j^k shared by the dual prox and
+//                           the x-gradient (H is evaluated once per node and
+//                           iteration, at x^k as in Appendix Algorithm A.1)
+//   prox(ctx, x, v, lam)    v <- argmin_p lam*H(x, p) + |p - v|^2/2
+//   gradx(ctx, x, p, g)     g <- grad_x H(x, p)
+//   H64(x, p)               H in double, for the value (fval of Algorithm 1)
+// All families have L = |u|^2/2, so H = <p, f0(x)> + |B(x)^T p|^2/2 (Section 2).
+#pragma once
+#include "hj_internal.cuh"
+
+namespace hj {
+
+template <typename T>
+__device__ __forceinline__ void sin_cos(T x, T* s, T* c);
+template <>
+__device__ __forceinline__ void sin_cos<float>(float x, float* s, float* c) {
+  __sincosf(x, s, c);
+}
+template <>
+__device__ __forceinline__ void sin_cos<double>(double x, double* s, double* c) {
+  sincos(x, s, c);
+}
+
+template <typename T>
+__device__ __forceinline__ T tanh_t(T y) { return tanh(y); }
+template <>
+__device__ __forceinline__ float tanh_t<float>(float y) { return tanhf(y); }
+
+// ---------------------------------------------------------------- H = |p|^2/2
+template <typename T, int D>
+struct FamQuadratic {
+  static constexpr bool kHasGradX = false;
+  struct Shared {};
+  struct Ctx {};
+  __device__ static void load_shared(const SolveArgs<T>&, Shared&) {}
+  __device__ FamQuadratic(const SolveArgs<T>&, const Shared&) {}
+  __device__ __forceinline__ void context(const T (&)[D], Ctx&) const {}
+  __device__ __forceinline__ void prox(const Ctx&, const T (&)[D], T (&v)[D], T lam) const {
+    const T s = T(1) / (T(1) + lam);
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] *= s;
+  }
+  __device__ __forceinline__ void gradx(const Ctx&, const T (&)[D], const T (&)[D], T (&g)[D]) const {
+#pragma unroll
+    for (int k = 0; k < D; ++k) g[k] = T(0);
+  }
+  __device__ __forceinline__ double H64(const double (&)[D], const double (&p)[D]) const {
+    double h = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) h += p[k] * p[k];
+    return 0.5 * h;
+  }
+};
+
+// ---------------------------------------------------------------- quadcopter, D = 12
+// State (x, y, z, psi, theta, phi, then rates).  Thrust direction
+//   a = (s_phi s_psi + c_phi c_psi s_theta, -c_psi s_phi + c_phi s_theta s_psi, c_theta c_phi)
+// f0 = (v_pos, v_ang, a_h a - g_z e3, 0), B = [(0_6; a/m; 0_3) | e10 | e11 | e12],
+// H = <p, f0> + |B^T p|^2/2 + eps |p|^2/2.
+template <typename T, int D>
+struct FamQuadcopter {
+  static_assert(D == 12, "quadcopter state is 12-D");
+  static constexpr bool kHasGradX = true;
+  struct Shared {};
+  struct Ctx { T a[3]; T J[9]; };
+  T m_inv, ah, gz, eps;
+  double m64, ah64, gz64, eps64;
+  __device__ static void load_shared(const SolveArgs<T>&, Shared&) {}
+  __device__ FamQuadcopter(const SolveArgs<T>& s, const Shared&)
+      : m_inv(T(1.0 / s.qc_m)), ah(T(s.qc_ah)), gz(T(s.qc_gz)), eps(T(s.qc_eps)),
+        m64(s.qc_m), ah64(s.qc_ah), gz64(s.qc_gz), eps64(s.qc_eps) {}
+
+  template <typename U>
+  __device__ __forceinline__ static void thrust(const U psi, const U th, const U ph, U (&a)[3],
+                                                U (&J)[9]) {
+    U sps, cps, sth, cth, sph, cph;
+    sin_cos<U>(psi, &sps, &cps);
+    sin_cos<U>(th, &sth, &cth);
+    sin_cos<U>(ph, &sph, &cph);
+    const U cc = cph * cps, cs = cph * sps, sc = sph * cps, ss = sph * sps;
+    a[0] = ss + cc * sth;
+    a[1] = -sc + cs * sth;
+    a[2] = cth * cph;
+    // J[3*r + k] = d a_r / d (psi, theta, phi)_k
+    J[0] = sc - cs * sth;
+    J[1] = cc * cth;
+    J[2] = cs - sc * sth;
+    J[3] = ss + cc * sth;
+    J[4] = cs * cth;
+    J[5] = -cc - ss * sth;
+    J[6] = U(0);
+    J[7] = -sth * cph;
+    J[8] = -cth * sph;
+  }
+
+  __device__ __forceinline__ void context(const T (&x)[D], Ctx& c) const {
+    thrust<T>(x[3], x[4], x[5], c.a, c.J);
+  }
+
+  // ((1 + lam eps) I + lam B B^T) p = v - lam f0.  Rows 0-5 and 9-11 decouple;
+  // rows 6-8 are a rank-1 update of a scaled identity (Sherman-Morrison).
+  __device__ __forceinline__ void prox(const Ctx& c, const T (&x)[D], T (&v)[D], T lam) const {
+    const T al = T(1) + lam * eps;
+    const T ial = T(1) / al;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] = (v[k] - lam * x[6 + k]) * ial;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[3 + k] = (v[3 + k] - lam * x[9 + k]) * ial;
+    const T irate = T(1) / (al + lam);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[9 + k] *= irate;
+    T w0 = v[6] - lam * ah * c.a[0];
+    T w1 = v[7] - lam * ah * c.a[1];
+    T w2 = v[8] - lam * (ah * c.a[2] - gz);
+    const T b0 = c.a[0] * m_inv, b1 = c.a[1] * m_inv, b2 = c.a[2] * m_inv;
+    const T bb = b0 * b0 + b1 * b1 + b2 * b2;
+    const T bw = b0 * w0 + b1 * w1 + b2 * w2;
+    const T f = lam * bw / (al + lam * bb);
+    v[6] = (w0 - f * b0) * ial;
+    v[7] = (w1 - f * b1) * ial;
+    v[8] = (w2 - f * b2) * ial;
+  }
+
+  __device__ __forceinline__ void gradx(const Ctx& c, const T (&)[D], const T (&p)[D],
+                                        T (&g)[D]) const {
+    const T u0 = (c.a[0] * p[6] + c.a[1] * p[7] + c.a[2] * p[8]) * m_inv;
+    const T coef = ah + u0 * m_inv;
+    g[0] = g[1] = g[2] = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      g[3 + k] = coef * (c.J[k] * p[6] + c.J[3 + k] * p[7] + c.J[6 + k] * p[8]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[6 + k] = p[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[9 + k] = p[3 + k];
+  }
+
+  __device__ __forceinline__ double H64(const double (&x)[D], const double (&p)[D]) const {
+    double a[3], J[9];
+    thrust<double>(x[3], x[4], x[5], a, J);
+    double h = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) h += p[k] * x[6 + k] + p[3 + k] * x[9 + k];
+    const double s = a[0] * p[6] + a[1] * p[7] + a[2] * p[8];
+    h += ah64 * s - gz64 * p[8];
+    const double u0 = s / m64;
+    double pp = 0.0, rr = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) pp += p[k] * p[k];
+#pragma unroll
+    for (int k = 9; k < 12; ++k) rr += p[k] * p[k];
+    return h + 0.5 * (u0 * u0 + rr) + 0.5 * eps64 * pp;
+  }
+};
+
+// ---------------------------------------------------------------- tanh drift, small D
+// H = <p, tanh(A x)> + |p|^2/2; A is held in shared memory (broadcast reads).
+template <typename T, int D>
+struct FamTanhDrift {
+  static constexpr bool kHasGradX = true;
+  struct Shared { T A[D * D]; };
+  struct Ctx { T a[D]; };
+  const T* A;
+  const double* A64;
+  __device__ static void load_shared(const SolveArgs<T>& s, Shared& sh) {
+    for (int i = threadIdx.x; i < D * D; i += blockDim.x) sh.A[i] = s.A[i];
+  }
+  __device__ FamTanhDrift(const SolveArgs<T>& s, const Shared& sh) : A(sh.A), A64(s.A64) {}
+  __device__ __forceinline__ void context(const T (&x)[D], Ctx& c) const {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      T y = T(0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) y += A[i * D + k] * x[k];
+      c.a[i] = tanh_t<T>(y);
+    }
+  }
+  __device__ __forceinline__ void prox(const Ctx& c, const T (&)[D], T (&v)[D], T lam) const {
+    const T s = T(1) / (T(1) + lam);
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = (v[k] - lam * c.a[k]) * s;
+  }
+  __device__ __forceinline__ void gradx(const Ctx& c, const T (&)[D], const T (&p)[D],
+                                        T (&g)[D]) const {
+    T w[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) w[k] = (T(1) - c.a[k] * c.a[k]) * p[k];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) s += A[k * D + i] * w[k];
+      g[i] = s;
+    }
+  }
+  __device__ __forceinline__ double H64(const double (&x)[D], const double (&p)[D]) const {
+    double h = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      double y = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) y += A64[i * D + k] * x[k];
+      h += p[i] * tanh(y) + 0.5 * p[i] * p[i];
+    }
+    return h;
+  }
+};
+
+}  // namespace hj

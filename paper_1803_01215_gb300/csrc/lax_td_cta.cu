@@ -1,0 +1,328 @@
+// Shared-memory batched PDHG for the tanh-drift Hamiltonian at larger d
+// (H = <p, tanh(A x)> + |p|^2/2, Algorithm 1 with the Section 5.3 updates).
+//
+// One CTA solves one query point at a time; the iterates live in shared memory
+// coordinate-major (X[k][j], k = coordinate, j = time node 0..N), so a thread
+// tile of 4 coordinates x 4 nodes reads 16-byte vectors.  Per iteration:
+//   phase A  Y = A X over all nodes (register-tiled SIMT product, A^T held in
+//            shared memory), epilogue: a = tanh(Y), dual prox
+//            p_j <- (p_j + sigma (z_j - z_{j-1}) - lam a) / (1 + lam), lam = sigma delta,
+//            and the work array W = (1 - a^2) * p_j.
+//   phase B  G = A^T W (second product, A held row-major), epilogue: the primal
+//            gradient step x_j <- x_j - tau (p_j - p_{j+1}) + tau delta G_j, the
+//            over-relaxation z_j, and the g-prox of x_0.
+// The squared increments are reduced in FP64 on test iterations only.  CTAs
+// draw points from a work counter (persistent grid).
+#include <cuda_runtime.h>
+
+#include "hj_internal.cuh"
+
+namespace hj {
+
+namespace {
+
+constexpr int kTI = 4;   // coordinates per thread tile
+constexpr int kTJ = 4;   // nodes per thread tile
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  __device__ __forceinline__ static void load(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+};
+template <>
+struct Vec4<double> {
+  __device__ __forceinline__ static void load(const double* p, double (&v)[4]) {
+    const double2 q0 = *reinterpret_cast<const double2*>(p);
+    const double2 q1 = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+  }
+};
+
+__host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
+
+template <typename T>
+__device__ __forceinline__ T tanh_c(T y) { return tanh(y); }
+template <>
+__device__ __forceinline__ float tanh_c<float>(float y) { return tanhf(y); }
+
+struct Layout {
+  int dp, Np;               // padded coordinate count and node count
+  size_t a_elems;           // one copy of A
+  size_t s_elems;           // one state array
+  __host__ __device__ Layout(int d, int N) {
+    dp = round4(d);
+    Np = round4(N + 1);
+    a_elems = (size_t)d * dp;
+    s_elems = (size_t)dp * Np;
+  }
+};
+
+// TWO: keep both A^T and A in shared memory (vector loads in both products);
+// otherwise only A, and the first product reads it with strided scalar loads.
+template <typename T, bool TWO>
+__global__ void __launch_bounds__(512)
+lax_td_cta_kernel(const SolveArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int d = a.d, N = a.N;
+  const Layout L(d, N);
+  const int dp = L.dp, Np = L.Np;
+  T* Am = reinterpret_cast<T*>(smem_raw);                 // Am[k*dp + i] = A[k][i]
+  T* At = TWO ? Am + L.a_elems : Am;                      // At[k*dp + i] = A[i][k]
+  T* X = (TWO ? At + L.a_elems : Am + L.a_elems);
+  T* P = X + L.s_elems;
+  T* Z = P + L.s_elems;
+  T* Wk = Z + L.s_elems;
+  double* red = reinterpret_cast<double*>(Wk + L.s_elems);  // [2 * nwarps]
+  __shared__ unsigned long long s_point;
+
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+
+  for (int e = tid; e < d * dp; e += nthr) {
+    const int k = e / dp, i = e - k * dp;
+    Am[e] = (i < d) ? a.A[k * d + i] : T(0);
+    if (TWO) At[e] = (i < d) ? a.At[k * d + i] : T(0);
+  }
+
+  const int tilesI = dp / kTI, tilesJ = Np / kTJ;
+  const int ntiles = tilesI * tilesJ;
+  const T sig = T(a.sigma), tau = T(a.tau), th = T(a.theta);
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_point = atomicAdd(a.counter, 1ull);
+    __syncthreads();
+    const int64_t b = (int64_t)s_point;
+    if (b >= a.B) break;
+    const double delta = a.t[b] / N;
+    const T lam = T(a.sigma * delta), taud = T(a.tau * delta);
+    const T ilam = T(1) / (T(1) + lam);
+    const uint64_t pt = (uint64_t)(a.point_offset + b);
+    const size_t stride = (size_t)(N + 1) * d;
+
+    // ---- initial iterate (Section 6 random guess, or a warm start)
+    for (int e = tid; e < dp * Np; e += nthr) {
+      const int k = e / Np, j = e - k * Np;
+      T xv = T(0), pv = T(0);
+      if (k < d && j <= N) {
+        const double xq = a.xq[b * d + k];
+        if (a.warm_x == nullptr) {
+          xv = (j < N) ? T(xq + a.radius * uniform_pm1(a.seed, pt, 0, j, k)) : T(xq);
+          pv = (j >= 1) ? T(a.radius * uniform_pm1(a.seed, pt, 1, j, k)) : T(0);
+        } else {
+          xv = (j < N) ? a.warm_x[b * stride + (size_t)j * d + k] : T(xq);
+          pv = (j >= 1) ? a.warm_p[b * stride + (size_t)j * d + k] : T(0);
+        }
+      }
+      X[e] = xv; P[e] = pv; Z[e] = xv; Wk[e] = T(0);
+    }
+    __syncthreads();
+
+    int k_it = 0;
+    int8_t st = HJ_POINT_MAX_ITER;
+    while (k_it < a.max_iter) {
+      ++k_it;
+      const bool chk = (k_it % a.check_every == 0) || (k_it == a.max_iter);
+      T rx = T(0), rp = T(0);
+      // ---- phase A: Y = A X, tanh, dual prox, W = (1 - a^2) p
+      for (int tile = tid; tile < ntiles; tile += nthr) {
+        const int i0 = (tile % tilesI) * kTI, j0 = (tile / tilesI) * kTJ;
+        T acc[kTI][kTJ];
+#pragma unroll
+        for (int r = 0; r < kTI; ++r)
+#pragma unroll
+          for (int c = 0; c < kTJ; ++c) acc[r][c] = T(0);
+#pragma unroll 4
+        for (int k = 0; k < d; ++k) {
+          T av[kTI], xv[kTJ];
+          if (TWO) {
+            Vec4<T>::load(At + k * dp + i0, av);
+          } else {
+#pragma unroll
+            for (int r = 0; r < kTI; ++r) av[r] = (i0 + r < d) ? Am[(i0 + r) * dp + k] : T(0);
+          }
+          Vec4<T>::load(X + k * Np + j0, xv);
+#pragma unroll
+          for (int r = 0; r < kTI; ++r)
+#pragma unroll
+            for (int c = 0; c < kTJ; ++c) acc[r][c] += av[r] * xv[c];
+        }
+#pragma unroll
+        for (int r = 0; r < kTI; ++r) {
+          const int i = i0 + r;
+#pragma unroll
+          for (int c = 0; c < kTJ; ++c) {
+            const int j = j0 + c;
+            if (i < d && j >= 1 && j <= N) {
+              const int e = i * Np + j;
+              const T av = tanh_c<T>(acc[r][c]);
+              const T v = P[e] + sig * (Z[e] - Z[e - 1]);
+              const T pn = (v - lam * av) * ilam;
+              if (chk) { const T df = pn - P[e]; rp += df * df; }
+              P[e] = pn;
+              Wk[e] = (T(1) - av * av) * pn;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      // ---- phase B: G = A^T W, primal gradient step, relaxation; g-prox of x_0
+      for (int tile = tid; tile < ntiles; tile += nthr) {
+        const int i0 = (tile % tilesI) * kTI, j0 = (tile / tilesI) * kTJ;
+        T acc[kTI][kTJ];
+#pragma unroll
+        for (int r = 0; r < kTI; ++r)
+#pragma unroll
+          for (int c = 0; c < kTJ; ++c) acc[r][c] = T(0);
+#pragma unroll 4
+        for (int k = 0; k < d; ++k) {
+          T av[kTI], wv[kTJ];
+          Vec4<T>::load(Am + k * dp + i0, av);
+          Vec4<T>::load(Wk + k * Np + j0, wv);
+#pragma unroll
+          for (int r = 0; r < kTI; ++r)
+#pragma unroll
+            for (int c = 0; c < kTJ; ++c) acc[r][c] += av[r] * wv[c];
+        }
+#pragma unroll
+        for (int r = 0; r < kTI; ++r) {
+          const int i = i0 + r;
+#pragma unroll
+          for (int c = 0; c < kTJ; ++c) {
+            const int j = j0 + c;
+            if (i < d && j >= 1 && j < N) {
+              const int e = i * Np + j;
+              const T xo = X[e];
+              const T xn = xo - tau * (P[e] - P[e + 1]) + taud * acc[r][c];
+              if (chk) { const T df = xn - xo; rx += df * df; }
+              Z[e] = xn + th * (xn - xo);
+              X[e] = xn;
+            }
+          }
+        }
+      }
+      if (tid < d) {
+        const int e = tid * Np;
+        const T w2 = T(a.W2[tid]), cc = T(a.c[tid]);
+        const T xo = X[e];
+        const T xn = (xo + tau * P[e + 1] + tau * w2 * cc) / (T(1) + tau * w2);
+        if (chk) { const T df = xn - xo; rx += df * df; }
+        Z[e] = xn + th * (xn - xo);
+        X[e] = xn;
+      }
+      if (chk) {
+        const double sx = warp_sum((double)rx), sp = warp_sum((double)rp);
+        if (lane == 0) { red[2 * warp] = sx; red[2 * warp + 1] = sp; }
+      }
+      __syncthreads();
+      if (chk) {
+        double sx = 0.0, sp = 0.0;
+        for (int w = 0; w < nwarps; ++w) { sx += red[2 * w]; sp += red[2 * w + 1]; }
+        if (!(isfinite(sx) && isfinite(sp))) { st = HJ_POINT_NONFINITE; break; }
+        if (sx < a.tol && sp < a.tol) { st = HJ_POINT_CONVERGED; break; }
+      }
+    }
+
+    // ---- value in FP64: g(x_0) + sum_j <p_j, x_j - x_{j-1}> - delta sum_j H(x_j, p_j)
+    double acc = 0.0;
+    for (int e = tid; e < d * N; e += nthr) {
+      const int j = 1 + e / d, i = e - (j - 1) * d;
+      const double* Ar = a.A64 + (size_t)i * d;
+      double y = 0.0;
+      for (int k = 0; k < d; ++k) y += Ar[k] * (double)X[k * Np + j];
+      const double pv = (double)P[i * Np + j];
+      const double dx = (double)X[i * Np + j] - (double)X[i * Np + j - 1];
+      acc += pv * dx - delta * (pv * tanh(y) + 0.5 * pv * pv);
+    }
+    if (tid < d) {
+      const double e0 = (double)X[tid * Np] - a.c[tid];
+      acc += 0.5 * a.W2[tid] * e0 * e0;
+    }
+    acc = warp_sum(acc);
+    __syncthreads();
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double v = 0.0;
+      for (int w = 0; w < nwarps; ++w) v += red[w];
+      a.V[b] = v;
+      a.iters[b] = k_it;
+      a.status[b] = st;
+    }
+    if (a.traj_x != nullptr || a.traj_p != nullptr) {
+      for (int e = tid; e < (N + 1) * d; e += nthr) {
+        const int j = e / d, i = e - j * d;
+        if (a.traj_x != nullptr) a.traj_x[b * stride + e] = X[i * Np + j];
+        if (a.traj_p != nullptr) a.traj_p[b * stride + e] = (j == 0) ? T(0) : P[i * Np + j];
+      }
+    }
+  }
+}
+
+template <typename T, bool TWO>
+size_t smem_bytes(int d, int N) {
+  const Layout L(d, N);
+  return ((TWO ? 2 : 1) * L.a_elems + 4 * L.s_elems) * sizeof(T) + 2 * 16 * sizeof(double);
+}
+
+template <typename T, bool TWO>
+hj_status launch(const SolveArgs<T>& a, cudaStream_t s, size_t smem) {
+  auto kern = lax_td_cta_kernel<T, TWO>;
+  int dev = 0, nsm = 0, max_optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HJ_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return HJ_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+      cudaSuccess)
+    return HJ_ERR_CUDA;
+  if (smem > (size_t)max_optin) return HJ_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return HJ_ERR_CUDA;
+  const Layout L(a.d, a.N);
+  const int tiles = (L.dp / kTI) * (L.Np / kTJ);
+  int threads = ((tiles + 31) / 32) * 32;
+  if (threads < 64) threads = 64;
+  if (threads > 512) threads = 512;
+  if (threads < a.d) threads = ((a.d + 31) / 32) * 32;   // x_0 update: one thread per coordinate
+  int bps = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, threads, smem) != cudaSuccess)
+    return HJ_ERR_CUDA;
+  if (bps < 1) return HJ_ERR_UNSUPPORTED;
+  const int64_t cap = (int64_t)bps * nsm;
+  const int grid = (int)(a.B < cap ? a.B : cap);
+  kern<<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? HJ_OK : HJ_ERR_CUDA;
+}
+
+}  // namespace
+
+template <typename T>
+size_t td_cta_smem_bytes(int d, int N) {
+  const size_t two = smem_bytes<T, true>(d, N);
+  if (two <= 227u * 1024u) return two;
+  const size_t one = smem_bytes<T, false>(d, N);
+  return one <= 227u * 1024u ? one : 0;
+}
+
+template <typename T>
+hj_status launch_td_cta_solver(const SolveArgs<T>& a, cudaStream_t s) {
+  if (a.d < 1 || a.d > kMaxD || a.N < 1 || a.N > kMaxN || a.inner_steps != 1)
+    return HJ_ERR_UNSUPPORTED;
+  const size_t two = smem_bytes<T, true>(a.d, a.N);
+  if (two <= 227u * 1024u) return launch<T, true>(a, s, two);
+  const size_t one = smem_bytes<T, false>(a.d, a.N);
+  if (one <= 227u * 1024u) return launch<T, false>(a, s, one);
+  return HJ_ERR_UNSUPPORTED;
+}
+
+template size_t td_cta_smem_bytes<float>(int, int);
+template size_t td_cta_smem_bytes<double>(int, int);
+template hj_status launch_td_cta_solver<float>(const SolveArgs<float>&, cudaStream_t);
+template hj_status launch_td_cta_solver<double>(const SolveArgs<double>&, cudaStream_t);
+
+}  // namespace hj
