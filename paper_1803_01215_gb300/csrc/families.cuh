@@ -24,6 +24,12 @@ __device__ __forceinline__ void sin_cos<double>(double x, double* s, double* c) 
   sincos(x, s, c);
 }
 
+// a / b; FP32 uses the fast reciprocal-based division (2 ulp).
+template <typename T>
+__device__ __forceinline__ T fdiv(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
+
 template <typename T>
 __device__ __forceinline__ T tanh_t(T y) { return tanh(y); }
 template <>
@@ -118,7 +124,7 @@ struct FamQuadcopter {
     const T b0 = c.a[0] * m_inv, b1 = c.a[1] * m_inv, b2 = c.a[2] * m_inv;
     const T bb = b0 * b0 + b1 * b1 + b2 * b2;
     const T bw = b0 * w0 + b1 * w1 + b2 * w2;
-    const T f = lam * bw / (al + lam * bb);
+    const T f = fdiv<T>(lam * bw, al + lam * bb);
     v[6] = (w0 - f * b0) * ial;
     v[7] = (w1 - f * b1) * ial;
     v[8] = (w2 - f * b2) * ial;

@@ -24,10 +24,19 @@ namespace hj {
 
 constexpr int kWarpsPerCta = 4;
 
+// Per-CTA constants in shared memory (kept out of registers): the family's own
+// data and the g-prox of x_0, x_0 <- (v + tau W^2 c) / (1 + tau W^2), as an
+// offset and a reciprocal per coordinate.
+template <typename T, class F, int D>
+struct WarpShared {
+  typename F::Shared fam;
+  T g_off[D], g_inv[D];
+  double w2d[D], cd[D];
+};
+
 template <typename T, class F, int D, int NPL>
 __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam, int64_t b,
-                                            int lane, const T (&w2)[D], const T (&cw)[D],
-                                            const double (&w2d)[D], const double (&cd)[D]) {
+                                            int lane, const WarpShared<T, F, D>& sh) {
   const int N = a.N;
   const double tb = a.t[b];
   const double delta = tb / N;
@@ -122,7 +131,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const T vx = x0[k] + tau * p[0][k];                  // (D^T p)_0 = -p_1
-        const T xn = (vx + tau * w2[k] * cw[k]) / (T(1) + tau * w2[k]);
+        const T xn = (vx + sh.g_off[k]) * sh.g_inv[k];
         if (chk) { const T e = xn - x0[k]; rx += e * e; }
         z0[k] = xn + th * (xn - x0[k]);
         x0[k] = xn;
@@ -195,8 +204,8 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
       double g = 0.0;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        const double e = (double)x0[k] - cd[k];
-        g += w2d[k] * e * e;
+        const double e = (double)x0[k] - sh.cd[k];
+        g += sh.w2d[k] * e * e;
       }
       acc += 0.5 * g;
     }
@@ -234,24 +243,24 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
 template <typename T, class F, int D, int NPL>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
 lax_warp_kernel(const SolveArgs<T> a) {
-  __shared__ typename F::Shared sh;
-  F::load_shared(a, sh);
-  __syncthreads();
-  const F fam(a, sh);
-  const int lane = threadIdx.x & 31;
-  T w2[D], cw[D];
-  double w2d[D], cd[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    w2d[k] = a.W2[k]; cd[k] = a.c[k];
-    w2[k] = T(w2d[k]); cw[k] = T(cd[k]);
+  __shared__ WarpShared<T, F, D> sh;
+  F::load_shared(a, sh.fam);
+  for (int k = threadIdx.x; k < D; k += blockDim.x) {
+    const double w2 = a.W2[k], c = a.c[k];
+    sh.w2d[k] = w2;
+    sh.cd[k] = c;
+    sh.g_off[k] = T(a.tau * w2 * c);
+    sh.g_inv[k] = T(1.0 / (1.0 + a.tau * w2));
   }
+  __syncthreads();
+  const F fam(a, sh.fam);
+  const int lane = threadIdx.x & 31;
   for (;;) {
     unsigned long long bb = 0;
     if (lane == 0) bb = atomicAdd(a.counter, 1ull);
     bb = __shfl_sync(kFull, bb, 0);
     if ((int64_t)bb >= a.B) break;
-    solve_point<T, F, D, NPL>(a, fam, (int64_t)bb, lane, w2, cw, w2d, cd);
+    solve_point<T, F, D, NPL>(a, fam, (int64_t)bb, lane, sh);
   }
 }
 

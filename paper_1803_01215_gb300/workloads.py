@@ -81,7 +81,7 @@ def tanh_drift(d, B=16384, seed=3, N=32):
 
 # Step sizes chosen on the oracle (sigma sweep at tau = 0.24 / sigma); the fixed
 # point does not depend on them, only the iteration count does.
-QC_SIGMA = 1.0
+QC_SIGMA = 1.4
 TD_SIGMA = 1.0
 
 
