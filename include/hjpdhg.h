@@ -60,8 +60,11 @@ enum {
  * value sum in FP64; FP64 runs everything in double.                        */
 enum { HJ_PREC_FP32 = 0, HJ_PREC_FP64 = 1 };
 
-/* Per-point outcome written to status[]. */
-enum { HJ_POINT_CONVERGED = 0, HJ_POINT_MAX_ITER = 1, HJ_POINT_NONFINITE = 2 };
+/* Per-point outcome written to status[].  HJ_POINT_INVALID marks a point whose
+ * own N was outside the range of the kernel it was routed to (ragged batches:
+ * N[b] outside 1..256); such a point is not iterated.                        */
+enum { HJ_POINT_CONVERGED = 0, HJ_POINT_MAX_ITER = 1, HJ_POINT_NONFINITE = 2,
+       HJ_POINT_INVALID = 3 };
 
 typedef struct hj_problem_s* hj_problem;
 
@@ -130,6 +133,89 @@ hj_status hj_solve_batch(hj_problem prob, int64_t B,
                          void* traj_x, void* traj_p,
                          const void* warm_x, const void* warm_p,
                          void* stream);
+
+/* Launch shape of the register-resident kernel (quadratic d <= 4, quadcopter,
+ * tanh drift d in {2, 4}): a group of `warps_per_point` warps (1, 2, 4, 8)
+ * solves one point, each lane holding `nodes_per_lane` time nodes (1 or 2; 1
+ * for FP64), so N <= 32 * warps_per_point * nodes_per_lane.  The shape does not
+ * change any result, only the speed (the nodes a lane owns and the exchange
+ * between lanes are the same arithmetic).  The shape is stored on the handle for
+ * (precision, N) and used by later solves with that N.
+ * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_UNSUPPORTED (no such instantiation).     */
+hj_status hj_set_launch_shape(hj_problem prob, int32_t precision, int32_t N,
+                              int32_t warps_per_point, int32_t nodes_per_lane);
+
+/* The launch shape solves with (precision, N) will use (host outputs).      */
+hj_status hj_get_launch_shape(hj_problem prob, int32_t precision, int32_t N,
+                              int32_t* warps_per_point, int32_t* nodes_per_lane);
+
+/* Autotuner: times every instantiated launch shape on the caller's sample
+ * (xq, t device arrays of B points, options as for hj_solve_batch), `repeats`
+ * timed runs each after one warm-up, stores the fastest on the handle for
+ * (opts->precision, N) and returns it (host outputs, each may be NULL).
+ * Synchronises `stream`; allocates and frees its own scratch outputs.
+ * Errors: as hj_solve_batch; HJ_ERR_UNSUPPORTED when the family/d has no
+ * register-resident kernel (the shared-memory kernel has no shape to tune). */
+hj_status hj_autotune(hj_problem prob, int64_t B, const double* xq, const double* t, int32_t N,
+                      const hj_solver_opts* opts, int32_t repeats, int32_t* warps_per_point,
+                      int32_t* nodes_per_lane, float* best_ms, void* stream);
+
+/* ---------------------------------------------------------------- ragged batches
+ * A ragged batch mixes points of several problems (family, d) and their own
+ * number of time steps N (Algorithm 1 per point, as hj_solve_batch).  A plan
+ * fixes the batch's structure once; every solve with it is one CUDA-graph
+ * launch in which each (problem, N class) bucket of points runs its own
+ * persistent kernel as a parallel branch.  The paper has no ragged batches; the
+ * arithmetic per point is exactly that of hj_solve_batch.                    */
+typedef struct hj_ragged_plan_s* hj_ragged_plan;
+
+/* Build a plan.
+ *   probs    (host) n_prob problem handles, all on the current device; they must
+ *            outlive the plan.
+ *   prob_of  (host) [B] int32: problem index of each point (0..n_prob-1).
+ *   N_of     (host) [B] int32: time steps of each point (1..256).
+ *   opts     (host) options shared by every point; point b's initial guess uses
+ *            global index opts->point_offset + b.
+ * Packed layouts (offsets from hj_ragged_plan_layout): the query points are
+ * xq[xq_off[b] .. xq_off[b] + d_b) (doubles), the trajectories
+ * traj[traj_off[b] .. traj_off[b+1]) as [N_b+1][d_b] (iterate type).
+ * The plan owns device copies of N, the offsets and the bucket index lists,
+ * one work counter per bucket and four side streams.
+ * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_STEP_SIZE, HJ_ERR_OOM, HJ_ERR_CUDA.      */
+hj_status hj_ragged_plan_create(hj_ragged_plan* out, int32_t n_prob, const hj_problem* probs,
+                                int64_t B, const int32_t* prob_of, const int32_t* N_of,
+                                const hj_solver_opts* opts);
+
+/* Host outputs, each may be NULL: xq_offsets[B+1] (doubles), traj_offsets[B+1]
+ * (elements), number of buckets.                                            */
+hj_status hj_ragged_plan_layout(hj_ragged_plan plan, int64_t* xq_offsets, int64_t* traj_offsets,
+                                int32_t* n_buckets);
+
+/* Host outputs for bucket i (each may be NULL): its problem index, largest N,
+ * number of points and launch shape (0, 0 = shared-memory kernel).           */
+hj_status hj_ragged_plan_bucket(hj_ragged_plan plan, int32_t i, int32_t* problem, int32_t* n_max,
+                                int64_t* n_points, int32_t* warps_per_point,
+                                int32_t* nodes_per_lane);
+
+/* Solve the batch: xq (device, packed), t (device, [B]); V, iters, status
+ * (device, [B]); traj_x, traj_p (device, packed, may be NULL).  The first call
+ * with a given set of buffers captures the graph on `stream` (so it must not be
+ * called while `stream` is itself being captured); later calls with the same
+ * buffers replay it.  Solves on one plan must be ordered on one stream.
+ * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_CUDA.                                   */
+hj_status hj_ragged_solve(hj_ragged_plan plan, const double* xq, const double* t, double* V,
+                          int32_t* iters, int8_t* status, void* traj_x, void* traj_p,
+                          void* stream);
+
+/* Autotune every bucket that runs the register-resident kernel: time each
+ * instantiated launch shape on the bucket's own points (`repeats` timed runs
+ * after one warm-up) and keep the fastest.  Synchronises `stream`; allocates
+ * and frees scratch outputs; drops the captured graph.                       */
+hj_status hj_ragged_autotune(hj_ragged_plan plan, const double* xq, const double* t,
+                             int32_t repeats, void* stream);
+
+/* Destroy a plan (NULL accepted); synchronises its device first.            */
+hj_status hj_ragged_plan_destroy(hj_ragged_plan plan);
 
 /* Human-readable name of a status code (static storage). */
 const char* hj_status_str(hj_status s);

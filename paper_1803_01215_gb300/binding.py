@@ -35,6 +35,9 @@ class SolverOpts(ctypes.Structure):
 
 _LIB = None
 EXPORTED = ("hj_problem_create", "hj_problem_destroy", "hj_solve_batch",
+            "hj_set_launch_shape", "hj_get_launch_shape", "hj_autotune",
+            "hj_ragged_plan_create", "hj_ragged_plan_layout", "hj_ragged_plan_bucket",
+            "hj_ragged_solve", "hj_ragged_autotune", "hj_ragged_plan_destroy",
             "hj_status_str", "hj_version")
 
 
@@ -51,6 +54,24 @@ def _lib():
         lib.hj_problem_destroy.argtypes = [P]
         lib.hj_solve_batch.argtypes = [P, I64, P, P, I32, ctypes.POINTER(SolverOpts),
                                        P, P, P, P, P, P, P, P]
+        lib.hj_set_launch_shape.argtypes = [P, I32, I32, I32, I32]
+        lib.hj_get_launch_shape.argtypes = [P, I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I32)]
+        lib.hj_autotune.argtypes = [P, I64, P, P, I32, ctypes.POINTER(SolverOpts), I32,
+                                    ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                    ctypes.POINTER(ctypes.c_float), P]
+        for name in ("hj_set_launch_shape", "hj_get_launch_shape", "hj_autotune"):
+            getattr(lib, name).restype = ctypes.c_int
+        PI32, PI64 = ctypes.POINTER(I32), ctypes.POINTER(I64)
+        lib.hj_ragged_plan_create.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(P), I64,
+                                              PI32, PI32, ctypes.POINTER(SolverOpts)]
+        lib.hj_ragged_plan_layout.argtypes = [P, PI64, PI64, PI32]
+        lib.hj_ragged_plan_bucket.argtypes = [P, I32, PI32, PI32, PI64, PI32, PI32]
+        lib.hj_ragged_solve.argtypes = [P, P, P, P, P, P, P, P, P]
+        lib.hj_ragged_autotune.argtypes = [P, P, P, I32, P]
+        lib.hj_ragged_plan_destroy.argtypes = [P]
+        for name in ("hj_ragged_plan_create", "hj_ragged_plan_layout", "hj_ragged_plan_bucket",
+                     "hj_ragged_solve", "hj_ragged_autotune", "hj_ragged_plan_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
         lib.hj_status_str.restype = ctypes.c_char_p
         lib.hj_status_str.argtypes = [ctypes.c_int]
         lib.hj_version.restype = ctypes.c_int32
@@ -96,6 +117,35 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def set_launch_shape(problem, precision, N, warps_per_point, nodes_per_lane):
+    """hj_set_launch_shape: G warps per point, NPL nodes per lane for (precision, N)."""
+    r = _lib().hj_set_launch_shape(problem.handle, PREC[precision], int(N), int(warps_per_point),
+                                   int(nodes_per_lane))
+    if r != HJ_OK:
+        raise HJError(r, "hj_set_launch_shape")
+
+
+def get_launch_shape(problem, precision, N):
+    g, n = ctypes.c_int32(), ctypes.c_int32()
+    r = _lib().hj_get_launch_shape(problem.handle, PREC[precision], int(N), ctypes.byref(g),
+                                   ctypes.byref(n))
+    if r != HJ_OK:
+        raise HJError(r, "hj_get_launch_shape")
+    return g.value, n.value
+
+
+def autotune(problem, xq, t, N, opts, repeats=2, stream=None):
+    """hj_autotune on a device sample; returns (warps_per_point, nodes_per_lane, ms)."""
+    g, n, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    s = stream if stream is not None else torch.cuda.current_stream(xq.device)
+    r = _lib().hj_autotune(problem.handle, xq.shape[0], _ptr(xq.contiguous()), _ptr(t.contiguous()),
+                           int(N), ctypes.byref(opts), int(repeats), ctypes.byref(g),
+                           ctypes.byref(n), ctypes.byref(ms), ctypes.c_void_p(s.cuda_stream))
+    if r != HJ_OK:
+        raise HJError(r, "hj_autotune")
+    return g.value, n.value, ms.value
 
 
 def _ptr(t):
@@ -155,3 +205,92 @@ def solve_workload(w, *, precision="fp32", return_traj=False, problem=None, devi
     xq = torch.as_tensor(np.asarray(w["xq"], dtype=np.float64), device=device)
     t = torch.as_tensor(np.asarray(w["t"], dtype=np.float64), device=device)
     return solve_batch(prob, xq, t, int(w["N"]), opts, return_traj=return_traj)
+
+
+class RaggedPlan:
+    """hj_ragged_plan_*: a batch mixing problems and per-point N, solved by one
+    CUDA-graph launch.  `problems` are Problem objects (kept alive here)."""
+
+    def __init__(self, problems, prob_of, N_of, opts):
+        self.problems = list(problems)
+        self.prob_of = np.ascontiguousarray(prob_of, dtype=np.int32)
+        self.N_of = np.ascontiguousarray(N_of, dtype=np.int32)
+        self.B = len(self.prob_of)
+        self.opts = opts
+        hs = (ctypes.c_void_p * len(self.problems))(*[p.handle.value for p in self.problems])
+        h = ctypes.c_void_p()
+        I32P = ctypes.POINTER(ctypes.c_int32)
+        r = _lib().hj_ragged_plan_create(ctypes.byref(h), len(self.problems), hs, self.B,
+                                         self.prob_of.ctypes.data_as(I32P),
+                                         self.N_of.ctypes.data_as(I32P), ctypes.byref(opts))
+        if r != HJ_OK:
+            raise HJError(r, "hj_ragged_plan_create")
+        self.handle = h
+        self.xq_off = np.zeros(self.B + 1, dtype=np.int64)
+        self.traj_off = np.zeros(self.B + 1, dtype=np.int64)
+        nb = ctypes.c_int32()
+        I64P = ctypes.POINTER(ctypes.c_int64)
+        _lib().hj_ragged_plan_layout(h, self.xq_off.ctypes.data_as(I64P),
+                                     self.traj_off.ctypes.data_as(I64P), ctypes.byref(nb))
+        self.n_buckets = nb.value
+
+    def buckets(self):
+        out = []
+        for i in range(self.n_buckets):
+            v = [ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(),
+                 ctypes.c_int32()]
+            _lib().hj_ragged_plan_bucket(self.handle, i, *[ctypes.byref(x) for x in v])
+            out.append(dict(problem=v[0].value, n_max=v[1].value, n_points=v[2].value,
+                            warps_per_point=v[3].value, nodes_per_lane=v[4].value))
+        return out
+
+    def pack_xq(self, xq_list):
+        """Host list of per-point query arrays -> packed float64 numpy array."""
+        out = np.empty(self.xq_off[-1])
+        for b, x in enumerate(xq_list):
+            out[self.xq_off[b]:self.xq_off[b + 1]] = x
+        return out
+
+    def autotune(self, xq, t, repeats=1, stream=None):
+        s = stream if stream is not None else torch.cuda.current_stream(xq.device)
+        r = _lib().hj_ragged_autotune(self.handle, _ptr(xq), _ptr(t), int(repeats),
+                                      ctypes.c_void_p(s.cuda_stream))
+        if r != HJ_OK:
+            raise HJError(r, "hj_ragged_autotune")
+
+    def solve(self, xq, t, *, return_traj=False, out=None, stream=None):
+        """xq packed float64 cuda tensor, t [B] float64 cuda tensor."""
+        dev = xq.device
+        it_dtype = torch.float32 if self.opts.precision == 0 else torch.float64
+        if out is None:
+            out = dict(V=torch.empty(self.B, dtype=torch.float64, device=dev),
+                       iters=torch.empty(self.B, dtype=torch.int32, device=dev),
+                       status=torch.empty(self.B, dtype=torch.int8, device=dev))
+            if return_traj:
+                n = int(self.traj_off[-1])
+                out["traj_x"] = torch.empty(n, dtype=it_dtype, device=dev)
+                out["traj_p"] = torch.empty(n, dtype=it_dtype, device=dev)
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        r = _lib().hj_ragged_solve(self.handle, _ptr(xq), _ptr(t), _ptr(out["V"]),
+                                   _ptr(out["iters"]), _ptr(out["status"]),
+                                   _ptr(out.get("traj_x")), _ptr(out.get("traj_p")),
+                                   ctypes.c_void_p(s.cuda_stream))
+        if r != HJ_OK:
+            raise HJError(r, "hj_ragged_solve")
+        return out
+
+    def point_traj(self, flat, b):
+        """Trajectory block [N_b+1][d_b] of point b in a packed array."""
+        d = int((self.xq_off[b + 1] - self.xq_off[b]))
+        return flat[self.traj_off[b]:self.traj_off[b + 1]].reshape(-1, d)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib().hj_ragged_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -4,58 +4,18 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "hj_internal.cuh"
 #include "hjpdhg.h"
 
-struct hj_problem_s {
-  int family = 0, d = 0, device = 0;
-  double qc[4] = {0, 0, 0, 0};        // m, a_h, g_z, eps
-  double* W2 = nullptr;               // [d]
-  double* c = nullptr;                // [d]
-  float* Af = nullptr;                // [d][d]
-  float* Atf = nullptr;               // [d][d]
-  double* Ad = nullptr;               // [d][d]
-  double* Atd = nullptr;              // [d][d]
-  unsigned long long* counter = nullptr;
-};
+#include "problem.cuh"
 
-namespace {
-
-bool all_finite(const double* v, int64_t n) {
-  for (int64_t i = 0; i < n; ++i)
-    if (!std::isfinite(v[i])) return false;
-  return true;
-}
-
-template <typename T>
-hj_status upload(T** dst, const T* src, size_t n) {
-  if (cudaMalloc(reinterpret_cast<void**>(dst), n * sizeof(T)) != cudaSuccess) return HJ_ERR_OOM;
-  if (cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
-    return HJ_ERR_CUDA;
-  return HJ_OK;
-}
-
-void release(hj_problem_s* p) {
-  cudaFree(p->W2); cudaFree(p->c);
-  cudaFree(p->Af); cudaFree(p->Atf); cudaFree(p->Ad); cudaFree(p->Atd);
-  cudaFree(p->counter);
-  delete p;
-}
-
-// Which kernel serves a request: the register-resident warp kernel when it has
-// an instantiation for (family, d, N), else the shared-memory tanh-drift kernel.
-template <typename T>
-hj_status dispatch(const hj_problem_s* p, const hj::SolveArgs<T>& a, cudaStream_t s) {
-  hj_status r = hj::launch_warp_solver<T>(p->family, a, s);
-  if (r != HJ_ERR_UNSUPPORTED) return r;
-  if (p->family == HJ_FAMILY_TANH_DRIFT) return hj::launch_td_cta_solver<T>(a, s);
-  return HJ_ERR_UNSUPPORTED;
-}
-
-}  // namespace
+using namespace hj_detail;
 
 extern "C" {
 
@@ -150,53 +110,113 @@ hj_status hj_solve_batch(hj_problem prob, int64_t B, const double* xq, const dou
   if (prob == nullptr || opts == nullptr || B < 0) return HJ_ERR_INVALID_ARG;
   if (N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;
   const hj_solver_opts& o = *opts;
-  if (!(std::isfinite(o.sigma) && o.sigma > 0) || !(std::isfinite(o.tau) && o.tau > 0))
-    return HJ_ERR_INVALID_ARG;
-  if (!(o.theta >= 0.0 && o.theta <= 1.0) || !(o.tol >= 0.0) || !std::isfinite(o.tol))
-    return HJ_ERR_INVALID_ARG;
-  if (o.max_iter < 1 || o.check_every < 1 || o.inner_steps < 1) return HJ_ERR_INVALID_ARG;
-  if (o.precision != HJ_PREC_FP32 && o.precision != HJ_PREC_FP64) return HJ_ERR_INVALID_ARG;
-  if (!(std::isfinite(o.init_radius) && o.init_radius >= 0.0) || o.point_offset < 0)
-    return HJ_ERR_INVALID_ARG;
+  const hj_status oc = check_opts(o);
+  if (oc != HJ_OK) return oc;
   if ((warm_x == nullptr) != (warm_p == nullptr)) return HJ_ERR_INVALID_ARG;
   if (o.point_offset + B > (int64_t(1) << 32)) return HJ_ERR_INVALID_ARG;
-  if (4.0 * o.sigma * o.tau >= 1.0) return HJ_ERR_STEP_SIZE;
   if (B == 0) return HJ_OK;
   if (xq == nullptr || t == nullptr || V == nullptr || iters == nullptr || status == nullptr)
     return HJ_ERR_INVALID_ARG;
   int cur = 0;
   if (cudaGetDevice(&cur) != cudaSuccess) return HJ_ERR_CUDA;
   if (cur != prob->device) return HJ_ERR_INVALID_ARG;
-
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(prob->counter, 0, sizeof(unsigned long long), s) != cudaSuccess)
-    return HJ_ERR_CUDA;
-  if (o.precision == HJ_PREC_FP32) {
-    hj::SolveArgs<float> a{};
-    a.B = B; a.N = N; a.d = prob->d;
-    a.sigma = o.sigma; a.tau = o.tau; a.theta = o.theta; a.tol = o.tol;
-    a.max_iter = o.max_iter; a.check_every = o.check_every; a.inner_steps = o.inner_steps;
-    a.seed = o.seed; a.radius = o.init_radius; a.point_offset = o.point_offset;
-    a.xq = xq; a.t = t; a.V = V; a.iters = iters; a.status = status;
-    a.traj_x = static_cast<float*>(traj_x); a.traj_p = static_cast<float*>(traj_p);
-    a.warm_x = static_cast<const float*>(warm_x); a.warm_p = static_cast<const float*>(warm_p);
-    a.W2 = prob->W2; a.c = prob->c; a.A = prob->Af; a.At = prob->Atf; a.A64 = prob->Ad;
-    a.qc_m = prob->qc[0]; a.qc_ah = prob->qc[1]; a.qc_gz = prob->qc[2]; a.qc_eps = prob->qc[3];
-    a.counter = prob->counter;
-    return dispatch<float>(prob, a, s);
+  const hj::WarpConfig cfg = shape_for(prob, o.precision, N);
+  if (o.precision == HJ_PREC_FP32)
+    return run_solve<float>(prob, B, N, o, cfg, xq, t, V, iters, status, traj_x, traj_p,
+                            warm_x, warm_p, s);
+  return run_solve<double>(prob, B, N, o, cfg, xq, t, V, iters, status, traj_x, traj_p, warm_x,
+                           warm_p, s);
+}
+
+hj_status hj_set_launch_shape(hj_problem prob, int32_t precision, int32_t N,
+                              int32_t warps_per_point, int32_t nodes_per_lane) {
+  if (prob == nullptr || N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;
+  if (precision != HJ_PREC_FP32 && precision != HJ_PREC_FP64) return HJ_ERR_INVALID_ARG;
+  const hj::WarpConfig c{warps_per_point, nodes_per_lane};
+  if (!hj::warp_config_available(prob->family, prob->d, c, precision == HJ_PREC_FP64))
+    return HJ_ERR_UNSUPPORTED;
+  if (N > 32 * c.G * c.NPL) return HJ_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> g(prob->mu);
+  prob->shapes[{precision, N}] = c;
+  return HJ_OK;
+}
+
+hj_status hj_get_launch_shape(hj_problem prob, int32_t precision, int32_t N,
+                              int32_t* warps_per_point, int32_t* nodes_per_lane) {
+  if (prob == nullptr || warps_per_point == nullptr || nodes_per_lane == nullptr)
+    return HJ_ERR_INVALID_ARG;
+  if (N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;
+  const hj::WarpConfig c = shape_for(prob, precision, N);
+  *warps_per_point = c.G;
+  *nodes_per_lane = c.NPL;
+  return HJ_OK;
+}
+
+hj_status hj_autotune(hj_problem prob, int64_t B, const double* xq, const double* t, int32_t N,
+                      const hj_solver_opts* opts, int32_t repeats, int32_t* warps_per_point,
+                      int32_t* nodes_per_lane, float* best_ms, void* stream) {
+  if (prob == nullptr || opts == nullptr || xq == nullptr || t == nullptr || B < 1)
+    return HJ_ERR_INVALID_ARG;
+  if (N < 1 || N > hj::kMaxN || repeats < 1) return HJ_ERR_INVALID_ARG;
+  const hj_status oc = check_opts(*opts);
+  if (oc != HJ_OK) return oc;
+  const bool f64 = opts->precision == HJ_PREC_FP64;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  double* V = nullptr;
+  int32_t* it = nullptr;
+  int8_t* st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  hj_status r = HJ_OK;
+  if (cudaMalloc(&V, B * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&it, B * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&st, B * sizeof(int8_t)) != cudaSuccess)
+    r = HJ_ERR_OOM;
+  if (r == HJ_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    r = HJ_ERR_CUDA;
+  float best = -1.0f;
+  hj::WarpConfig best_c{0, 0};
+  const int Gs[4] = {1, 2, 4, 8};
+  for (int npl = 1; npl <= 2 && r == HJ_OK; ++npl) {
+    for (int gi = 0; gi < 4 && r == HJ_OK; ++gi) {
+      const hj::WarpConfig c{Gs[gi], npl};
+      if (!hj::warp_config_available(prob->family, prob->d, c, f64) || N > 32 * c.G * c.NPL)
+        continue;
+      float tot = 0.0f;
+      for (int rep = 0; rep <= repeats && r == HJ_OK; ++rep) {   // rep 0 warms up
+        if (cudaEventRecord(e0, s) != cudaSuccess) { r = HJ_ERR_CUDA; break; }
+        r = f64 ? run_solve<double>(prob, B, N, *opts, c, xq, t, V, it, st, nullptr, nullptr,
+                                    nullptr, nullptr, s)
+                : run_solve<float>(prob, B, N, *opts, c, xq, t, V, it, st, nullptr, nullptr,
+                                   nullptr, nullptr, s);
+        if (r != HJ_OK) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+          r = HJ_ERR_CUDA;
+          break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tot += ms;
+      }
+      if (r == HJ_OK && (best < 0.0f || tot / repeats < best)) {
+        best = tot / repeats;
+        best_c = c;
+      }
+    }
   }
-  hj::SolveArgs<double> a{};
-  a.B = B; a.N = N; a.d = prob->d;
-  a.sigma = o.sigma; a.tau = o.tau; a.theta = o.theta; a.tol = o.tol;
-  a.max_iter = o.max_iter; a.check_every = o.check_every; a.inner_steps = o.inner_steps;
-  a.seed = o.seed; a.radius = o.init_radius; a.point_offset = o.point_offset;
-  a.xq = xq; a.t = t; a.V = V; a.iters = iters; a.status = status;
-  a.traj_x = static_cast<double*>(traj_x); a.traj_p = static_cast<double*>(traj_p);
-  a.warm_x = static_cast<const double*>(warm_x); a.warm_p = static_cast<const double*>(warm_p);
-  a.W2 = prob->W2; a.c = prob->c; a.A = prob->Ad; a.At = prob->Atd; a.A64 = prob->Ad;
-  a.qc_m = prob->qc[0]; a.qc_ah = prob->qc[1]; a.qc_gz = prob->qc[2]; a.qc_eps = prob->qc[3];
-  a.counter = prob->counter;
-  return dispatch<double>(prob, a, s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(V); cudaFree(it); cudaFree(st);
+  if (r != HJ_OK) return r;
+  if (best_c.G == 0) return HJ_ERR_UNSUPPORTED;
+  {
+    std::lock_guard<std::mutex> g(prob->mu);
+    prob->shapes[{opts->precision, N}] = best_c;
+  }
+  if (warps_per_point) *warps_per_point = best_c.G;
+  if (nodes_per_lane) *nodes_per_lane = best_c.NPL;
+  if (best_ms) *best_ms = best;
+  return HJ_OK;
 }
 
 }  // extern "C"

@@ -4,9 +4,11 @@
 //   context(x, ctx)         quantities of H at x_j^k shared by the dual prox and
 //                           the x-gradient (H is evaluated once per node and
 //                           iteration, at x^k as in Appendix Algorithm A.1)
-//   prox(ctx, x, v, lam)    v <- argmin_p lam*H(x, p) + |p - v|^2/2
+//   point(lam)              per-point constants of the prox (lam = sigma delta)
+//   prox(ctx, pc, x, v)     v <- argmin_p lam*H(x, p) + |p - v|^2/2
 //   gradx(ctx, x, p, g)     g <- grad_x H(x, p)
-//   H64(x, p)               H in double, for the value (fval of Algorithm 1)
+//   H64(x, p)               H in double from the iterates, for the value
+//                           (fval of Algorithm 1); converts element by element
 // All families have L = |u|^2/2, so H = <p, f0(x)> + |B(x)^T p|^2/2 (Section 2).
 #pragma once
 #include "hj_internal.cuh"
@@ -41,22 +43,23 @@ struct FamQuadratic {
   static constexpr bool kHasGradX = false;
   struct Shared {};
   struct Ctx {};
+  struct PC { T s; };
   __device__ static void load_shared(const SolveArgs<T>&, Shared&) {}
   __device__ FamQuadratic(const SolveArgs<T>&, const Shared&) {}
+  __device__ __forceinline__ PC point(T lam) const { return PC{T(1) / (T(1) + lam)}; }
   __device__ __forceinline__ void context(const T (&)[D], Ctx&) const {}
-  __device__ __forceinline__ void prox(const Ctx&, const T (&)[D], T (&v)[D], T lam) const {
-    const T s = T(1) / (T(1) + lam);
+  __device__ __forceinline__ void prox(const Ctx&, const PC& pc, const T (&)[D], T (&v)[D]) const {
 #pragma unroll
-    for (int k = 0; k < D; ++k) v[k] *= s;
+    for (int k = 0; k < D; ++k) v[k] *= pc.s;
   }
   __device__ __forceinline__ void gradx(const Ctx&, const T (&)[D], const T (&)[D], T (&g)[D]) const {
 #pragma unroll
     for (int k = 0; k < D; ++k) g[k] = T(0);
   }
-  __device__ __forceinline__ double H64(const double (&)[D], const double (&p)[D]) const {
+  __device__ __forceinline__ double H64(const T (&)[D], const T (&p)[D]) const {
     double h = 0.0;
 #pragma unroll
-    for (int k = 0; k < D; ++k) h += p[k] * p[k];
+    for (int k = 0; k < D; ++k) h += (double)p[k] * (double)p[k];
     return 0.5 * h;
   }
 };
@@ -106,25 +109,37 @@ struct FamQuadcopter {
     thrust<T>(x[3], x[4], x[5], c.a, c.J);
   }
 
+  // Per-point constants of the prox: al = 1 + lam eps and the reciprocals used below.
+  struct PC { T lam, ial, irate, lam_ah, lam_gz, al; };
+  __device__ __forceinline__ PC point(T lam) const {
+    PC c;
+    c.lam = lam;
+    c.al = T(1) + lam * eps;
+    c.ial = T(1) / c.al;
+    c.irate = T(1) / (c.al + lam);
+    c.lam_ah = lam * ah;
+    c.lam_gz = lam * gz;
+    return c;
+  }
+
   // ((1 + lam eps) I + lam B B^T) p = v - lam f0.  Rows 0-5 and 9-11 decouple;
   // rows 6-8 are a rank-1 update of a scaled identity (Sherman-Morrison).
-  __device__ __forceinline__ void prox(const Ctx& c, const T (&x)[D], T (&v)[D], T lam) const {
-    const T al = T(1) + lam * eps;
-    const T ial = T(1) / al;
+  __device__ __forceinline__ void prox(const Ctx& c, const PC& pc, const T (&x)[D],
+                                       T (&v)[D]) const {
+    const T lam = pc.lam, ial = pc.ial;
 #pragma unroll
     for (int k = 0; k < 3; ++k) v[k] = (v[k] - lam * x[6 + k]) * ial;
 #pragma unroll
     for (int k = 0; k < 3; ++k) v[3 + k] = (v[3 + k] - lam * x[9 + k]) * ial;
-    const T irate = T(1) / (al + lam);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v[9 + k] *= irate;
-    T w0 = v[6] - lam * ah * c.a[0];
-    T w1 = v[7] - lam * ah * c.a[1];
-    T w2 = v[8] - lam * (ah * c.a[2] - gz);
+    for (int k = 0; k < 3; ++k) v[9 + k] *= pc.irate;
+    const T w0 = v[6] - pc.lam_ah * c.a[0];
+    const T w1 = v[7] - pc.lam_ah * c.a[1];
+    const T w2 = v[8] - (pc.lam_ah * c.a[2] - pc.lam_gz);
     const T b0 = c.a[0] * m_inv, b1 = c.a[1] * m_inv, b2 = c.a[2] * m_inv;
     const T bb = b0 * b0 + b1 * b1 + b2 * b2;
     const T bw = b0 * w0 + b1 * w1 + b2 * w2;
-    const T f = fdiv<T>(lam * bw, al + lam * bb);
+    const T f = fdiv<T>(lam * bw, pc.al + lam * bb);
     v[6] = (w0 - f * b0) * ial;
     v[7] = (w1 - f * b1) * ial;
     v[8] = (w2 - f * b2) * ial;
@@ -144,20 +159,21 @@ struct FamQuadcopter {
     for (int k = 0; k < 3; ++k) g[9 + k] = p[3 + k];
   }
 
-  __device__ __forceinline__ double H64(const double (&x)[D], const double (&p)[D]) const {
+  __device__ __forceinline__ double H64(const T (&x)[D], const T (&p)[D]) const {
     double a[3], J[9];
-    thrust<double>(x[3], x[4], x[5], a, J);
-    double h = 0.0;
+    thrust<double>((double)x[3], (double)x[4], (double)x[5], a, J);
+    double h = 0.0, pp = 0.0;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) h += p[k] * x[6 + k] + p[3 + k] * x[9 + k];
-    const double s = a[0] * p[6] + a[1] * p[7] + a[2] * p[8];
-    h += ah64 * s - gz64 * p[8];
+    for (int k = 0; k < 3; ++k)
+      h += (double)p[k] * (double)x[6 + k] + (double)p[3 + k] * (double)x[9 + k];
+    const double s = a[0] * (double)p[6] + a[1] * (double)p[7] + a[2] * (double)p[8];
+    h += ah64 * s - gz64 * (double)p[8];
     const double u0 = s / m64;
-    double pp = 0.0, rr = 0.0;
 #pragma unroll
-    for (int k = 0; k < D; ++k) pp += p[k] * p[k];
+    for (int k = 0; k < D; ++k) pp += (double)p[k] * (double)p[k];
+    double rr = 0.0;
 #pragma unroll
-    for (int k = 9; k < 12; ++k) rr += p[k] * p[k];
+    for (int k = 9; k < 12; ++k) rr += (double)p[k] * (double)p[k];
     return h + 0.5 * (u0 * u0 + rr) + 0.5 * eps64 * pp;
   }
 };
@@ -184,10 +200,12 @@ struct FamTanhDrift {
       c.a[i] = tanh_t<T>(y);
     }
   }
-  __device__ __forceinline__ void prox(const Ctx& c, const T (&)[D], T (&v)[D], T lam) const {
-    const T s = T(1) / (T(1) + lam);
+  struct PC { T lam, s; };
+  __device__ __forceinline__ PC point(T lam) const { return PC{lam, T(1) / (T(1) + lam)}; }
+  __device__ __forceinline__ void prox(const Ctx& c, const PC& pc, const T (&)[D],
+                                       T (&v)[D]) const {
 #pragma unroll
-    for (int k = 0; k < D; ++k) v[k] = (v[k] - lam * c.a[k]) * s;
+    for (int k = 0; k < D; ++k) v[k] = (v[k] - pc.lam * c.a[k]) * pc.s;
   }
   __device__ __forceinline__ void gradx(const Ctx& c, const T (&)[D], const T (&p)[D],
                                         T (&g)[D]) const {
@@ -202,14 +220,15 @@ struct FamTanhDrift {
       g[i] = s;
     }
   }
-  __device__ __forceinline__ double H64(const double (&x)[D], const double (&p)[D]) const {
+  __device__ __forceinline__ double H64(const T (&x)[D], const T (&p)[D]) const {
     double h = 0.0;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       double y = 0.0;
 #pragma unroll
-      for (int k = 0; k < D; ++k) y += A64[i * D + k] * x[k];
-      h += p[i] * tanh(y) + 0.5 * p[i] * p[i];
+      for (int k = 0; k < D; ++k) y += A64[i * D + k] * (double)x[k];
+      const double pi = (double)p[i];
+      h += pi * tanh(y) + 0.5 * pi * pi;
     }
     return h;
   }

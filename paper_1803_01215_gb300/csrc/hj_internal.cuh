@@ -18,6 +18,10 @@ struct SolveArgs {
   int64_t B;
   int32_t N, d;
   double sigma, tau, theta, tol;
+  // The same step sizes rounded once to the iterate type on the host, so the
+  // iteration loop holds no double-derived value the compiler could recompute
+  // there (FP64 instructions are ~64x the cost of FP32 ones on this GPU).
+  T sigma_t, tau_t, theta_t;
   int32_t max_iter, check_every, inner_steps;
   uint64_t seed;
   double radius;
@@ -38,6 +42,38 @@ struct SolveArgs {
   const double* A64;     // tanh drift: [d][d] row-major in double (value epilogue)
   double qc_m, qc_ah, qc_gz, qc_eps;   // quadcopter parameters
   unsigned long long* counter;        // work counter (zeroed before launch)
+  // Ragged batches: the launch processes items i = 0..B-1, point id idx[i]
+  // (idx null: id = i).  Per-point N (Nv null: N), xq offset in doubles
+  // (xq_off null: id*d) and trajectory offset in elements (traj_off null:
+  // id*(N+1)*d).  V, iters, status and t are indexed by the point id.
+  const int32_t* idx;
+  const int32_t* Nv;
+  const int64_t* xq_off;
+  const int64_t* traj_off;
+};
+
+template <typename T>
+struct PointRef {
+  int64_t id;
+  int N;
+  const double* xq;
+  size_t traj;      // element offset of the point's [N+1][d] block
+};
+
+template <typename T>
+__device__ __forceinline__ PointRef<T> point_ref(const SolveArgs<T>& a, int64_t item) {
+  PointRef<T> r;
+  r.id = a.idx ? (int64_t)a.idx[item] : item;
+  r.N = a.Nv ? a.Nv[r.id] : a.N;
+  r.xq = a.xq + (a.xq_off ? a.xq_off[r.id] : r.id * (int64_t)a.d);
+  r.traj = a.traj_off ? (size_t)a.traj_off[r.id] : (size_t)r.id * (size_t)(r.N + 1) * a.d;
+  return r;
+}
+
+// Launch shape of the register-resident kernel: G warps per point, NPL time
+// nodes per lane; a point needs N <= 32 * G * NPL.
+struct WarpConfig {
+  int G, NPL;
 };
 
 // splitmix64 (Vigna 2015) evaluated at a counter: z = seed + (c + 1) * golden,
@@ -55,7 +91,8 @@ __device__ __forceinline__ double uniform_pm1(uint64_t seed, uint64_t point, uin
   return 2.0 * u - 1.0;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename U>
+__device__ __forceinline__ U warp_sum(U v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
@@ -68,11 +105,22 @@ __device__ __forceinline__ bool finite_val(T v) { return isfinite(v); }
 // Each returns HJ_OK, HJ_ERR_UNSUPPORTED (no instantiation for this shape) or
 // HJ_ERR_CUDA.
 template <typename T>
-hj_status launch_warp_solver(int family, const SolveArgs<T>& a, cudaStream_t s);
+hj_status launch_warp_solver(int family, const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 template <typename T>
-hj_status launch_td_cta_solver(const SolveArgs<T>& a, cudaStream_t s);
-// Shared memory the tanh-drift CTA kernel needs for (d, N); 0 if unsupported.
+hj_status launch_warp_quadratic(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 template <typename T>
-size_t td_cta_smem_bytes(int d, int N);
+hj_status launch_warp_quadcopter(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
+template <typename T>
+hj_status launch_warp_tanh(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
+// Default launch shape for (family, d, Nmax); {0, 0} when no warp kernel fits.
+WarpConfig default_warp_config(int family, int d, int Nmax, bool fp64);
+// Whether the warp kernel has an instantiation for (family, d, cfg, precision).
+bool warp_config_available(int family, int d, WarpConfig cfg, bool fp64);
+// Shared-memory CTA kernel: tanh drift (drift = true) or H = |p|^2/2 (drift = false).
+template <typename T>
+hj_status launch_td_cta_solver(const SolveArgs<T>& a, bool drift, cudaStream_t s);
+// Shared memory that kernel needs for (d, N); 0 if it does not fit.
+template <typename T>
+size_t td_cta_smem_bytes(int d, int N, bool drift);
 
 }  // namespace hj

@@ -1,5 +1,7 @@
 // Shared-memory batched PDHG for the tanh-drift Hamiltonian at larger d
-// (H = <p, tanh(A x)> + |p|^2/2, Algorithm 1 with the Section 5.3 updates).
+// (H = <p, tanh(A x)> + |p|^2/2, Algorithm 1 with the Section 5.3 updates);
+// with DRIFT = false the same kernel serves H = |p|^2/2 at any d (the products
+// are skipped: a = 0, G = 0).
 //
 // One CTA solves one query point at a time; the iterates live in shared memory
 // coordinate-major (X[k][j], k = coordinate, j = time node 0..N), so a thread
@@ -63,16 +65,16 @@ struct Layout {
 
 // TWO: keep both A^T and A in shared memory (vector loads in both products);
 // otherwise only A, and the first product reads it with strided scalar loads.
-template <typename T, bool TWO>
+template <typename T, bool TWO, bool DRIFT>
 __global__ void __launch_bounds__(512)
 lax_td_cta_kernel(const SolveArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int d = a.d, N = a.N;
-  const Layout L(d, N);
-  const int dp = L.dp, Np = L.Np;
+  const int d = a.d;
+  const Layout L(d, a.N);                                 // a.N: the largest N of the launch
+  const int dp = L.dp;
   T* Am = reinterpret_cast<T*>(smem_raw);                 // Am[k*dp + i] = A[k][i]
   T* At = TWO ? Am + L.a_elems : Am;                      // At[k*dp + i] = A[i][k]
-  T* X = (TWO ? At + L.a_elems : Am + L.a_elems);
+  T* X = DRIFT ? (TWO ? At + L.a_elems : Am + L.a_elems) : Am;   // no A without drift
   T* P = X + L.s_elems;
   T* Z = P + L.s_elems;
   T* Wk = Z + L.s_elems;
@@ -82,40 +84,50 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
 
-  for (int e = tid; e < d * dp; e += nthr) {
-    const int k = e / dp, i = e - k * dp;
-    Am[e] = (i < d) ? a.A[k * d + i] : T(0);
-    if (TWO) At[e] = (i < d) ? a.At[k * d + i] : T(0);
+  if (DRIFT) {
+    for (int e = tid; e < d * dp; e += nthr) {
+      const int k = e / dp, i = e - k * dp;
+      Am[e] = (i < d) ? a.A[k * d + i] : T(0);
+      if (TWO) At[e] = (i < d) ? a.At[k * d + i] : T(0);
+    }
   }
 
-  const int tilesI = dp / kTI, tilesJ = Np / kTJ;
-  const int ntiles = tilesI * tilesJ;
-  const T sig = T(a.sigma), tau = T(a.tau), th = T(a.theta);
+  const T sig = a.sigma_t, tau = a.tau_t, th = a.theta_t;
 
   for (;;) {
     __syncthreads();
     if (tid == 0) s_point = atomicAdd(a.counter, 1ull);
     __syncthreads();
-    const int64_t b = (int64_t)s_point;
-    if (b >= a.B) break;
-    const double delta = a.t[b] / N;
-    const T lam = T(a.sigma * delta), taud = T(a.tau * delta);
+    const int64_t item = (int64_t)s_point;
+    if (item >= a.B) break;
+    const PointRef<T> ref = point_ref(a, item);
+    const int64_t b = ref.id;
+    const int N = ref.N;
+    if (N < 1 || N > a.N) {                                // the host never routes such a point here
+      if (tid == 0) { a.status[b] = HJ_POINT_INVALID; a.iters[b] = 0; a.V[b] = 0.0; }
+      continue;
+    }
+    const int Np = round4(N + 1);
+    const int tilesI = dp / kTI, tilesJ = Np / kTJ;
+    const int ntiles = tilesI * tilesJ;
+    const double delta = a.t[b] / N;                      // value epilogue only
+    const T delta_t = T(a.t[b]) / T(N);
+    const T lam = sig * delta_t, taud = tau * delta_t;
     const T ilam = T(1) / (T(1) + lam);
     const uint64_t pt = (uint64_t)(a.point_offset + b);
-    const size_t stride = (size_t)(N + 1) * d;
 
     // ---- initial iterate (Section 6 random guess, or a warm start)
     for (int e = tid; e < dp * Np; e += nthr) {
       const int k = e / Np, j = e - k * Np;
       T xv = T(0), pv = T(0);
       if (k < d && j <= N) {
-        const double xq = a.xq[b * d + k];
+        const double xq = ref.xq[k];
         if (a.warm_x == nullptr) {
           xv = (j < N) ? T(xq + a.radius * uniform_pm1(a.seed, pt, 0, j, k)) : T(xq);
           pv = (j >= 1) ? T(a.radius * uniform_pm1(a.seed, pt, 1, j, k)) : T(0);
         } else {
-          xv = (j < N) ? a.warm_x[b * stride + (size_t)j * d + k] : T(xq);
-          pv = (j >= 1) ? a.warm_p[b * stride + (size_t)j * d + k] : T(0);
+          xv = (j < N) ? a.warm_x[ref.traj + (size_t)j * d + k] : T(xq);
+          pv = (j >= 1) ? a.warm_p[ref.traj + (size_t)j * d + k] : T(0);
         }
       }
       X[e] = xv; P[e] = pv; Z[e] = xv; Wk[e] = T(0);
@@ -137,7 +149,7 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
 #pragma unroll
           for (int c = 0; c < kTJ; ++c) acc[r][c] = T(0);
 #pragma unroll 4
-        for (int k = 0; k < d; ++k) {
+        for (int k = 0; k < (DRIFT ? d : 0); ++k) {
           T av[kTI], xv[kTJ];
           if (TWO) {
             Vec4<T>::load(At + k * dp + i0, av);
@@ -159,7 +171,7 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
             const int j = j0 + c;
             if (i < d && j >= 1 && j <= N) {
               const int e = i * Np + j;
-              const T av = tanh_c<T>(acc[r][c]);
+              const T av = DRIFT ? tanh_c<T>(acc[r][c]) : T(0);
               const T v = P[e] + sig * (Z[e] - Z[e - 1]);
               const T pn = (v - lam * av) * ilam;
               if (chk) { const T df = pn - P[e]; rp += df * df; }
@@ -179,7 +191,7 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
 #pragma unroll
           for (int c = 0; c < kTJ; ++c) acc[r][c] = T(0);
 #pragma unroll 4
-        for (int k = 0; k < d; ++k) {
+        for (int k = 0; k < (DRIFT ? d : 0); ++k) {
           T av[kTI], wv[kTJ];
           Vec4<T>::load(Am + k * dp + i0, av);
           Vec4<T>::load(Wk + k * Np + j0, wv);
@@ -215,7 +227,7 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
         X[e] = xn;
       }
       if (chk) {
-        const double sx = warp_sum((double)rx), sp = warp_sum((double)rp);
+        const double sx = (double)warp_sum<T>(rx), sp = (double)warp_sum<T>(rp);
         if (lane == 0) { red[2 * warp] = sx; red[2 * warp + 1] = sp; }
       }
       __syncthreads();
@@ -231,18 +243,22 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
     double acc = 0.0;
     for (int e = tid; e < d * N; e += nthr) {
       const int j = 1 + e / d, i = e - (j - 1) * d;
-      const double* Ar = a.A64 + (size_t)i * d;
-      double y = 0.0;
-      for (int k = 0; k < d; ++k) y += Ar[k] * (double)X[k * Np + j];
+      double th_y = 0.0;
+      if (DRIFT) {
+        const double* Ar = a.A64 + (size_t)i * d;
+        double y = 0.0;
+        for (int k = 0; k < d; ++k) y += Ar[k] * (double)X[k * Np + j];
+        th_y = tanh(y);
+      }
       const double pv = (double)P[i * Np + j];
       const double dx = (double)X[i * Np + j] - (double)X[i * Np + j - 1];
-      acc += pv * dx - delta * (pv * tanh(y) + 0.5 * pv * pv);
+      acc += pv * dx - delta * (pv * th_y + 0.5 * pv * pv);
     }
     if (tid < d) {
       const double e0 = (double)X[tid * Np] - a.c[tid];
       acc += 0.5 * a.W2[tid] * e0 * e0;
     }
-    acc = warp_sum(acc);
+    acc = warp_sum<double>(acc);
     __syncthreads();
     if (lane == 0) red[warp] = acc;
     __syncthreads();
@@ -256,22 +272,23 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
     if (a.traj_x != nullptr || a.traj_p != nullptr) {
       for (int e = tid; e < (N + 1) * d; e += nthr) {
         const int j = e / d, i = e - j * d;
-        if (a.traj_x != nullptr) a.traj_x[b * stride + e] = X[i * Np + j];
-        if (a.traj_p != nullptr) a.traj_p[b * stride + e] = (j == 0) ? T(0) : P[i * Np + j];
+        if (a.traj_x != nullptr) a.traj_x[ref.traj + e] = X[i * Np + j];
+        if (a.traj_p != nullptr) a.traj_p[ref.traj + e] = (j == 0) ? T(0) : P[i * Np + j];
       }
     }
   }
 }
 
 template <typename T, bool TWO>
-size_t smem_bytes(int d, int N) {
+size_t smem_bytes(int d, int N, bool drift) {
   const Layout L(d, N);
-  return ((TWO ? 2 : 1) * L.a_elems + 4 * L.s_elems) * sizeof(T) + 2 * 16 * sizeof(double);
+  const size_t na = drift ? (TWO ? 2 : 1) : 0;
+  return (na * L.a_elems + 4 * L.s_elems) * sizeof(T) + 2 * 16 * sizeof(double);
 }
 
-template <typename T, bool TWO>
+template <typename T, bool TWO, bool DRIFT>
 hj_status launch(const SolveArgs<T>& a, cudaStream_t s, size_t smem) {
-  auto kern = lax_td_cta_kernel<T, TWO>;
+  auto kern = lax_td_cta_kernel<T, TWO, DRIFT>;
   int dev = 0, nsm = 0, max_optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return HJ_ERR_CUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -302,27 +319,31 @@ hj_status launch(const SolveArgs<T>& a, cudaStream_t s, size_t smem) {
 }  // namespace
 
 template <typename T>
-size_t td_cta_smem_bytes(int d, int N) {
-  const size_t two = smem_bytes<T, true>(d, N);
+size_t td_cta_smem_bytes(int d, int N, bool drift) {
+  const size_t two = smem_bytes<T, true>(d, N, drift);
   if (two <= 227u * 1024u) return two;
-  const size_t one = smem_bytes<T, false>(d, N);
+  const size_t one = smem_bytes<T, false>(d, N, drift);
   return one <= 227u * 1024u ? one : 0;
 }
 
 template <typename T>
-hj_status launch_td_cta_solver(const SolveArgs<T>& a, cudaStream_t s) {
+hj_status launch_td_cta_solver(const SolveArgs<T>& a, bool drift, cudaStream_t s) {
   if (a.d < 1 || a.d > kMaxD || a.N < 1 || a.N > kMaxN || a.inner_steps != 1)
     return HJ_ERR_UNSUPPORTED;
-  const size_t two = smem_bytes<T, true>(a.d, a.N);
-  if (two <= 227u * 1024u) return launch<T, true>(a, s, two);
-  const size_t one = smem_bytes<T, false>(a.d, a.N);
-  if (one <= 227u * 1024u) return launch<T, false>(a, s, one);
+  if (!drift) {
+    const size_t sm = smem_bytes<T, false>(a.d, a.N, false);
+    return sm <= 227u * 1024u ? launch<T, false, false>(a, s, sm) : HJ_ERR_UNSUPPORTED;
+  }
+  const size_t two = smem_bytes<T, true>(a.d, a.N, true);
+  if (two <= 227u * 1024u) return launch<T, true, true>(a, s, two);
+  const size_t one = smem_bytes<T, false>(a.d, a.N, true);
+  if (one <= 227u * 1024u) return launch<T, false, true>(a, s, one);
   return HJ_ERR_UNSUPPORTED;
 }
 
-template size_t td_cta_smem_bytes<float>(int, int);
-template size_t td_cta_smem_bytes<double>(int, int);
-template hj_status launch_td_cta_solver<float>(const SolveArgs<float>&, cudaStream_t);
-template hj_status launch_td_cta_solver<double>(const SolveArgs<double>&, cudaStream_t);
+template size_t td_cta_smem_bytes<float>(int, int, bool);
+template size_t td_cta_smem_bytes<double>(int, int, bool);
+template hj_status launch_td_cta_solver<float>(const SolveArgs<float>&, bool, cudaStream_t);
+template hj_status launch_td_cta_solver<double>(const SolveArgs<double>&, bool, cudaStream_t);
 
 }  // namespace hj

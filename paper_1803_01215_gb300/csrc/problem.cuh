@@ -1,0 +1,148 @@
+// Problem handle and solve helpers shared by the C ABI entry points.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "hj_internal.cuh"
+#include "hjpdhg.h"
+
+struct hj_problem_s {
+  int family = 0, d = 0, device = 0;
+  double qc[4] = {0, 0, 0, 0};        // m, a_h, g_z, eps
+  double* W2 = nullptr;               // [d]
+  double* c = nullptr;                // [d]
+  float* Af = nullptr;                // [d][d]
+  float* Atf = nullptr;               // [d][d]
+  double* Ad = nullptr;               // [d][d]
+  double* Atd = nullptr;              // [d][d]
+  unsigned long long* counter = nullptr;
+  // Launch shapes chosen by hj_autotune / hj_set_launch_shape, keyed by
+  // (precision, N); absent keys use the default shape.
+  std::map<std::pair<int, int>, hj::WarpConfig> shapes;
+  std::mutex mu;
+};
+
+namespace hj_detail {
+
+inline bool all_finite(const double* v, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+template <typename T>
+hj_status upload(T** dst, const T* src, size_t n) {
+  if (cudaMalloc(reinterpret_cast<void**>(dst), n * sizeof(T)) != cudaSuccess) return HJ_ERR_OOM;
+  if (cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return HJ_ERR_CUDA;
+  return HJ_OK;
+}
+
+inline void release(hj_problem_s* p) {
+  cudaFree(p->W2); cudaFree(p->c);
+  cudaFree(p->Af); cudaFree(p->Atf); cudaFree(p->Ad); cudaFree(p->Atd);
+  cudaFree(p->counter);
+  delete p;
+}
+
+inline hj::WarpConfig shape_for(hj_problem_s* p, int precision, int N) {
+  {
+    std::lock_guard<std::mutex> g(p->mu);
+    auto it = p->shapes.find({precision, N});
+    if (it != p->shapes.end()) return it->second;
+  }
+  return hj::default_warp_config(p->family, p->d, N, precision == HJ_PREC_FP64);
+}
+
+// Which kernel serves a request: the register-resident warp kernel when it has
+// an instantiation for (family, d), else the shared-memory CTA kernel (tanh
+// drift at any d, or H = |p|^2/2 at any d).
+template <typename T>
+hj_status dispatch(hj_problem_s* p, const hj::SolveArgs<T>& a, hj::WarpConfig cfg,
+                   cudaStream_t s) {
+  if (cfg.G > 0) {
+    const hj_status r = hj::launch_warp_solver<T>(p->family, a, cfg, s);
+    if (r != HJ_ERR_UNSUPPORTED) return r;
+  }
+  if (p->family == HJ_FAMILY_TANH_DRIFT) return hj::launch_td_cta_solver<T>(a, true, s);
+  if (p->family == HJ_FAMILY_QUADRATIC) return hj::launch_td_cta_solver<T>(a, false, s);
+  return HJ_ERR_UNSUPPORTED;
+}
+
+template <typename T>
+void fill_args(hj::SolveArgs<T>& a, const hj_problem_s* prob, int64_t B, int32_t N,
+               const hj_solver_opts& o, const double* xq, const double* t, double* V,
+               int32_t* iters, int8_t* status, void* traj_x, void* traj_p,
+               const void* warm_x, const void* warm_p);
+
+template <>
+inline void fill_args<float>(hj::SolveArgs<float>& a, const hj_problem_s* prob, int64_t B, int32_t N,
+                      const hj_solver_opts& o, const double* xq, const double* t, double* V,
+                      int32_t* iters, int8_t* status, void* traj_x, void* traj_p,
+                      const void* warm_x, const void* warm_p) {
+  a.A = prob->Af; a.At = prob->Atf;
+  a.traj_x = static_cast<float*>(traj_x); a.traj_p = static_cast<float*>(traj_p);
+  a.warm_x = static_cast<const float*>(warm_x); a.warm_p = static_cast<const float*>(warm_p);
+  (void)B; (void)N; (void)o; (void)xq; (void)t; (void)V; (void)iters; (void)status;
+}
+
+template <>
+inline void fill_args<double>(hj::SolveArgs<double>& a, const hj_problem_s* prob, int64_t B, int32_t N,
+                       const hj_solver_opts& o, const double* xq, const double* t, double* V,
+                       int32_t* iters, int8_t* status, void* traj_x, void* traj_p,
+                       const void* warm_x, const void* warm_p) {
+  a.A = prob->Ad; a.At = prob->Atd;
+  a.traj_x = static_cast<double*>(traj_x); a.traj_p = static_cast<double*>(traj_p);
+  a.warm_x = static_cast<const double*>(warm_x); a.warm_p = static_cast<const double*>(warm_p);
+  (void)B; (void)N; (void)o; (void)xq; (void)t; (void)V; (void)iters; (void)status;
+}
+
+template <typename T>
+hj::SolveArgs<T> make_args(const hj_problem_s* prob, int64_t B, int32_t N,
+                           const hj_solver_opts& o, const double* xq, const double* t,
+                           double* V, int32_t* iters, int8_t* status, void* traj_x,
+                           void* traj_p, const void* warm_x, const void* warm_p) {
+  hj::SolveArgs<T> a{};
+  a.B = B; a.N = N; a.d = prob->d;
+  a.sigma = o.sigma; a.tau = o.tau; a.theta = o.theta; a.tol = o.tol;
+  a.sigma_t = T(o.sigma); a.tau_t = T(o.tau); a.theta_t = T(o.theta);
+  a.max_iter = o.max_iter; a.check_every = o.check_every; a.inner_steps = o.inner_steps;
+  a.seed = o.seed; a.radius = o.init_radius; a.point_offset = o.point_offset;
+  a.xq = xq; a.t = t; a.V = V; a.iters = iters; a.status = status;
+  a.W2 = prob->W2; a.c = prob->c; a.A64 = prob->Ad;
+  a.qc_m = prob->qc[0]; a.qc_ah = prob->qc[1]; a.qc_gz = prob->qc[2]; a.qc_eps = prob->qc[3];
+  a.counter = prob->counter;
+  fill_args<T>(a, prob, B, N, o, xq, t, V, iters, status, traj_x, traj_p, warm_x, warm_p);
+  return a;
+}
+
+inline hj_status check_opts(const hj_solver_opts& o) {
+  if (!(std::isfinite(o.sigma) && o.sigma > 0) || !(std::isfinite(o.tau) && o.tau > 0))
+    return HJ_ERR_INVALID_ARG;
+  if (!(o.theta >= 0.0 && o.theta <= 1.0) || !(o.tol >= 0.0) || !std::isfinite(o.tol))
+    return HJ_ERR_INVALID_ARG;
+  if (o.max_iter < 1 || o.check_every < 1 || o.inner_steps < 1) return HJ_ERR_INVALID_ARG;
+  if (o.precision != HJ_PREC_FP32 && o.precision != HJ_PREC_FP64) return HJ_ERR_INVALID_ARG;
+  if (!(std::isfinite(o.init_radius) && o.init_radius >= 0.0) || o.point_offset < 0)
+    return HJ_ERR_INVALID_ARG;
+  if (4.0 * o.sigma * o.tau >= 1.0) return HJ_ERR_STEP_SIZE;
+  return HJ_OK;
+}
+
+template <typename T>
+hj_status run_solve(hj_problem_s* prob, int64_t B, int32_t N, const hj_solver_opts& o,
+                    hj::WarpConfig cfg, const double* xq, const double* t, double* V,
+                    int32_t* iters, int8_t* status, void* traj_x, void* traj_p,
+                    const void* warm_x, const void* warm_p, cudaStream_t s) {
+  if (cudaMemsetAsync(prob->counter, 0, sizeof(unsigned long long), s) != cudaSuccess)
+    return HJ_ERR_CUDA;
+  const hj::SolveArgs<T> a = make_args<T>(prob, B, N, o, xq, t, V, iters, status, traj_x,
+                                          traj_p, warm_x, warm_p);
+  return dispatch<T>(prob, a, cfg, s);
+}
+
+}  // namespace hj_detail

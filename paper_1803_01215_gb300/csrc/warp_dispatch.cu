@@ -1,0 +1,51 @@
+// Launch-shape selection for the register-resident solver.
+#include "hj_internal.cuh"
+
+namespace hj {
+
+namespace {
+bool warp_family_has(int family, int d) {
+  switch (family) {
+    case HJ_FAMILY_QUADRATIC: return d >= 1 && d <= 4;
+    case HJ_FAMILY_QUADCOPTER: return d == 12;
+    case HJ_FAMILY_TANH_DRIFT: return d == 2 || d == 4;
+    default: return false;
+  }
+}
+}  // namespace
+
+bool warp_config_available(int family, int d, WarpConfig c, bool fp64) {
+  if (!warp_family_has(family, d)) return false;
+  if (c.G != 1 && c.G != 2 && c.G != 4 && c.G != 8) return false;
+  return fp64 ? c.NPL == 1 : (c.NPL == 1 || c.NPL == 2);
+}
+
+WarpConfig default_warp_config(int family, int d, int Nmax, bool fp64) {
+  if (!warp_family_has(family, d) || Nmax < 1 || Nmax > kMaxN) return WarpConfig{0, 0};
+  if (fp64) {
+    int G = 1;
+    while (32 * G < Nmax) G *= 2;
+    return WarpConfig{G, 1};
+  }
+  if (Nmax <= 32) return WarpConfig{1, 1};
+  if (Nmax <= 64) return WarpConfig{1, 2};
+  if (Nmax <= 128) return WarpConfig{2, 2};
+  return WarpConfig{4, 2};
+}
+
+template <typename T>
+hj_status launch_warp_solver(int family, const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s) {
+  if (!warp_config_available(family, a.d, cfg, sizeof(T) == 8)) return HJ_ERR_UNSUPPORTED;
+  if (a.N > 32 * cfg.G * cfg.NPL) return HJ_ERR_UNSUPPORTED;
+  switch (family) {
+    case HJ_FAMILY_QUADRATIC: return launch_warp_quadratic<T>(a, cfg, s);
+    case HJ_FAMILY_QUADCOPTER: return launch_warp_quadcopter<T>(a, cfg, s);
+    case HJ_FAMILY_TANH_DRIFT: return launch_warp_tanh<T>(a, cfg, s);
+    default: return HJ_ERR_UNSUPPORTED;
+  }
+}
+
+template hj_status launch_warp_solver<float>(int, const SolveArgs<float>&, WarpConfig, cudaStream_t);
+template hj_status launch_warp_solver<double>(int, const SolveArgs<double>&, WarpConfig, cudaStream_t);
+
+}  // namespace hj

@@ -1,0 +1,17 @@
+// Instantiations of the register-resident solver for the Quadcopter family.
+#include "warp_solver.cuh"
+
+namespace hj {
+
+template <typename T>
+hj_status launch_warp_quadcopter(const SolveArgs<T>& a, WarpConfig c, cudaStream_t s) {
+  switch (a.d) {
+    case 12: return launch_warp_shape<T, FamQuadcopter, 12>(a, c, s);
+    default: return HJ_ERR_UNSUPPORTED;
+  }
+}
+
+template hj_status launch_warp_quadcopter<float>(const SolveArgs<float>&, WarpConfig, cudaStream_t);
+template hj_status launch_warp_quadcopter<double>(const SolveArgs<double>&, WarpConfig, cudaStream_t);
+
+}  // namespace hj

@@ -98,3 +98,45 @@ def subset(w, idx):
     out["point_index"] = (np.asarray(base)[idx] if base is not None
                           else idx.astype(np.int64))
     return out
+
+
+def ragged_mix(B=100000, seed=6, sigma=1.4):
+    """Ragged batch: thirds of tanh drift d = 4, the 12-D quadcopter and tanh drift
+    d = 32 (problem parameters from the generators above), each point with its own
+    N ~ U{16..256} and the horizon its generator draws.  Returns
+        problems  list of three problem dicts (family, d, dyn, W, c)
+        prob_of   [B] int32 problem index,  N_of [B] int32,
+        xq        list of B arrays (d_b,),  t [B]
+    plus the shared solver options."""
+    r = _rng(seed)
+    gens = [tanh_drift(4, B=1, seed=seed + 100), quadcopter(B=1, seed=seed + 200),
+            tanh_drift(32, B=1, seed=seed + 300)]
+    problems = [{k: g[k] for k in ("family", "d", "dyn", "W", "c")} for g in gens]
+    prob_of = r.integers(0, 3, size=B).astype(np.int32)
+    N_of = r.integers(16, 257, size=B).astype(np.int32)
+    xq, t = [], np.empty(B)
+    for b in range(B):
+        k = prob_of[b]
+        if k == 1:
+            xq.append(0.5 * r.standard_normal(12))
+            t[b] = 1.0
+        else:
+            xq.append(r.standard_normal(problems[k]["d"]))
+            t[b] = r.uniform(0.5, 2.0)
+    return dict(problems=problems, prob_of=prob_of, N_of=N_of, xq=xq, t=t,
+                sigma=sigma, tau=0.24 / sigma, tol=1e-8, max_iter=20000, check_every=16,
+                seed=seed, init_radius=0.1)
+
+
+def ragged_group(rw, k, N, idx=None):
+    """The points of ragged workload `rw` with problem k and time steps N (or the
+    given global indices) as a uniform workload dict for the oracle; global point
+    indices are kept so the counter-based initial guess matches."""
+    if idx is None:
+        idx = np.where((rw["prob_of"] == k) & (rw["N_of"] == N))[0]
+    out = dict(rw["problems"][k])
+    out.update(xq=np.stack([rw["xq"][i] for i in idx]), t=rw["t"][idx], N=int(N),
+               point_index=np.asarray(idx, dtype=np.int64),
+               **{key: rw[key] for key in ("sigma", "tau", "tol", "max_iter", "check_every",
+                                           "seed", "init_radius")})
+    return out

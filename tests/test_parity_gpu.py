@@ -243,3 +243,55 @@ def test_error_codes():
     with pytest.raises(binding.HJError) as e:
         binding.solve_batch(prob, xq, t, 300, binding.make_opts(sigma=1.0, tau=0.2))
     assert e.value.code == binding.HJ_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------- launch shapes and autotuner
+@pytest.mark.parametrize("family,d,N", [("quadcopter", 12, 64), ("tanh_drift", 4, 100),
+                                        ("quadratic", 3, 120)])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_every_launch_shape_gives_identical_iterates(family, d, N, precision):
+    """The lane/warp mapping (G warps per point, NPL nodes per lane) changes no
+    formula of a node: after K iterations the iterates agree across shapes to the
+    rounding level (instantiations may contract a*b+c into an FMA differently),
+    and the values agree to FP64 summation order."""
+    from paper_1803_01215_gb300 import binding
+    w = _custom(family, d, N, B=21)
+    prob = binding.Problem.from_workload(w)
+    xq = torch.as_tensor(w["xq"], device="cuda")
+    t = torch.as_tensor(w["t"], device="cuda")
+    opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], tol=0.0, max_iter=60,
+                             check_every=60, precision=precision, seed=w["seed"])
+    outs = []
+    for G in (1, 2, 4, 8):
+        for npl in ((1, 2) if precision == "fp32" else (1,)):
+            if N > 32 * G * npl:
+                continue
+            binding.set_launch_shape(prob, precision, N, G, npl)
+            assert binding.get_launch_shape(prob, precision, N) == (G, npl)
+            o = binding.solve_batch(prob, xq, t, N, opts, return_traj=True)
+            outs.append(((G, npl), {k: v.cpu().numpy() for k, v in o.items()}))
+    assert len(outs) >= 2
+    ref = outs[0][1]
+    o = oracle_same_stop(w, tol=0.0, max_iter=60, check_every=60)
+    assert np.max(np.abs(ref["traj_x"] - o["x"])) <= (1e-10 if precision == "fp64" else 1e-4)
+    rt = 1e-13 if precision == "fp64" else 1e-5
+    for shape, out in outs[1:]:
+        np.testing.assert_allclose(out["traj_x"], ref["traj_x"], rtol=rt, atol=rt, err_msg=str(shape))
+        np.testing.assert_allclose(out["traj_p"], ref["traj_p"], rtol=rt, atol=rt, err_msg=str(shape))
+        assert np.max(value_err(out["V"], ref["V"])) <= (1e-12 if precision == "fp64" else 1e-6)
+
+
+def test_autotune_picks_an_instantiated_shape():
+    from paper_1803_01215_gb300 import binding
+    w = W.quadcopter(B=512)
+    prob = binding.Problem.from_workload(w)
+    xq = torch.as_tensor(w["xq"], device="cuda")
+    t = torch.as_tensor(w["t"], device="cuda")
+    opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], tol=w["tol"], max_iter=w["max_iter"],
+                             check_every=w["check_every"], seed=w["seed"])
+    G, npl, ms = binding.autotune(prob, xq, t, 64, opts, repeats=1)
+    assert G in (1, 2, 4, 8) and npl in (1, 2) and 64 <= 32 * G * npl and ms > 0
+    assert binding.get_launch_shape(prob, "fp32", 64) == (G, npl)
+    with pytest.raises(binding.HJError) as e:
+        binding.set_launch_shape(prob, "fp64", 64, 1, 2)       # no FP64 instantiation with NPL 2
+    assert e.value.code == binding.HJ_ERR_UNSUPPORTED

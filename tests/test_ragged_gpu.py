@@ -1,0 +1,144 @@
+"""Ragged batches (mixed problems and per-point N, one CUDA-graph launch)
+against the FP64 oracle and against uniform solves of the same points."""
+import numpy as np
+import pytest
+
+from gpu_common import value_err
+from oracle import lax_pdhg as O
+from paper_1803_01215_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _plan(rw, precision, **ov):
+    from paper_1803_01215_gb300 import binding
+    probs = [binding.Problem.from_workload(p) for p in rw["problems"]]
+    o = dict(sigma=rw["sigma"], tau=rw["tau"], tol=rw["tol"], max_iter=rw["max_iter"],
+             check_every=rw["check_every"], seed=rw["seed"], init_radius=rw["init_radius"])
+    o.update(ov)
+    plan = binding.RaggedPlan(probs, rw["prob_of"], rw["N_of"], binding.make_opts(precision=precision, **o))
+    xq = torch.as_tensor(plan.pack_xq(rw["xq"]), device="cuda")
+    t = torch.as_tensor(rw["t"], device="cuda")
+    return plan, xq, t
+
+
+def _small_mix(B=90, seed=11):
+    rw = W.ragged_mix(B=B, seed=seed)
+    r = np.random.default_rng(seed)
+    rw["N_of"] = r.choice(np.array([3, 17, 40, 64, 100, 130, 256], dtype=np.int32), size=B)
+    return rw
+
+
+def _groups(rw):
+    keys = sorted(set(zip(rw["prob_of"].tolist(), rw["N_of"].tolist())))
+    return [(k, N) for k, N in keys]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ragged_fixed_iterations_elementwise(precision):
+    rw = _small_mix()
+    K = 40
+    plan, xq, t = _plan(rw, precision, tol=0.0, max_iter=K, check_every=K)
+    out = {k: v.cpu().numpy() for k, v in plan.solve(xq, t, return_traj=True).items()}
+    assert np.all(out["iters"] == K)
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    for k, N in _groups(rw):
+        g = W.ragged_group(rw, k, N)
+        o = O.solve(g, tol=0.0, max_iter=K, check_every=K)
+        for i, b in enumerate(g["point_index"]):
+            tx = plan.point_traj(out["traj_x"], b)
+            tp = plan.point_traj(out["traj_p"], b)
+            assert np.max(np.abs(tx - o["x"][i])) <= tol, (k, N, b)
+            assert np.max(np.abs(tp - o["p"][i])) <= tol, (k, N, b)
+        assert np.max(value_err(out["V"][g["point_index"]], o["V"])) <= (1e-9 if precision == "fp64" else 1e-4)
+
+
+def test_ragged_fp64_same_stop_and_fp32_converged():
+    rw = _small_mix(B=45, seed=12)
+    rw["max_iter"] = 6000
+    plan64, xq, t = _plan(rw, "fp64")
+    o64 = {k: v.cpu().numpy() for k, v in plan64.solve(xq, t).items()}
+    plan32, xq, t = _plan(rw, "fp32")
+    o32 = {k: v.cpu().numpy() for k, v in plan32.solve(xq, t).items()}
+    for k, N in _groups(rw):
+        g = W.ragged_group(rw, k, N)
+        o = O.solve(g)
+        ids = g["point_index"]
+        same = o64["iters"][ids] == o["iters"]
+        assert np.mean(same) >= 0.8
+        assert np.max(value_err(o64["V"][ids][same], o["V"][same]), initial=0.0) <= 1e-9
+        conv = o["status"] == O.CONVERGED
+        ok = conv & (o32["status"][ids] == O.CONVERGED)
+        assert np.max(value_err(o32["V"][ids][ok], o["V"][ok]), initial=0.0) <= 1e-4, (k, N)
+
+
+def test_ragged_matches_uniform_solves_and_replays():
+    from paper_1803_01215_gb300 import binding
+    rw = _small_mix(B=60, seed=13)
+    plan, xq, t = _plan(rw, "fp32", tol=0.0, max_iter=30, check_every=30)
+    a = {k: v.cpu().numpy() for k, v in plan.solve(xq, t, return_traj=True).items()}
+    b = {k: v.cpu().numpy() for k, v in plan.solve(xq, t, return_traj=True).items()}   # new buffers
+    out = plan.solve(xq, t, return_traj=True)
+    c = {k: v.cpu().numpy() for k, v in plan.solve(xq, t, out=out).items()}            # replay
+    for key in ("V", "iters", "status", "traj_x", "traj_p"):
+        assert np.array_equal(a[key], b[key]) and np.array_equal(a[key], c[key]), key
+    # each (problem, N) group through hj_solve_batch: same point ids via point_offset slices
+    for k, N in _groups(rw)[:6]:
+        ids = np.where((rw["prob_of"] == k) & (rw["N_of"] == N))[0]
+        prob = binding.Problem.from_workload(rw["problems"][k])
+        for b_ in ids[:2]:
+            opts = binding.make_opts(sigma=rw["sigma"], tau=rw["tau"], tol=0.0, max_iter=30,
+                                     check_every=30, seed=rw["seed"], point_offset=int(b_))
+            u = binding.solve_batch(prob, torch.as_tensor(rw["xq"][b_][None], device="cuda"),
+                                    torch.as_tensor(rw["t"][b_:b_ + 1], device="cuda"), int(N),
+                                    opts, return_traj=True)
+            np.testing.assert_allclose(u["traj_x"].cpu().numpy()[0], plan.point_traj(a["traj_x"], b_),
+                                       rtol=1e-5, atol=1e-5)
+            assert abs(u["V"].item() - a["V"][b_]) <= 1e-5 * max(1.0, abs(a["V"][b_]))
+
+
+def test_ragged_autotune_keeps_results():
+    rw = _small_mix(B=120, seed=14)
+    plan, xq, t = _plan(rw, "fp32", tol=0.0, max_iter=25, check_every=25)
+    before = {k: v.cpu().numpy() for k, v in plan.solve(xq, t, return_traj=True).items()}
+    plan.autotune(xq, t, repeats=1)
+    shapes = plan.buckets()
+    assert all(s["n_max"] <= 32 * max(1, s["warps_per_point"]) * max(1, s["nodes_per_lane"])
+               or s["warps_per_point"] == 0 for s in shapes)
+    after = {k: v.cpu().numpy() for k, v in plan.solve(xq, t, return_traj=True).items()}
+    np.testing.assert_allclose(after["traj_x"], before["traj_x"], rtol=1e-5, atol=1e-5)
+    assert np.max(value_err(after["V"], before["V"])) <= 1e-6
+
+
+def test_ragged_full_size_sampled():
+    """100 000 points, thirds of tanh d=4, quadcopter d=12, tanh d=32, N ~ U{16..256}."""
+    rw = W.ragged_mix()
+    plan, xq, t = _plan(rw, "fp32")
+    plan.autotune(xq, t, repeats=1)
+    out = {k: v.cpu().numpy() for k, v in plan.solve(xq, t).items()}
+    conv = out["status"] == O.CONVERGED
+    print(f"ragged 100k: converged {conv.mean():.4f}, iters median {np.median(out['iters'])} "
+          f"max {out['iters'].max()}; buckets {plan.buckets()}")
+    assert conv.mean() >= 0.99
+    assert np.all(np.isin(out["status"], [O.CONVERGED, O.MAX_ITER]))
+    r = np.random.default_rng(5)
+    for k in range(3):
+        ids = r.choice(np.where((rw["prob_of"] == k) & conv)[0], 3, replace=False)
+        for b in ids:
+            g = W.ragged_group(rw, k, int(rw["N_of"][b]), idx=[b])
+            o = O.solve(g, tol=1e-16, check_every=1, max_iter=100000)
+            assert value_err(out["V"][b:b + 1], o["V"])[0] <= 1e-4, (k, b)
+
+
+def test_ragged_invalid_arguments():
+    from paper_1803_01215_gb300 import binding
+    rw = _small_mix(B=10, seed=15)
+    probs = [binding.Problem.from_workload(p) for p in rw["problems"]]
+    opts = binding.make_opts(sigma=1.0, tau=0.2)
+    bad_N = rw["N_of"].copy(); bad_N[3] = 300
+    with pytest.raises(binding.HJError):
+        binding.RaggedPlan(probs, rw["prob_of"], bad_N, opts)
+    bad_p = rw["prob_of"].copy(); bad_p[0] = 7
+    with pytest.raises(binding.HJError):
+        binding.RaggedPlan(probs, bad_p, rw["N_of"], opts)
