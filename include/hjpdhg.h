@@ -134,6 +134,31 @@ hj_status hj_solve_batch(hj_problem prob, int64_t B,
                          const void* warm_x, const void* warm_p,
                          void* stream);
 
+/* Gradient of L = sum_b w_b V_b at solved points (the adjoint of the value).
+ * At a saddle of Eq. (disclaxBE) every total derivative of V equals the partial
+ * derivative of its Lagrangian (envelope theorem), so from the trajectories of
+ * a converged hj_solve_batch call (same problem, t, N, precision):
+ *   dV/dW_i = W_i (x_0i - c_i)^2,   dV/dc_i = -W_i^2 (x_0i - c_i),
+ *   dV/dtheta = -delta sum_{j=1..N} dH/dtheta(x_j, p_j)     (theta = dyn parameters),
+ *   dV/dx_q   = p_N - delta grad_x H(x_N, p_N)              (x_N = x_q is pinned),
+ * which for H independent of x is the costate p_N (Section 2: p = grad_x phi).
+ *   t        (device) [B] horizons; traj_x, traj_p (device) [B][N+1][d] in the
+ *            precision's type (as written by hj_solve_batch).
+ *   dL_dV    (device) [B] weights w_b (e.g. 1/B for the mean value).
+ *   dW, dc   (device) [d] double out: sum_b w_b dV_b/dW, dV_b/dc (zeroed first).
+ *   ddyn     (device) [n_dyn] double out, the family's dyn layout (quadcopter:
+ *            m, a_h, g_z, eps; tanh drift: A row-major; NULL for quadratic).
+ *   dxq      (device, may be NULL) [B][d] double out: w_b dV_b/dx_q.
+ * Node arithmetic runs in the trajectory type, all sums in FP64.  The result is
+ * the gradient of the value at the given iterates; it equals the derivative of
+ * the converged value to the accuracy the iterates satisfy the saddle
+ * conditions (Appendix A.1 stopping rule).
+ * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_UNSUPPORTED (tanh drift with d > 128), HJ_ERR_CUDA. */
+hj_status hj_solve_grad(hj_problem prob, int64_t B, const double* t, int32_t N,
+                        int32_t precision, const void* traj_x, const void* traj_p,
+                        const double* dL_dV, double* dW, double* dc, double* ddyn, double* dxq,
+                        void* stream);
+
 /* Launch shape of the register-resident kernel (quadratic d <= 4, quadcopter,
  * tanh drift d in {2, 4}): a group of `warps_per_point` warps (1, 2, 4, 8)
  * solves one point, each lane holding `nodes_per_lane` time nodes (1 or 2; 1
@@ -199,9 +224,10 @@ hj_status hj_ragged_plan_bucket(hj_ragged_plan plan, int32_t i, int32_t* problem
 
 /* Solve the batch: xq (device, packed), t (device, [B]); V, iters, status
  * (device, [B]); traj_x, traj_p (device, packed, may be NULL).  The first call
- * with a given set of buffers captures the graph on `stream` (so it must not be
- * called while `stream` is itself being captured); later calls with the same
- * buffers replay it.  Solves on one plan must be ordered on one stream.
+ * with a given set of buffers captures the graph on a stream the plan owns;
+ * every call launches it on `stream` (the legacy default stream is accepted).
+ * Later calls with the same buffers replay the graph without capturing.  Solves
+ * on one plan must be ordered on one stream.
  * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_CUDA.                                   */
 hj_status hj_ragged_solve(hj_ragged_plan plan, const double* xq, const double* t, double* V,
                           int32_t* iters, int8_t* status, void* traj_x, void* traj_p,

@@ -38,7 +38,7 @@ EXPORTED = ("hj_problem_create", "hj_problem_destroy", "hj_solve_batch",
             "hj_set_launch_shape", "hj_get_launch_shape", "hj_autotune",
             "hj_ragged_plan_create", "hj_ragged_plan_layout", "hj_ragged_plan_bucket",
             "hj_ragged_solve", "hj_ragged_autotune", "hj_ragged_plan_destroy",
-            "hj_status_str", "hj_version")
+            "hj_solve_grad", "hj_status_str", "hj_version")
 
 
 def _lib():
@@ -72,6 +72,8 @@ def _lib():
         for name in ("hj_ragged_plan_create", "hj_ragged_plan_layout", "hj_ragged_plan_bucket",
                      "hj_ragged_solve", "hj_ragged_autotune", "hj_ragged_plan_destroy"):
             getattr(lib, name).restype = ctypes.c_int
+        lib.hj_solve_grad.argtypes = [P, I64, P, I32, I32, P, P, P, P, P, P, P, P]
+        lib.hj_solve_grad.restype = ctypes.c_int
         lib.hj_status_str.restype = ctypes.c_char_p
         lib.hj_status_str.argtypes = [ctypes.c_int]
         lib.hj_version.restype = ctypes.c_int32
@@ -150,6 +152,31 @@ def autotune(problem, xq, t, N, opts, repeats=2, stream=None):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def n_dyn(problem):
+    return {0: 0, 1: 4, 2: problem.d * problem.d}[problem.family]
+
+
+def solve_grad(problem, t, N, precision, traj_x, traj_p, dL_dV, want_dxq=True, stream=None):
+    """hj_solve_grad: gradient of sum_b dL_dV[b] V_b at solved trajectories.
+    Returns dict(dW [d], dc [d], ddyn [n_dyn], dxq [B, d] or None), FP64 device tensors."""
+    dev = t.device
+    d = problem.d
+    B = t.shape[0]
+    out = dict(dW=torch.empty(d, dtype=torch.float64, device=dev),
+               dc=torch.empty(d, dtype=torch.float64, device=dev),
+               ddyn=torch.empty(max(n_dyn(problem), 1), dtype=torch.float64, device=dev),
+               dxq=torch.empty(B, d, dtype=torch.float64, device=dev) if want_dxq else None)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    r = _lib().hj_solve_grad(problem.handle, B, _ptr(t.contiguous()), int(N), PREC[precision],
+                             _ptr(traj_x.contiguous()), _ptr(traj_p.contiguous()),
+                             _ptr(dL_dV.contiguous()), _ptr(out["dW"]), _ptr(out["dc"]),
+                             _ptr(out["ddyn"]), _ptr(out["dxq"]), ctypes.c_void_p(s.cuda_stream))
+    if r != HJ_OK:
+        raise HJError(r, "hj_solve_grad")
+    out["ddyn"] = out["ddyn"][:n_dyn(problem)]
+    return out
 
 
 def make_opts(*, sigma, tau, theta=1.0, tol=1e-8, max_iter=20000, check_every=16,

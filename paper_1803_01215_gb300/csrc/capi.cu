@@ -65,6 +65,7 @@ hj_status hj_problem_create(hj_problem* out, int32_t family, int32_t d, const do
   std::vector<double> w2(d);
   for (int i = 0; i < d; ++i) w2[i] = W[i] * W[i];
   hj_status r = upload(&p->W2, w2.data(), d);
+  if (r == HJ_OK) r = upload(&p->W, W, d);
   if (r == HJ_OK) r = upload(&p->c, c, d);
   if (r == HJ_OK && family == HJ_FAMILY_QUADCOPTER) {
     for (int i = 0; i < 4; ++i) p->qc[i] = dyn[i];
@@ -127,6 +128,44 @@ hj_status hj_solve_batch(hj_problem prob, int64_t B, const double* xq, const dou
                             warm_x, warm_p, s);
   return run_solve<double>(prob, B, N, o, cfg, xq, t, V, iters, status, traj_x, traj_p, warm_x,
                            warm_p, s);
+}
+
+hj_status hj_solve_grad(hj_problem prob, int64_t B, const double* t, int32_t N,
+                        int32_t precision, const void* traj_x, const void* traj_p,
+                        const double* dL_dV, double* dW, double* dc, double* ddyn, double* dxq,
+                        void* stream) {
+  if (prob == nullptr || B < 0 || N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;
+  if (precision != HJ_PREC_FP32 && precision != HJ_PREC_FP64) return HJ_ERR_INVALID_ARG;
+  const int n_dyn = prob->family == HJ_FAMILY_QUADCOPTER ? 4
+                    : prob->family == HJ_FAMILY_TANH_DRIFT ? prob->d * prob->d : 0;
+  if (dW == nullptr || dc == nullptr || (n_dyn > 0 && ddyn == nullptr)) return HJ_ERR_INVALID_ARG;
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return HJ_ERR_CUDA;
+  if (cur != prob->device) return HJ_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(dW, 0, prob->d * sizeof(double), s) != cudaSuccess ||
+      cudaMemsetAsync(dc, 0, prob->d * sizeof(double), s) != cudaSuccess ||
+      (n_dyn > 0 && cudaMemsetAsync(ddyn, 0, n_dyn * sizeof(double), s) != cudaSuccess))
+    return HJ_ERR_CUDA;
+  if (B == 0) return HJ_OK;
+  if (t == nullptr || traj_x == nullptr || traj_p == nullptr || dL_dV == nullptr)
+    return HJ_ERR_INVALID_ARG;
+  if (precision == HJ_PREC_FP32) {
+    hj::GradArgs<float> g{};
+    g.B = B; g.N = N; g.d = prob->d; g.n_dyn = n_dyn; g.t = t;
+    g.X = static_cast<const float*>(traj_x); g.P = static_cast<const float*>(traj_p);
+    g.w = dL_dV; g.W = prob->W; g.W2 = prob->W2; g.c = prob->c; g.A = prob->Af;
+    g.qc_m = prob->qc[0]; g.qc_ah = prob->qc[1]; g.qc_gz = prob->qc[2]; g.qc_eps = prob->qc[3];
+    g.dW = dW; g.dc = dc; g.ddyn = ddyn; g.dxq = dxq;
+    return hj::launch_value_grad<float>(prob->family, g, s);
+  }
+  hj::GradArgs<double> g{};
+  g.B = B; g.N = N; g.d = prob->d; g.n_dyn = n_dyn; g.t = t;
+  g.X = static_cast<const double*>(traj_x); g.P = static_cast<const double*>(traj_p);
+  g.w = dL_dV; g.W = prob->W; g.W2 = prob->W2; g.c = prob->c; g.A = prob->Ad;
+  g.qc_m = prob->qc[0]; g.qc_ah = prob->qc[1]; g.qc_gz = prob->qc[2]; g.qc_eps = prob->qc[3];
+  g.dW = dW; g.dc = dc; g.ddyn = ddyn; g.dxq = dxq;
+  return hj::launch_value_grad<double>(prob->family, g, s);
 }
 
 hj_status hj_set_launch_shape(hj_problem prob, int32_t precision, int32_t N,

@@ -101,6 +101,29 @@ __device__ __forceinline__ U warp_sum(U v) {
 template <typename T>
 __device__ __forceinline__ bool finite_val(T v) { return isfinite(v); }
 
+// Arguments of the value-gradient kernel (value_grad.cu).
+template <typename T>
+struct GradArgs {
+  int64_t B;
+  int32_t N, d, n_dyn;
+  const double* t;
+  const T* X;            // [B][N+1][d]
+  const T* P;            // [B][N+1][d]
+  const double* w;       // [B] dL/dV
+  const double* W;       // [d]
+  const double* W2;      // [d]
+  const double* c;       // [d]
+  const T* A;            // tanh drift [d][d]
+  double qc_m, qc_ah, qc_gz, qc_eps;
+  double* dW;            // [d]      accumulated (atomicAdd)
+  double* dc;            // [d]
+  double* ddyn;          // [n_dyn]
+  double* dxq;           // [B][d] or null (written)
+};
+
+template <typename T>
+hj_status launch_value_grad(int family, const GradArgs<T>& g, cudaStream_t s);
+
 // Kernel launchers (one per kernel family), defined in their .cu files.
 // Each returns HJ_OK, HJ_ERR_UNSUPPORTED (no instantiation for this shape) or
 // HJ_ERR_CUDA.

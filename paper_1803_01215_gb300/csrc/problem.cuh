@@ -13,7 +13,8 @@
 struct hj_problem_s {
   int family = 0, d = 0, device = 0;
   double qc[4] = {0, 0, 0, 0};        // m, a_h, g_z, eps
-  double* W2 = nullptr;               // [d]
+  double* W2 = nullptr;               // [d]  W_i^2
+  double* W = nullptr;                // [d]  W_i as given (sign kept for dV/dW)
   double* c = nullptr;                // [d]
   float* Af = nullptr;                // [d][d]
   float* Atf = nullptr;               // [d][d]
@@ -43,7 +44,7 @@ hj_status upload(T** dst, const T* src, size_t n) {
 }
 
 inline void release(hj_problem_s* p) {
-  cudaFree(p->W2); cudaFree(p->c);
+  cudaFree(p->W2); cudaFree(p->W); cudaFree(p->c);
   cudaFree(p->Af); cudaFree(p->Atf); cudaFree(p->Ad); cudaFree(p->Atd);
   cudaFree(p->counter);
   delete p;

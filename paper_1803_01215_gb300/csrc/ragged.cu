@@ -58,6 +58,7 @@ struct hj_ragged_plan_s {
   int64_t* d_traj_off = nullptr;
   unsigned long long* d_counters = nullptr;
   std::vector<Bucket> buckets;                // sorted by decreasing work
+  cudaStream_t cap = nullptr;                 // the graph is captured here
   cudaStream_t side[kSideStreams] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kSideStreams] = {};
   cudaGraphExec_t exec = nullptr;
@@ -75,6 +76,7 @@ void plan_release(hj_ragged_plan_s* p) {
     if (p->ev_join[i]) cudaEventDestroy(p->ev_join[i]);
   }
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->cap) cudaStreamDestroy(p->cap);
   delete p;
 }
 
@@ -182,6 +184,8 @@ hj_status hj_ragged_plan_create(hj_ragged_plan* out, int32_t n_prob, const hj_pr
   }
   if (r == HJ_OK && cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess)
     r = HJ_ERR_CUDA;
+  if (r == HJ_OK && cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess)
+    r = HJ_ERR_CUDA;
   if (r != HJ_OK) { plan_release(p); return r; }
   *out = p;
   return HJ_OK;
@@ -235,13 +239,16 @@ hj_status hj_ragged_solve(hj_ragged_plan plan, const double* xq, const double* t
   const void* ptrs[7] = {xq, t, V, iters, status, traj_x, traj_p};
   const bool same = plan->exec != nullptr && std::memcmp(ptrs, plan->bound, sizeof(ptrs)) == 0;
   if (!same) {
+    // capture on the plan's own stream (the caller's may be the uncapturable
+    // legacy default stream); the graph is then launched on the caller's stream
     if (plan->exec) { cudaGraphExecDestroy(plan->exec); plan->exec = nullptr; }
-    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return HJ_ERR_CUDA;
+    cudaStream_t c = plan->cap;
+    if (cudaStreamBeginCapture(c, cudaStreamCaptureModeRelaxed) != cudaSuccess) return HJ_ERR_CUDA;
     hj_status r = HJ_OK;
     const size_t nb = plan->buckets.size();
     const int nside = (int)std::min<size_t>(nb, kSideStreams);
-    if (cudaMemsetAsync(plan->d_counters, 0, nb * sizeof(unsigned long long), s) != cudaSuccess ||
-        cudaEventRecord(plan->ev_fork, s) != cudaSuccess)
+    if (cudaMemsetAsync(plan->d_counters, 0, nb * sizeof(unsigned long long), c) != cudaSuccess ||
+        cudaEventRecord(plan->ev_fork, c) != cudaSuccess)
       r = HJ_ERR_CUDA;
     for (int i = 0; i < nside && r == HJ_OK; ++i)
       if (cudaStreamWaitEvent(plan->side[i], plan->ev_fork, 0) != cudaSuccess) r = HJ_ERR_CUDA;
@@ -250,10 +257,10 @@ hj_status hj_ragged_solve(hj_ragged_plan plan, const double* xq, const double* t
                             traj_p, plan->side[bi % nside]);
     for (int i = 0; i < nside; ++i) {
       cudaEventRecord(plan->ev_join[i], plan->side[i]);
-      cudaStreamWaitEvent(s, plan->ev_join[i], 0);
+      cudaStreamWaitEvent(c, plan->ev_join[i], 0);
     }
     cudaGraph_t g = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(s, &g);
+    const cudaError_t ce = cudaStreamEndCapture(c, &g);
     if (r == HJ_OK && (ce != cudaSuccess || g == nullptr)) r = HJ_ERR_CUDA;
     if (r == HJ_OK && cudaGraphInstantiate(&plan->exec, g, 0) != cudaSuccess) r = HJ_ERR_CUDA;
     if (g) cudaGraphDestroy(g);

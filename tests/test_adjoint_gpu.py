@@ -1,0 +1,115 @@
+"""Adjoint of the value (hj_solve_grad behind torch.autograd) against central
+finite differences (h = 1e-4) of the FP64 oracle's converged value, the closed
+form, and the costate p_N."""
+import numpy as np
+import pytest
+
+from oracle import lax_pdhg as O
+from paper_1803_01215_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TIGHT = dict(tol=1e-24, check_every=1, max_iter=200000)
+
+
+def _mean_V(w):
+    return float(np.mean(O.solve(w, **TIGHT)["V"]))
+
+
+def _fd(w, field, i, h=1e-4):
+    wp, wm = dict(w), dict(w)
+    vp = np.array(w[field], dtype=float).copy(); vp.reshape(-1)[i] += h
+    vm = np.array(w[field], dtype=float).copy(); vm.reshape(-1)[i] -= h
+    wp[field], wm[field] = vp, vm
+    return (_mean_V(wp) - _mean_V(wm)) / (2 * h)
+
+
+def _gpu_grads(w, precision):
+    from paper_1803_01215_gb300.autograd import hj_value
+    xq = torch.as_tensor(w["xq"], device="cuda").requires_grad_(True)
+    t = torch.as_tensor(w["t"], device="cuda")
+    Wt = torch.as_tensor(w["W"]).requires_grad_(True)
+    ct = torch.as_tensor(w["c"]).requires_grad_(True)
+    dyn = torch.as_tensor(w["dyn"]).requires_grad_(w["dyn"].size > 0)
+    tol = 1e-24 if precision == "fp64" else 1e-11
+    V, it, st = hj_value(xq, t, Wt, ct, dyn, family=w["family"], N=w["N"], sigma=w["sigma"],
+                         tau=w["tau"], tol=tol, check_every=1, max_iter=100000,
+                         precision=precision, seed=w["seed"], init_radius=w["init_radius"])
+    V.mean().backward()
+    return dict(V=V.detach().cpu().numpy(), st=st.cpu().numpy(), dxq=xq.grad.cpu().numpy(),
+                dW=Wt.grad.cpu().numpy(), dc=ct.grad.cpu().numpy(),
+                ddyn=(dyn.grad.cpu().numpy() if dyn.grad is not None else None))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_quadcopter_gradient_vs_finite_differences(precision):
+    w = W.quadcopter(B=3, seed=31, N=10, t=0.4)
+    g = _gpu_grads(w, precision)
+    rt = 1e-6 if precision == "fp64" else 2e-3
+    def close(a, b):
+        return abs(a - b) <= rt * max(1.0, abs(b))
+    for i in range(12):
+        fd = _fd(w, "W", i)
+        assert close(g["dW"][i], fd), ("W", i, g["dW"][i], fd)
+    for i, name in enumerate(["m", "a_h", "g_z", "eps"]):
+        fd = _fd(w, "dyn", i)
+        assert close(g["ddyn"][i], fd), (name, g["ddyn"][i], fd)
+    for k in (0, 4, 7, 11):
+        fd = _fd(w, "xq", np.ravel_multi_index((1, k), w["xq"].shape))
+        assert close(g["dxq"][1, k], fd), ("xq", k, g["dxq"][1, k], fd)
+
+
+def test_tanh_drift_gradient_vs_finite_differences():
+    w = W.tanh_drift(3, B=3, seed=32, N=8)
+    w["sigma"], w["tau"] = 1.0, 0.24
+    g = _gpu_grads(w, "fp64")
+    for i in range(9):
+        fd = _fd(w, "dyn", i)
+        assert abs(g["ddyn"][i] - fd) <= 1e-6 * max(1.0, abs(fd)), ("A", i, g["ddyn"][i], fd)
+    for i in range(3):
+        fd = _fd(w, "c", i)
+        assert abs(g["dc"][i] - fd) <= 1e-6 * max(1.0, abs(fd)), ("c", i)
+    fd = _fd(w, "xq", 4)
+    assert abs(g["dxq"][1, 1] - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_quadratic_gradient_is_the_costate_and_the_closed_form():
+    """H = |p|^2/2: dV/dx_q = p_N exactly, and for g = |x|^2/2, V = |x|^2/(2(1+t))
+    gives dV/dx = x/(1+t)."""
+    w = W.quadratic_closed_form(B=8)
+    g = _gpu_grads(w, "fp64")
+    B = len(w["xq"])
+    np.testing.assert_allclose(g["dxq"] * B, w["xq"] / (1.0 + w["t"][:, None]), atol=1e-10)
+    o = O.solve(w, **TIGHT)
+    np.testing.assert_allclose(g["dxq"] * B, o["p"][:, -1, :], atol=1e-10)
+
+
+def test_full_size_adjoint_sampled():
+    """The 4096-point quadcopter batch: FP32 gradient of mean V; sampled per-point
+    gradients dV_b/dx_q against finite differences of the oracle, and the
+    O(delta) gap to the costate p_N reported."""
+    from paper_1803_01215_gb300 import binding
+    w = W.quadcopter()
+    prob = binding.Problem.from_workload(w)
+    xq = torch.as_tensor(w["xq"], device="cuda")
+    t = torch.as_tensor(w["t"], device="cuda")
+    opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], tol=1e-10, max_iter=20000,
+                             check_every=16, seed=w["seed"])
+    out = binding.solve_batch(prob, xq, t, 64, opts, return_traj=True)
+    B = len(w["xq"])
+    wts = torch.full((B,), 1.0 / B, dtype=torch.float64, device="cuda")
+    g = binding.solve_grad(prob, t, 64, "fp32", out["traj_x"], out["traj_p"], wts)
+    dxq = g["dxq"].cpu().numpy() * B
+    assert np.all(np.isfinite(dxq)) and np.all(np.isfinite(g["dW"].cpu().numpy()))
+    pN = out["traj_p"].cpu().numpy()[:, -1, :]
+    print(f"max |dV/dx - p_N| = {np.max(np.abs(dxq - pN)):.3e} (O(delta), delta = 1/64)")
+    for b in (7, 1234):
+        sub = W.subset(w, [b])
+        for k in (2, 5, 8):
+            h = 1e-4
+            sp, sm = dict(sub), dict(sub)
+            sp["xq"] = sub["xq"].copy(); sp["xq"][0, k] += h
+            sm["xq"] = sub["xq"].copy(); sm["xq"][0, k] -= h
+            fd = (O.solve(sp, **TIGHT)["V"][0] - O.solve(sm, **TIGHT)["V"][0]) / (2 * h)
+            assert abs(dxq[b, k] - fd) <= 2e-3 * max(1.0, abs(fd)), (b, k, dxq[b, k], fd)
