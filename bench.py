@@ -137,7 +137,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_1803_01215_gb300 import binding
+    from paper_1803_01215_gb300 import binding, sharding
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -152,7 +152,7 @@ def main():
     prob = binding.Problem.from_workload(w)
     base = dict(sigma=w["sigma"], tau=w["tau"], tol=w["tol"], max_iter=w["max_iter"],
                 check_every=w["check_every"], seed=w["seed"], init_radius=w["init_radius"],
-                point_offset=rank * B)
+                point_offset=sharding.weak_offset(rank, B))
     o32 = binding.make_opts(precision="fp32", **base)
     o64 = binding.make_opts(precision="fp64", **base)
     xq = torch.as_tensor(w["xq"], device=dev)
@@ -188,7 +188,7 @@ def main():
     V64 = out64["V"].clone()
     st64 = out64["status"].clone()
 
-    def timed(opts, out, steps, warmup):
+    def timed(opts, out, steps, warmup, tag):
         for _ in range(warmup):
             step(opts, out)
         barrier()
@@ -196,9 +196,11 @@ def main():
         for _ in range(steps):
             flush.fill_(1.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push(tag)          # lets a profiler select the timed launches
             e0.record(stream)
             step(opts, out)
             e1.record(stream)
+            torch.cuda.nvtx.range_pop()
             e1.synchronize()
             ms += e0.elapsed_time(e1)
         barrier()
@@ -206,11 +208,11 @@ def main():
 
     clocks_path = os.path.join(tempfile.gettempdir(), f"hj_clocks_{os.getpid()}.csv")
     sampler = _clock_sampler(clocks_path)
-    ms32 = timed(o32, out32, args.steps, args.warmup)
+    ms32 = timed(o32, out32, args.steps, args.warmup, "timed_fp32")
     if sampler is not None:
         sampler.terminate()
         sampler.wait()
-    ms64 = timed(o64, out64, args.fp64_steps, 1)
+    ms64 = timed(o64, out64, args.fp64_steps, 1, "timed_fp64")
 
     ok32 = ((out32["status"] == 0) & (st64 == 0) &
             ((out32["V"] - V64).abs() <= 1e-4 * V64.abs().clamp_min(1.0)))
@@ -243,13 +245,8 @@ def main():
     e2e_ms /= args.steps
 
     # max over ranks of the per-step time; total solves over ranks
-    tens = torch.tensor([ms32, ms64, e2e_ms], dtype=torch.float64, device=dev)
-    cnt = torch.tensor([n_ok32, n_ok64, iters_sum], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tens, op=dist.ReduceOp.MAX)
-        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
-    ms32, ms64, e2e_ms = [float(v) for v in tens.tolist()]
-    n_ok32, n_ok64, iters_sum = [float(v) for v in cnt.tolist()]
+    (ms32, ms64, e2e_ms), (n_ok32, n_ok64, iters_sum) = sharding.reduce_step_stats(
+        [ms32, ms64, e2e_ms], [n_ok32, n_ok64, iters_sum], device=dev)
 
     if rank != 0:
         if world > 1:

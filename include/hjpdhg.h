@@ -206,7 +206,10 @@ typedef struct hj_ragged_plan_s* hj_ragged_plan;
  * traj[traj_off[b] .. traj_off[b+1]) as [N_b+1][d_b] (iterate type).
  * The plan owns device copies of N, the offsets and the bucket index lists,
  * one work counter per bucket and four side streams.
- * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_STEP_SIZE, HJ_ERR_OOM, HJ_ERR_CUDA.      */
+ * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_STEP_SIZE, HJ_ERR_OOM, HJ_ERR_CUDA;
+ * HJ_ERR_UNSUPPORTED when a bucket served by the shared-memory kernel does not
+ * fit its 227 KB (FP64 tanh drift: 4 (N+1) d + d^2 doubles, e.g. d = 32 allows
+ * N <= 200).                                                                */
 hj_status hj_ragged_plan_create(hj_ragged_plan* out, int32_t n_prob, const hj_problem* probs,
                                 int64_t B, const int32_t* prob_of, const int32_t* N_of,
                                 const hj_solver_opts* opts);

@@ -169,6 +169,14 @@ hj_status hj_ragged_plan_create(hj_ragged_plan* out, int32_t n_prob, const hj_pr
   for (auto& k : p->buckets) {
     const hj_problem_s* pr = probs[k.prob];
     k.cfg = hj::default_warp_config(pr->family, pr->d, k.ncap, f64);
+    if (k.cfg.G == 0) {
+      // shared-memory kernel: the bucket's largest N must fit its shared memory
+      const bool drift = pr->family == HJ_FAMILY_TANH_DRIFT;
+      if (pr->family == HJ_FAMILY_QUADCOPTER) r = HJ_ERR_UNSUPPORTED;
+      else if ((f64 ? hj::td_cta_smem_bytes<double>(pr->d, k.nmax, drift)
+                    : hj::td_cta_smem_bytes<float>(pr->d, k.nmax, drift)) == 0)
+        r = HJ_ERR_UNSUPPORTED;
+    }
     if (r == HJ_OK) r = upload(&k.d_ids, k.ids.data(), k.ids.size());
   }
   if (r == HJ_OK) r = upload(&p->d_N, N_of, (size_t)B);

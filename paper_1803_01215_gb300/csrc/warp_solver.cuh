@@ -2,11 +2,13 @@
 //
 // A group of G warps solves one query point at a time.  Lane gl (0..32G-1)
 // of the group owns the time nodes j = 1 + gl*NPL .. gl*NPL + NPL (those <= N),
-// with x_j, p_j and the relaxed z_j in registers; lane 0 also owns node 0
-// (x_0, the g-prox node).  The nearest-neighbour terms of the difference
+// with x_j, p_j and the relaxed z_j in registers; node 0 (x_0, the g-prox
+// node) is spread over lanes 0..D-1, one coordinate each.  The nearest-neighbour terms of the difference
 // operator D ((Dz)_j = z_j - z_{j-1}, (D^T p)_j = p_j - p_{j+1}, Appendix A.1)
-// cross a lane boundary once per direction and iteration as warp shuffles, and
-// a warp boundary (G > 1) through a shared-memory slot between two barriers.
+// cross a lane boundary once per direction and iteration through one
+// shared-memory slot per lane (the z of its last node, the p of its first),
+// written and read as 16-byte vectors around a group barrier (__syncwarp when
+// G = 1).
 // Groups draw points from a work counter until the batch is exhausted
 // (persistent grid sized to the SM count).
 //
@@ -30,16 +32,25 @@ constexpr int kWarpsPerCtaG1 = 4;   // independent single-warp groups per CTA wh
 template <int G>
 constexpr int warp_block_threads() { return (G == 1 ? kWarpsPerCtaG1 : G) * 32; }
 
+// Coordinates padded to a whole number of 16-byte vectors.
+template <typename T, int D>
+constexpr int padded_dim() { return ((D * (int)sizeof(T) + 15) / 16) * 16 / (int)sizeof(T); }
+
 // Per-CTA shared memory: the family's data, the g-prox of x_0
-// (x_0 <- (v + tau W^2 c) / (1 + tau W^2) as offset and reciprocal), and for
-// G > 1 the warp-boundary slots and reduction scratch of the CTA's one group.
+// (x_0 <- (v + tau W^2 c) / (1 + tau W^2) as offset and reciprocal), the
+// per-lane exchange slots of the CTA's groups, and for G > 1 the reduction
+// scratch of the CTA's one group.
 template <typename T, class F, int D, int G>
 struct WarpShared {
+  static constexpr int kGroups = (G == 1) ? kWarpsPerCtaG1 : 1;
+  static constexpr int DP = padded_dim<T, D>();
   typename F::Shared fam;
-  T g_off[D], g_inv[D];
+  alignas(16) T g_off[DP];
+  alignas(16) T g_inv[DP];
   double w2d[D], cd[D];
-  T zb[G][D];          // z (then x) of each warp's last lane
-  T pb[G][D];          // p of each warp's first lane
+  alignas(16) T zs[kGroups][32 * G][DP];   // z (in the epilogue x) of each lane's last node
+  alignas(16) T ps[kGroups][32 * G][DP];   // p of each lane's first node
+  alignas(16) T x0s[kGroups][DP];          // z_0 (in the epilogue x_0), one coordinate per lane
   double red[G][2];
   double vred[G];
   unsigned long long item;
@@ -48,6 +59,46 @@ struct WarpShared {
 template <int G>
 __device__ __forceinline__ void group_sync() {
   if constexpr (G > 1) __syncthreads();
+  else __syncwarp();
+}
+
+// 16-byte vector copies between a D-array in registers and a padded slot.
+template <typename T, int D>
+__device__ __forceinline__ void slot_store(T* dst, const T (&v)[D]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k + 4 <= D; k += 4)
+      *reinterpret_cast<float4*>(dst + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+#pragma unroll
+    for (int k = D - D % 4; k < D; ++k) dst[k] = v[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k + 2 <= D; k += 2)
+      *reinterpret_cast<double2*>(dst + k) = make_double2(v[k], v[k + 1]);
+#pragma unroll
+    for (int k = D - D % 2; k < D; ++k) dst[k] = v[k];
+  }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void slot_load(const T* src, T (&v)[D]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k + 4 <= D; k += 4) {
+      const float4 q = *reinterpret_cast<const float4*>(src + k);
+      v[k] = q.x; v[k + 1] = q.y; v[k + 2] = q.z; v[k + 3] = q.w;
+    }
+#pragma unroll
+    for (int k = D - D % 4; k < D; ++k) v[k] = src[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k + 2 <= D; k += 2) {
+      const double2 q = *reinterpret_cast<const double2*>(src + k);
+      v[k] = q.x; v[k + 1] = q.y;
+    }
+#pragma unroll
+    for (int k = D - D % 2; k < D; ++k) v[k] = src[k];
+  }
 }
 
 template <typename T, class F, int D, int NPL, int G>
@@ -68,30 +119,28 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   const uint64_t gid = (uint64_t)(a.point_offset + pt.id);
 
   T x[NPL][D], p[NPL][D], z[NPL][D];
-  T x0[D], z0[D];
+  // x_0: lane gl < D holds coordinate gl (x0 = x_0[gl], z0 = z_0[gl])
+  const bool own0 = gl < D;
+  const int k0 = own0 ? gl : 0;
+  T x0 = T(0), z0 = T(0);
+  const T goff = sh.g_off[k0], ginv = sh.g_inv[k0];
   const int jbase = 1 + gl * NPL;
   {
-    double xqd[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) xqd[k] = pt.xq[k];
     if (a.warm_x == nullptr) {
 #pragma unroll
       for (int i = 0; i < NPL; ++i) {
         const int j = jbase + i;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
+          const double xq = pt.xq[k];
           T xv = T(0), pv = T(0);
-          if (j < N) xv = T(xqd[k] + a.radius * uniform_pm1(a.seed, gid, 0, j, k));
-          else if (j == N) xv = T(xqd[k]);
+          if (j < N) xv = T(xq + a.radius * uniform_pm1(a.seed, gid, 0, j, k));
+          else if (j == N) xv = T(xq);
           if (j <= N) pv = T(a.radius * uniform_pm1(a.seed, gid, 1, j, k));
           x[i][k] = xv; p[i][k] = pv; z[i][k] = xv;
         }
       }
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        x0[k] = T(xqd[k] + a.radius * uniform_pm1(a.seed, gid, 0, 0, k));
-        z0[k] = x0[k];
-      }
+      if (own0) x0 = T(pt.xq[k0] + a.radius * uniform_pm1(a.seed, gid, 0, 0, k0));
     } else {
       const T* wx = a.warm_x + pt.traj;
       const T* wp = a.warm_p + pt.traj;
@@ -102,20 +151,22 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         for (int k = 0; k < D; ++k) {
           T xv = T(0), pv = T(0);
           if (j < N) xv = wx[(size_t)j * D + k];
-          else if (j == N) xv = T(xqd[k]);
+          else if (j == N) xv = T(pt.xq[k]);
           if (j <= N) pv = wp[(size_t)j * D + k];
           x[i][k] = xv; p[i][k] = pv; z[i][k] = xv;
         }
       }
-#pragma unroll
-      for (int k = 0; k < D; ++k) { x0[k] = wx[k]; z0[k] = x0[k]; }
+      if (own0) x0 = wx[k0];
     }
+    z0 = x0;
   }
-  if constexpr (G > 1) {
-    if (lane == 31)
-#pragma unroll
-      for (int k = 0; k < D; ++k) sh.zb[wg][k] = z[NPL - 1][k];
-  }
+  const int grp = (G == 1) ? (int)(threadIdx.x >> 5) : 0;
+  T* zslot = &sh.zs[grp][0][0];
+  T* pslot = &sh.ps[grp][0][0];
+  T* x0slot = &sh.x0s[grp][0];
+  if (own0) x0slot[k0] = z0;                  // read by lane 0 after the first barrier
+  constexpr int DP = WarpShared<T, F, D, G>::DP;
+  constexpr int kLanes = 32 * G;
 
   int k_it = 0;
   int8_t st = HJ_POINT_MAX_ITER;
@@ -127,19 +178,11 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     if (until_check == 0) until_check = check_every;
     T rx = T(0), rp = T(0);
     typename F::Ctx ctx[NPL];
-    group_sync<G>();                                            // zb of the last iteration
-    // ---- dual step, nodes 1..N (z_{j-1} of the first owned node from the left lane)
+    // ---- z_{j-1} of the first owned node: the left lane's slot (z^k of its last node)
+    slot_store<T, D>(zslot + gl * DP, z[NPL - 1]);
+    group_sync<G>();
     T zl[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const T up = __shfl_up_sync(kFull, z[NPL - 1][k], 1);
-      T v = up;
-      if (lane == 0) {
-        if constexpr (G > 1) v = (wg == 0) ? z0[k] : sh.zb[wg - 1][k];
-        else v = z0[k];
-      }
-      zl[k] = v;
-    }
+    slot_load<T, D>(gl > 0 ? zslot + (gl - 1) * DP : x0slot, zl);
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
       if (jbase + i <= N) {
@@ -159,31 +202,23 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         for (int k = 0; k < D; ++k) p[i][k] = v[k];
       }
     }
-    // ---- primal step: p_{j+1} of the last owned node from the right lane
-    if constexpr (G > 1) {
-      if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < D; ++k) sh.pb[wg][k] = p[0][k];
-    }
+    // ---- primal step: p_{j+1} of the last owned node from the right lane's slot
+    slot_store<T, D>(pslot + gl * DP, p[0]);
     group_sync<G>();
     T pr[D];
+    if (gl + 1 < kLanes) {
+      slot_load<T, D>(pslot + (gl + 1) * DP, pr);
+    } else {
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      T v = __shfl_down_sync(kFull, p[0][k], 1);
-      if constexpr (G > 1) {
-        if (lane == 31 && wg + 1 < G) v = sh.pb[wg + 1][k];
-      }
-      pr[k] = v;
+      for (int k = 0; k < D; ++k) pr[k] = T(0);    // the last lane never updates an x with it
     }
-    if (gl == 0) {
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const T vx = x0[k] + tau * p[0][k];                  // (D^T p)_0 = -p_1
-        const T xn = (vx + sh.g_off[k]) * sh.g_inv[k];
-        if (chk) { const T e = xn - x0[k]; rx += e * e; }
-        z0[k] = xn + th * (xn - x0[k]);
-        x0[k] = xn;
-      }
+    if (own0) {
+      // x_0 <- prox_{tau g}(x_0 + tau p_1), coordinate k0; p_1 is lane 0's slot
+      const T xn = (x0 + tau * pslot[k0] + goff) * ginv;      // (D^T p)_0 = -p_1
+      if (chk) { const T e = xn - x0; rx += e * e; }
+      z0 = xn + th * (xn - x0);
+      x0 = xn;
+      x0slot[k0] = z0;
     }
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
@@ -216,11 +251,6 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         }
       }
     }
-    if constexpr (G > 1) {
-      if (lane == 31)
-#pragma unroll
-        for (int k = 0; k < D; ++k) sh.zb[wg][k] = z[NPL - 1][k];
-    }
     if (chk) {
       // lane partials summed across the warp in the iterate type, then in FP64
       double sx = (double)warp_sum<T>(rx);
@@ -238,26 +268,15 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   }
 
   // ---- value (fval of Algorithm 1) in FP64, and outputs
-  if constexpr (G > 1) {
-    if (lane == 31)
-#pragma unroll
-      for (int k = 0; k < D; ++k) sh.zb[wg][k] = x[NPL - 1][k];
-    __syncthreads();
-  }
+  group_sync<G>();                                 // every lane is done with the slots
+  slot_store<T, D>(zslot + gl * DP, x[NPL - 1]);
+  if (own0) x0slot[k0] = x0;
+  group_sync<G>();
   double acc = 0.0;
   {
     const double delta = a.t[pt.id] / N;
     T xl[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const T up = __shfl_up_sync(kFull, x[NPL - 1][k], 1);
-      T v = up;
-      if (lane == 0) {
-        if constexpr (G > 1) v = (wg == 0) ? x0[k] : sh.zb[wg - 1][k];
-        else v = x0[k];
-      }
-      xl[k] = v;
-    }
+    slot_load<T, D>(gl > 0 ? zslot + (gl - 1) * DP : x0slot, xl);
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
       if (jbase + i <= N) {
@@ -270,14 +289,9 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         acc += s - delta * fam.H64(x[i], p[i]);
       }
     }
-    if (gl == 0) {
-      double g = 0.0;
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const double e = (double)x0[k] - sh.cd[k];
-        g += sh.w2d[k] * e * e;
-      }
-      acc += 0.5 * g;
+    if (own0) {
+      const double e = (double)x0 - sh.cd[k0];
+      acc += 0.5 * sh.w2d[k0] * e * e;                // g(x_0), coordinate k0
     }
   }
   acc = warp_sum<double>(acc);
@@ -300,9 +314,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
       if (jbase + i <= N)
 #pragma unroll
         for (int k = 0; k < D; ++k) o[(size_t)(jbase + i) * D + k] = x[i][k];
-    if (gl == 0)
-#pragma unroll
-      for (int k = 0; k < D; ++k) o[k] = x0[k];
+    if (own0) o[k0] = x0;
   }
   if (a.traj_p != nullptr) {
     T* o = a.traj_p + pt.traj;
@@ -311,9 +323,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
       if (jbase + i <= N)
 #pragma unroll
         for (int k = 0; k < D; ++k) o[(size_t)(jbase + i) * D + k] = p[i][k];
-    if (gl == 0)
-#pragma unroll
-      for (int k = 0; k < D; ++k) o[k] = T(0);
+    if (own0) o[k0] = T(0);
   }
 }
 
@@ -322,10 +332,9 @@ __global__ void __launch_bounds__(warp_block_threads<G>())
 lax_warp_kernel(const SolveArgs<T> a) {
   __shared__ WarpShared<T, F, D, G> sh;
   F::load_shared(a, sh.fam);
-  for (int k = threadIdx.x; k < D; k += blockDim.x) {
-    const double w2 = a.W2[k], c = a.c[k];
-    sh.w2d[k] = w2;
-    sh.cd[k] = c;
+  for (int k = threadIdx.x; k < WarpShared<T, F, D, G>::DP; k += blockDim.x) {
+    const double w2 = k < D ? a.W2[k] : 0.0, c = k < D ? a.c[k] : 0.0;
+    if (k < D) { sh.w2d[k] = w2; sh.cd[k] = c; }
     sh.g_off[k] = T(a.tau * w2 * c);
     sh.g_inv[k] = T(1.0 / (1.0 + a.tau * w2));
   }

@@ -23,10 +23,13 @@ def _plan(rw, precision, **ov):
     return plan, xq, t
 
 
-def _small_mix(B=90, seed=11):
+def _small_mix(B=90, seed=11, fp64=False):
+    """N from every class, with ragged values; FP64 tanh drift at d = 32 keeps
+    N <= 200 (its shared-memory kernel's limit in FP64)."""
     rw = W.ragged_mix(B=B, seed=seed)
     r = np.random.default_rng(seed)
-    rw["N_of"] = r.choice(np.array([3, 17, 40, 64, 100, 130, 256], dtype=np.int32), size=B)
+    choices = [3, 17, 40, 64, 100, 130, 200] if fp64 else [3, 17, 40, 64, 100, 130, 256]
+    rw["N_of"] = r.choice(np.array(choices, dtype=np.int32), size=B)
     return rw
 
 
@@ -37,7 +40,7 @@ def _groups(rw):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_ragged_fixed_iterations_elementwise(precision):
-    rw = _small_mix()
+    rw = _small_mix(fp64=precision == "fp64")
     K = 40
     plan, xq, t = _plan(rw, precision, tol=0.0, max_iter=K, check_every=K)
     out = {k: v.cpu().numpy() for k, v in plan.solve(xq, t, return_traj=True).items()}
@@ -55,7 +58,7 @@ def test_ragged_fixed_iterations_elementwise(precision):
 
 
 def test_ragged_fp64_same_stop_and_fp32_converged():
-    rw = _small_mix(B=45, seed=12)
+    rw = _small_mix(B=45, seed=12, fp64=True)
     rw["max_iter"] = 6000
     plan64, xq, t = _plan(rw, "fp64")
     o64 = {k: v.cpu().numpy() for k, v in plan64.solve(xq, t).items()}
@@ -136,6 +139,10 @@ def test_ragged_invalid_arguments():
     rw = _small_mix(B=10, seed=15)
     probs = [binding.Problem.from_workload(p) for p in rw["problems"]]
     opts = binding.make_opts(sigma=1.0, tau=0.2)
+    too_big = rw["N_of"].copy(); too_big[:] = 256; prob_of = np.full(10, 2, dtype=np.int32)
+    with pytest.raises(binding.HJError) as e:     # FP64 tanh d = 32 at N = 256 exceeds shared memory
+        binding.RaggedPlan(probs, prob_of, too_big, binding.make_opts(sigma=1.0, tau=0.2, precision="fp64"))
+    assert e.value.code == binding.HJ_ERR_UNSUPPORTED
     bad_N = rw["N_of"].copy(); bad_N[3] = 300
     with pytest.raises(binding.HJError):
         binding.RaggedPlan(probs, rw["prob_of"], bad_N, opts)
