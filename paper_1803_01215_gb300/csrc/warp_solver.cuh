@@ -22,6 +22,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "families.cuh"
 #include "hj_internal.cuh"
 
@@ -168,15 +170,10 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   constexpr int DP = WarpShared<T, F, D, G>::DP;
   constexpr int kLanes = 32 * G;
 
-  int k_it = 0;
-  int8_t st = HJ_POINT_MAX_ITER;
-  const int max_iter = a.max_iter, check_every = a.check_every;
-  int until_check = check_every;
-  while (k_it < max_iter) {
-    ++k_it;
-    const bool chk = (--until_check == 0) || (k_it == max_iter);
-    if (until_check == 0) until_check = check_every;
-    T rx = T(0), rp = T(0);
+  // One iteration; CHK adds the squared increments (test iterations only, so
+  // the plain iterations carry no residual code at all).
+  auto step = [&](auto chk_tag, T& rx, T& rp) {
+    constexpr bool CHK = decltype(chk_tag)::value;
     typename F::Ctx ctx[NPL];
     // ---- z_{j-1} of the first owned node: the left lane's slot (z^k of its last node)
     slot_store<T, D>(zslot + gl * DP, z[NPL - 1]);
@@ -194,7 +191,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
           v[k] = p[i][k] + sig * (z[i][k] - zm);
         }
         fam.prox(ctx[i], pc, x[i], v);
-        if (chk) {
+        if constexpr (CHK) {
 #pragma unroll
           for (int k = 0; k < D; ++k) { const T e = v[k] - p[i][k]; rp += e * e; }
         }
@@ -215,7 +212,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     if (own0) {
       // x_0 <- prox_{tau g}(x_0 + tau p_1), coordinate k0; p_1 is lane 0's slot
       const T xn = (x0 + tau * pslot[k0] + goff) * ginv;      // (D^T p)_0 = -p_1
-      if (chk) { const T e = xn - x0; rx += e * e; }
+      if constexpr (CHK) { const T e = xn - x0; rx += e * e; }
       z0 = xn + th * (xn - x0);
       x0 = xn;
       x0slot[k0] = z0;
@@ -245,26 +242,38 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         }
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          if (chk) { const T e = xn[k] - x[i][k]; rx += e * e; }
+          if constexpr (CHK) { const T e = xn[k] - x[i][k]; rx += e * e; }
           z[i][k] = xn[k] + th * (xn[k] - x[i][k]);
           x[i][k] = xn[k];
         }
       }
     }
-    if (chk) {
-      // lane partials summed across the warp in the iterate type, then in FP64
-      double sx = (double)warp_sum<T>(rx);
-      double sp = (double)warp_sum<T>(rp);
-      if constexpr (G > 1) {
-        if (lane == 0) { sh.red[wg][0] = sx; sh.red[wg][1] = sp; }
-        __syncthreads();
-        sx = 0.0; sp = 0.0;
+  };
+
+  // Test after every check_every-th iteration and after iteration max_iter.
+  int k_it = 0;
+  int8_t st = HJ_POINT_MAX_ITER;
+  const int max_iter = a.max_iter, check_every = a.check_every;
+  while (k_it < max_iter) {
+    const int left = max_iter - k_it;
+    const int plain = (check_every - 1 < left - 1) ? check_every - 1 : left - 1;
+    T dummy_x = T(0), dummy_p = T(0);
+    for (int r = 0; r < plain; ++r) step(std::integral_constant<bool, false>{}, dummy_x, dummy_p);
+    T rx = T(0), rp = T(0);
+    step(std::integral_constant<bool, true>{}, rx, rp);
+    k_it += plain + 1;
+    // lane partials summed across the warp in the iterate type, then in FP64
+    double sx = (double)warp_sum<T>(rx);
+    double sp = (double)warp_sum<T>(rp);
+    if constexpr (G > 1) {
+      if (lane == 0) { sh.red[wg][0] = sx; sh.red[wg][1] = sp; }
+      __syncthreads();
+      sx = 0.0; sp = 0.0;
 #pragma unroll
-        for (int w = 0; w < G; ++w) { sx += sh.red[w][0]; sp += sh.red[w][1]; }
-      }
-      if (!(isfinite(sx) && isfinite(sp))) { st = HJ_POINT_NONFINITE; break; }
-      if (sx < a.tol && sp < a.tol) { st = HJ_POINT_CONVERGED; break; }
+      for (int w = 0; w < G; ++w) { sx += sh.red[w][0]; sp += sh.red[w][1]; }
     }
+    if (!(isfinite(sx) && isfinite(sp))) { st = HJ_POINT_NONFINITE; break; }
+    if (sx < a.tol && sp < a.tol) { st = HJ_POINT_CONVERGED; break; }
   }
 
   // ---- value (fval of Algorithm 1) in FP64, and outputs
