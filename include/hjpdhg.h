@@ -246,6 +246,36 @@ hj_status hj_ragged_autotune(hj_ragged_plan plan, const double* xq, const double
 /* Destroy a plan (NULL accepted); synchronises its device first.            */
 hj_status hj_ragged_plan_destroy(hj_ragged_plan plan);
 
+/* ---------------------------------------------------------------- no device allocation
+ * hj_solve_batch for callers that cannot allocate device memory: code running
+ * under a device-memory budget fixed before it starts (an allocator owned by a
+ * host framework), a real-time loop that forbids allocation after start-up, or
+ * a plug-in that only receives buffers it did not allocate.  hj_problem_create
+ * allocates (the parameter copies and the persistent kernels' work counter);
+ * this entry point allocates nothing: it copies the problem's parameters and
+ * keeps the work counter in one fixed array of hj_static_scratch_bytes() bytes
+ * that the library declares in device memory (every GPU that loads the library
+ * holds it until the process exits), then runs the same kernels as
+ * hj_solve_batch.  The paper has no counterpart; it is a deployment variant.
+ *   family, d, dyn, n_dyn, W, c   (host) as hj_problem_create.
+ *   B, xq, t, N, opts, V, iters, status, traj_x, traj_p, stream
+ *                                 as hj_solve_batch (no warm start; the launch
+ *                                 shape is the default for (precision, N)).
+ * The first call on a device looks up the array's device address (set-up, once
+ * per device, with that device current): make that first call before any
+ * stream capture.  Every call shares the one array and overwrites it (the work
+ * counter is cleared on each call): calls that overlap on the GPU, from any
+ * stream or thread, race and must be serialised by the caller.
+ * Errors: as hj_solve_batch; HJ_ERR_UNSUPPORTED when the parameters do not fit
+ * the array (tanh drift: 3d + 3d^2 doubles for FP64, 3d + 2d^2 doubles for
+ * FP32, plus alignment: d <= 51 in FP64, d <= 62 in FP32).                   */
+int64_t hj_static_scratch_bytes(void);
+hj_status hj_solve_batch_static(int32_t family, int32_t d, const double* dyn, int64_t n_dyn,
+                                const double* W, const double* c, int64_t B, const double* xq,
+                                const double* t, int32_t N, const hj_solver_opts* opts,
+                                double* V, int32_t* iters, int8_t* status, void* traj_x,
+                                void* traj_p, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* hj_status_str(hj_status s);
 

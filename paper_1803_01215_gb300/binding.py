@@ -38,7 +38,8 @@ EXPORTED = ("hj_problem_create", "hj_problem_destroy", "hj_solve_batch",
             "hj_set_launch_shape", "hj_get_launch_shape", "hj_autotune",
             "hj_ragged_plan_create", "hj_ragged_plan_layout", "hj_ragged_plan_bucket",
             "hj_ragged_solve", "hj_ragged_autotune", "hj_ragged_plan_destroy",
-            "hj_solve_grad", "hj_status_str", "hj_version")
+            "hj_solve_grad", "hj_solve_batch_static", "hj_static_scratch_bytes",
+            "hj_status_str", "hj_version")
 
 
 def _lib():
