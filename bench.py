@@ -37,6 +37,11 @@ UNIT = "solves/s"
 # sin/cos are transcendental and not counted.  Derivation in the design doc.
 QC_FLOPS_PER_NODE_ITER = 240
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the timed FP32
+# kernel (lax_warp_kernel<float, FamQuadcopter, 12, 1, 2>) from the ncu capture
+# summarised in profiles/quadcopter12d_B4096_N64_fp32_warp_kernel.md; set to
+# None whenever that kernel changes until it is captured again.
+QC_TRAFFIC_BYTES = 493312 + 2560
 
 
 def workload_config():
@@ -276,7 +281,8 @@ def main():
         "fp32_over_fp64": value / value64 if value64 > 0 else None,
         "converged_accurate": n_ok32, "mean_iters": iters_sum / (B * world),
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved_tflops / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / peak,
+                     "traffic": QC_TRAFFIC_BYTES,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)"},
         "gpu_launches": args.steps,
         "e2e": {"value": n_ok32 / (e2e_ms * 1e-3), "unit": UNIT,
