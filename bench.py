@@ -41,7 +41,7 @@ SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # kernel (lax_warp_kernel<float, FamQuadcopter, 12, 1, 2>) from the ncu capture
 # summarised in profiles/quadcopter12d_B4096_N64_fp32_warp_kernel.md; set to
 # None whenever that kernel changes until it is captured again.
-QC_TRAFFIC_BYTES = 493312 + 2560
+QC_TRAFFIC_BYTES = None
 
 
 def workload_config():
@@ -99,6 +99,106 @@ def run_cpu_oracle(w, n_points, budget_s=20.0):
     return total_pts / total_t, total_pts, total_t
 
 
+def _events_time(fn, steps, warmup, flush, stream):
+    """Mean CUDA-event time (ms) of fn() over `steps` runs after `warmup`, with
+    the L2 flushed (outside the events) before each timed run."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps
+
+
+def measure_other_configs(dev, flush, stream, peak):
+    """The remaining workloads of the hot path, each timed like the headline:
+    the d = 2 closed-form batch (FP64), the tanh-drift scaling batches (FP32, and
+    FP64 on a 2048-point slice), the 100 000-point ragged batch (one graph
+    launch) and the adjoint of the 12-D batch."""
+    import torch
+    from paper_1803_01215_gb300 import binding
+    out = {}
+
+    def run_uniform(w, precision, npts=None):
+        if npts is not None:
+            w = W.subset(w, np.arange(npts))
+        prob = binding.Problem.from_workload(w)
+        opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], tol=w["tol"],
+                                 max_iter=w["max_iter"], check_every=w["check_every"],
+                                 seed=w["seed"], init_radius=w["init_radius"], precision=precision)
+        xq = torch.as_tensor(w["xq"], device=dev)
+        t = torch.as_tensor(w["t"], device=dev)
+        res = binding.solve_batch(prob, xq, t, int(w["N"]), opts, return_traj=True)
+        ms = _events_time(lambda: binding.solve_batch(prob, xq, t, int(w["N"]), opts, out=res,
+                                                      stream=stream), 2, 1, flush, stream)
+        conv = int((res["status"] == 0).sum().item())
+        iters = int(res["iters"].to(torch.int64).sum().item())
+        return ms, conv, iters, res
+
+    w1 = W.quadratic_closed_form()
+    ms, conv, _, res = run_uniform(w1, "fp64")
+    exact = torch.as_tensor((w1["xq"] ** 2).sum(1) / (2 * (1 + w1["t"])), device=dev)
+    out["quadratic_d2_B64_N20_fp64"] = {
+        "solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
+        "max_abs_err_vs_closed_form": float((res["V"] - exact).abs().max().item())}
+
+    for d, seed in ((32, 3), (64, 4), (100, 5)):
+        w = W.tanh_drift(d, seed=seed)
+        ms, conv, iters, _ = run_uniform(w, "fp32")
+        flops = iters * 32 * (4 * d * d + 14 * d)
+        ms64, conv64, _, _ = run_uniform(w, "fp64", npts=2048)
+        out[f"tanh_drift_d{d}_B16384_N32"] = {
+            "fp32": {"solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
+                     "tflops": flops / (ms * 1e-3) / 1e12,
+                     "frac_of_fp32_peak": flops / (ms * 1e-3) / 1e12 / peak},
+            "fp64_2048_points": {"solves_per_s": conv64 / (ms64 * 1e-3), "ms_per_step": ms64,
+                                 "converged": conv64},
+            "fp32_over_fp64": (conv / ms) / (conv64 / ms64) if conv64 else None}
+
+    rw = W.ragged_mix()
+    probs = [binding.Problem.from_workload(p) for p in rw["problems"]]
+    ropts = binding.make_opts(sigma=rw["sigma"], tau=rw["tau"], tol=rw["tol"],
+                              max_iter=rw["max_iter"], check_every=rw["check_every"], seed=rw["seed"])
+    plan = binding.RaggedPlan(probs, rw["prob_of"], rw["N_of"], ropts)
+    xq = torch.as_tensor(plan.pack_xq(rw["xq"]), device=dev)
+    t = torch.as_tensor(rw["t"], device=dev)
+    plan.autotune(xq, t, repeats=1)
+    res = plan.solve(xq, t, return_traj=True)
+    ms = _events_time(lambda: plan.solve(xq, t, out=res, stream=stream), 2, 1, flush, stream)
+    conv = int((res["status"] == 0).sum().item())
+    out["ragged_B100000_d4_12_32_N16_256"] = {
+        "solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
+        "graph_launches_per_step": 1, "buckets": len(plan.buckets())}
+
+    wq = W.quadcopter()
+    prob = binding.Problem.from_workload(wq)
+    opts = binding.make_opts(sigma=wq["sigma"], tau=wq["tau"], tol=wq["tol"],
+                             max_iter=wq["max_iter"], check_every=wq["check_every"], seed=wq["seed"])
+    xq = torch.as_tensor(wq["xq"], device=dev)
+    t = torch.as_tensor(wq["t"], device=dev)
+    B = len(wq["xq"])
+    wts = torch.full((B,), 1.0 / B, dtype=torch.float64, device=dev)
+    res = binding.solve_batch(prob, xq, t, 64, opts, return_traj=True)
+    g_ms = _events_time(lambda: binding.solve_grad(prob, t, 64, "fp32", res["traj_x"], res["traj_p"],
+                                                   wts, stream=stream), 3, 1, flush, stream)
+    both = _events_time(lambda: (binding.solve_batch(prob, xq, t, 64, opts, out=res, stream=stream),
+                                 binding.solve_grad(prob, t, 64, "fp32", res["traj_x"], res["traj_p"],
+                                                    wts, stream=stream)), 2, 1, flush, stream)
+    traj_bytes = 2 * B * 65 * 12 * 4
+    out["adjoint_quadcopter_B4096_N64"] = {
+        "value_and_grad_per_s": B / (both * 1e-3), "ms_solve_plus_grad": both,
+        "ms_grad_kernel": g_ms, "grad_kernel_gbs": traj_bytes / (g_ms * 1e-3) / 1e9}
+    return out
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -136,6 +236,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-other-configs", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -290,6 +391,8 @@ def main():
                 "d2h_bytes_per_step": int(V_h.numel() * 8 + st_h.numel())},
         "clocks": clocks,
     }
+    if not args.no_other_configs:
+        line["configs"] = measure_other_configs(dev, flush, stream, peak)
     if not args.no_cpu_baseline:
         v, n, tsec = run_cpu_oracle(w, 16, budget_s=15.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -103,7 +103,15 @@ __device__ __forceinline__ void slot_load(const T* src, T (&v)[D]) {
   }
 }
 
-template <typename T, class F, int D, int NPL, int G>
+// relaxation z = x_new + theta (x_new - x); TH1: theta = 1 (the paper's choice,
+// Section 6), one fused multiply-add per coordinate
+template <typename T, bool TH1>
+__device__ __forceinline__ T relax(T xn, T xo, T th) {
+  if constexpr (TH1) return T(2) * xn - xo;
+  else return xn + th * (xn - xo);
+}
+
+template <typename T, class F, int D, int NPL, int G, bool TH1>
 __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam, int64_t item,
                                             int lane, int wg, WarpShared<T, F, D, G>& sh) {
   const PointRef<T> pt = point_ref(a, item);
@@ -213,7 +221,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
       // x_0 <- prox_{tau g}(x_0 + tau p_1), coordinate k0; p_1 is lane 0's slot
       const T xn = (x0 + tau * pslot[k0] + goff) * ginv;      // (D^T p)_0 = -p_1
       if constexpr (CHK) { const T e = xn - x0; rx += e * e; }
-      z0 = xn + th * (xn - x0);
+      z0 = relax<T, TH1>(xn, x0, th);
       x0 = xn;
       x0slot[k0] = z0;
     }
@@ -243,7 +251,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           if constexpr (CHK) { const T e = xn[k] - x[i][k]; rx += e * e; }
-          z[i][k] = xn[k] + th * (xn[k] - x[i][k]);
+          z[i][k] = relax<T, TH1>(xn[k], x[i][k], th);
           x[i][k] = xn[k];
         }
       }
@@ -336,7 +344,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   }
 }
 
-template <typename T, class F, int D, int NPL, int G>
+template <typename T, class F, int D, int NPL, int G, bool TH1>
 __global__ void __launch_bounds__(warp_block_threads<G>())
 lax_warp_kernel(const SolveArgs<T> a) {
   __shared__ WarpShared<T, F, D, G> sh;
@@ -364,15 +372,15 @@ lax_warp_kernel(const SolveArgs<T> a) {
       item = (int64_t)sh.item;
     }
     if (item >= a.B) break;
-    solve_point<T, F, D, NPL, G>(a, fam, item, lane, wg, sh);
+    solve_point<T, F, D, NPL, G, TH1>(a, fam, item, lane, wg, sh);
   }
 }
 
-template <typename T, class F, int D, int NPL, int G>
-hj_status launch_warp_cfg(const SolveArgs<T>& a, cudaStream_t s) {
+template <typename T, class F, int D, int NPL, int G, bool TH1>
+hj_status launch_warp_cfg_th(const SolveArgs<T>& a, cudaStream_t s) {
   static int blocks_per_sm = -1;
   static int num_sms = 0;
-  auto kern = lax_warp_kernel<T, F, D, NPL, G>;
+  auto kern = lax_warp_kernel<T, F, D, NPL, G, TH1>;
   constexpr int threads = warp_block_threads<G>();
   if (blocks_per_sm < 0) {
     int dev = 0;
@@ -391,6 +399,13 @@ hj_status launch_warp_cfg(const SolveArgs<T>& a, cudaStream_t s) {
   if (grid <= 0) return HJ_OK;
   kern<<<grid, threads, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? HJ_OK : HJ_ERR_CUDA;
+}
+
+// theta = 1 (the paper's choice) gets its own kernel
+template <typename T, class F, int D, int NPL, int G>
+hj_status launch_warp_cfg(const SolveArgs<T>& a, cudaStream_t s) {
+  return a.theta == 1.0 ? launch_warp_cfg_th<T, F, D, NPL, G, true>(a, s)
+                        : launch_warp_cfg_th<T, F, D, NPL, G, false>(a, s);
 }
 
 // Every (G, NPL) the library instantiates: FP32 G in {1,2,4,8} x NPL in {1,2};
