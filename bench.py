@@ -99,9 +99,10 @@ def run_cpu_oracle(w, n_points, budget_s=20.0):
     return total_pts / total_t, total_pts, total_t
 
 
-def _events_time(fn, steps, warmup, flush, stream):
+def _events_time(fn, steps, warmup, flush, stream, tag):
     """Mean CUDA-event time (ms) of fn() over `steps` runs after `warmup`, with
-    the L2 flushed (outside the events) before each timed run."""
+    the L2 flushed (outside the events) before each timed run; the timed runs sit
+    in the NVTX range `tag` so a profiler can select them."""
     import torch
     for _ in range(warmup):
         fn()
@@ -110,9 +111,11 @@ def _events_time(fn, steps, warmup, flush, stream):
     for _ in range(steps):
         flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(tag)
         e0.record(stream)
         fn()
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         e1.synchronize()
         tot += e0.elapsed_time(e1)
     return tot / steps
@@ -127,7 +130,7 @@ def measure_other_configs(dev, flush, stream, peak):
     from paper_1803_01215_gb300 import binding
     out = {}
 
-    def run_uniform(w, precision, npts=None):
+    def run_uniform(w, precision, tag, npts=None):
         if npts is not None:
             w = W.subset(w, np.arange(npts))
         prob = binding.Problem.from_workload(w)
@@ -138,13 +141,13 @@ def measure_other_configs(dev, flush, stream, peak):
         t = torch.as_tensor(w["t"], device=dev)
         res = binding.solve_batch(prob, xq, t, int(w["N"]), opts, return_traj=True)
         ms = _events_time(lambda: binding.solve_batch(prob, xq, t, int(w["N"]), opts, out=res,
-                                                      stream=stream), 2, 1, flush, stream)
+                                                      stream=stream), 2, 1, flush, stream, tag)
         conv = int((res["status"] == 0).sum().item())
         iters = int(res["iters"].to(torch.int64).sum().item())
         return ms, conv, iters, res
 
     w1 = W.quadratic_closed_form()
-    ms, conv, _, res = run_uniform(w1, "fp64")
+    ms, conv, _, res = run_uniform(w1, "fp64", "timed_quadratic_d2")
     exact = torch.as_tensor((w1["xq"] ** 2).sum(1) / (2 * (1 + w1["t"])), device=dev)
     out["quadratic_d2_B64_N20_fp64"] = {
         "solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
@@ -152,9 +155,9 @@ def measure_other_configs(dev, flush, stream, peak):
 
     for d, seed in ((32, 3), (64, 4), (100, 5)):
         w = W.tanh_drift(d, seed=seed)
-        ms, conv, iters, _ = run_uniform(w, "fp32")
+        ms, conv, iters, _ = run_uniform(w, "fp32", f"timed_tanh_d{d}")
         flops = iters * 32 * (4 * d * d + 14 * d)
-        ms64, conv64, _, _ = run_uniform(w, "fp64", npts=2048)
+        ms64, conv64, _, _ = run_uniform(w, "fp64", f"timed_tanh_d{d}_fp64", npts=2048)
         out[f"tanh_drift_d{d}_B16384_N32"] = {
             "fp32": {"solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
                      "tflops": flops / (ms * 1e-3) / 1e12,
@@ -172,7 +175,8 @@ def measure_other_configs(dev, flush, stream, peak):
     t = torch.as_tensor(rw["t"], device=dev)
     plan.autotune(xq, t, repeats=1)
     res = plan.solve(xq, t, return_traj=True)
-    ms = _events_time(lambda: plan.solve(xq, t, out=res, stream=stream), 2, 1, flush, stream)
+    ms = _events_time(lambda: plan.solve(xq, t, out=res, stream=stream), 2, 1, flush, stream,
+                      "timed_ragged")
     conv = int((res["status"] == 0).sum().item())
     out["ragged_B100000_d4_12_32_N16_256"] = {
         "solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
@@ -188,10 +192,12 @@ def measure_other_configs(dev, flush, stream, peak):
     wts = torch.full((B,), 1.0 / B, dtype=torch.float64, device=dev)
     res = binding.solve_batch(prob, xq, t, 64, opts, return_traj=True)
     g_ms = _events_time(lambda: binding.solve_grad(prob, t, 64, "fp32", res["traj_x"], res["traj_p"],
-                                                   wts, stream=stream), 3, 1, flush, stream)
+                                                   wts, stream=stream), 3, 1, flush, stream,
+                        "timed_grad")
     both = _events_time(lambda: (binding.solve_batch(prob, xq, t, 64, opts, out=res, stream=stream),
                                  binding.solve_grad(prob, t, 64, "fp32", res["traj_x"], res["traj_p"],
-                                                    wts, stream=stream)), 2, 1, flush, stream)
+                                                    wts, stream=stream)), 2, 1, flush, stream,
+                        "timed_solve_grad")
     traj_bytes = 2 * B * 65 * 12 * 4
     out["adjoint_quadcopter_B4096_N64"] = {
         "value_and_grad_per_s": B / (both * 1e-3), "ms_solve_plus_grad": both,

@@ -22,6 +22,9 @@ struct SolveArgs {
   // iteration loop holds no double-derived value the compiler could recompute
   // there (FP64 instructions are ~64x the cost of FP32 ones on this GPU).
   T sigma_t, tau_t, theta_t;
+  // tol rounded up to the iterate type: for a sum s of that type,
+  // (double)s < tol exactly when s < tol_t, so the test needs no FP64 operation.
+  T tol_t;
   int32_t max_iter, check_every, inner_steps;
   uint64_t seed;
   double radius;

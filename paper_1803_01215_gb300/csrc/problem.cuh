@@ -111,6 +111,8 @@ hj::SolveArgs<T> make_args(const hj_problem_s* prob, int64_t B, int32_t N,
   a.B = B; a.N = N; a.d = prob->d;
   a.sigma = o.sigma; a.tau = o.tau; a.theta = o.theta; a.tol = o.tol;
   a.sigma_t = T(o.sigma); a.tau_t = T(o.tau); a.theta_t = T(o.theta);
+  a.tol_t = T(o.tol);
+  if ((double)a.tol_t < o.tol) a.tol_t = std::nextafter(a.tol_t, T(INFINITY));
   a.max_iter = o.max_iter; a.check_every = o.check_every; a.inner_steps = o.inner_steps;
   a.seed = o.seed; a.radius = o.init_radius; a.point_offset = o.point_offset;
   a.xq = xq; a.t = t; a.V = V; a.iters = iters; a.status = status;

@@ -270,18 +270,22 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     T rx = T(0), rp = T(0);
     step(std::integral_constant<bool, true>{}, rx, rp);
     k_it += plain + 1;
-    // lane partials summed across the warp in the iterate type, then in FP64
-    double sx = (double)warp_sum<T>(rx);
-    double sp = (double)warp_sum<T>(rp);
-    if constexpr (G > 1) {
-      if (lane == 0) { sh.red[wg][0] = sx; sh.red[wg][1] = sp; }
+    // lane partials summed across the warp in the iterate type; one warp: the
+    // test against tol_t is the FP64 test of that sum; several warps: the warp
+    // sums are added in FP64
+    const T wx = warp_sum<T>(rx), wp = warp_sum<T>(rp);
+    if constexpr (G == 1) {
+      if (!(isfinite(wx) && isfinite(wp))) { st = HJ_POINT_NONFINITE; break; }
+      if (wx < a.tol_t && wp < a.tol_t) { st = HJ_POINT_CONVERGED; break; }
+    } else {
+      if (lane == 0) { sh.red[wg][0] = (double)wx; sh.red[wg][1] = (double)wp; }
       __syncthreads();
-      sx = 0.0; sp = 0.0;
+      double sx = 0.0, sp = 0.0;
 #pragma unroll
       for (int w = 0; w < G; ++w) { sx += sh.red[w][0]; sp += sh.red[w][1]; }
+      if (!(isfinite(sx) && isfinite(sp))) { st = HJ_POINT_NONFINITE; break; }
+      if (sx < a.tol && sp < a.tol) { st = HJ_POINT_CONVERGED; break; }
     }
-    if (!(isfinite(sx) && isfinite(sp))) { st = HJ_POINT_NONFINITE; break; }
-    if (sx < a.tol && sp < a.tol) { st = HJ_POINT_CONVERGED; break; }
   }
 
   // ---- value (fval of Algorithm 1) in FP64, and outputs

@@ -295,3 +295,27 @@ def test_autotune_picks_an_instantiated_shape():
     with pytest.raises(binding.HJError) as e:
         binding.set_launch_shape(prob, "fp64", 64, 1, 2)       # no FP64 instantiation with NPL 2
     assert e.value.code == binding.HJ_ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------- several points per CTA
+@pytest.mark.parametrize("d,B,precision", [(32, 700, "fp32"), (13, 700, "fp64"), (64, 330, "fp32")])
+def test_shared_memory_kernel_with_several_points_per_cta(d, B, precision):
+    """Batches large enough for the shared-memory kernel to hold 2 or 4 points per
+    CTA (slots refilled as points finish): every point element-wise against the
+    oracle after a fixed number of iterations, and values at the same stop."""
+    w = _custom("tanh_drift", d, 24, B=B, seed=51)
+    K = 60
+    g = gpu(w, precision, tol=0.0, max_iter=K, check_every=K)
+    o = oracle_same_stop(w, tol=0.0, max_iter=K, check_every=K)
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    assert np.all(g["iters"] == K)
+    assert np.max(np.abs(g["traj_x"] - o["x"])) <= tol
+    assert np.max(np.abs(g["traj_p"] - o["p"])) <= tol
+    # the same stop, with points finishing at different iterations and slots refilled
+    g = gpu(w, precision, max_iter=3000)
+    idx = np.arange(0, B, 37)
+    o = oracle_same_stop(W.subset(w, idx), max_iter=3000)
+    same = g["iters"][idx] == o["iters"]
+    assert np.mean(same) >= 0.8
+    bar = 1e-9 if precision == "fp64" else 1e-4
+    assert np.max(value_err(g["V"][idx][same], o["V"][same])) <= bar
