@@ -220,10 +220,11 @@ hj_status hj_ragged_plan_layout(hj_ragged_plan plan, int64_t* xq_offsets, int64_
                                 int32_t* n_buckets);
 
 /* Host outputs for bucket i (each may be NULL): its problem index, largest N,
- * number of points and launch shape (0, 0 = shared-memory kernel).           */
+ * number of points, launch shape (0, 0 = shared-memory kernel) and inner
+ * gradient steps per x-update.                                              */
 hj_status hj_ragged_plan_bucket(hj_ragged_plan plan, int32_t i, int32_t* problem, int32_t* n_max,
                                 int64_t* n_points, int32_t* warps_per_point,
-                                int32_t* nodes_per_lane);
+                                int32_t* nodes_per_lane, int32_t* inner_steps);
 
 /* Solve the batch: xq (device, packed), t (device, [B]); V, iters, status
  * (device, [B]); traj_x, traj_p (device, packed, may be NULL).  The first call
@@ -238,10 +239,14 @@ hj_status hj_ragged_solve(hj_ragged_plan plan, const double* xq, const double* t
 
 /* Autotune every bucket that runs the register-resident kernel: time each
  * instantiated launch shape on the bucket's own points (`repeats` timed runs
- * after one warm-up) and keep the fastest.  Synchronises `stream`; allocates
- * and frees scratch outputs; drops the captured graph.                       */
+ * after one warm-up) and keep the fastest.  With max_inner_steps > 1 the
+ * inner gradient steps per x-update (1..max_inner_steps, families whose H
+ * depends on x) are tuned too: they change the iterates and iteration counts,
+ * not the fixed point; 1 keeps the plan's option (Section 5.3's single step).
+ * Synchronises `stream`; allocates and frees scratch outputs; drops the
+ * captured graph.                                                            */
 hj_status hj_ragged_autotune(hj_ragged_plan plan, const double* xq, const double* t,
-                             int32_t repeats, void* stream);
+                             int32_t repeats, int32_t max_inner_steps, void* stream);
 
 /* Destroy a plan (NULL accepted); synchronises its device first.            */
 hj_status hj_ragged_plan_destroy(hj_ragged_plan plan);

@@ -66,9 +66,9 @@ def _lib():
         lib.hj_ragged_plan_create.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(P), I64,
                                               PI32, PI32, ctypes.POINTER(SolverOpts)]
         lib.hj_ragged_plan_layout.argtypes = [P, PI64, PI64, PI32]
-        lib.hj_ragged_plan_bucket.argtypes = [P, I32, PI32, PI32, PI64, PI32, PI32]
+        lib.hj_ragged_plan_bucket.argtypes = [P, I32, PI32, PI32, PI64, PI32, PI32, PI32]
         lib.hj_ragged_solve.argtypes = [P, P, P, P, P, P, P, P, P]
-        lib.hj_ragged_autotune.argtypes = [P, P, P, I32, P]
+        lib.hj_ragged_autotune.argtypes = [P, P, P, I32, I32, P]
         lib.hj_ragged_plan_destroy.argtypes = [P]
         for name in ("hj_ragged_plan_create", "hj_ragged_plan_layout", "hj_ragged_plan_bucket",
                      "hj_ragged_solve", "hj_ragged_autotune", "hj_ragged_plan_destroy"):
@@ -266,10 +266,11 @@ class RaggedPlan:
         out = []
         for i in range(self.n_buckets):
             v = [ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(),
-                 ctypes.c_int32()]
+                 ctypes.c_int32(), ctypes.c_int32()]
             _lib().hj_ragged_plan_bucket(self.handle, i, *[ctypes.byref(x) for x in v])
             out.append(dict(problem=v[0].value, n_max=v[1].value, n_points=v[2].value,
-                            warps_per_point=v[3].value, nodes_per_lane=v[4].value))
+                            warps_per_point=v[3].value, nodes_per_lane=v[4].value,
+                            inner_steps=v[5].value))
         return out
 
     def pack_xq(self, xq_list):
@@ -279,10 +280,10 @@ class RaggedPlan:
             out[self.xq_off[b]:self.xq_off[b + 1]] = x
         return out
 
-    def autotune(self, xq, t, repeats=1, stream=None):
+    def autotune(self, xq, t, repeats=1, max_inner_steps=1, stream=None):
         s = stream if stream is not None else torch.cuda.current_stream(xq.device)
         r = _lib().hj_ragged_autotune(self.handle, _ptr(xq), _ptr(t), int(repeats),
-                                      ctypes.c_void_p(s.cuda_stream))
+                                      int(max_inner_steps), ctypes.c_void_p(s.cuda_stream))
         if r != HJ_OK:
             raise HJError(r, "hj_ragged_autotune")
 

@@ -26,6 +26,78 @@ __device__ __forceinline__ void sin_cos<double>(double x, double* s, double* c) 
   sincos(x, s, c);
 }
 
+// Elementwise operations on coordinate arrays.  FP32 issues the packed
+// two-wide instructions (one instruction per pair of coordinates, each element
+// rounded once exactly as the scalar operation); FP64 and odd tails are scalar.
+template <typename T, int D>
+__device__ __forceinline__ void v_sub(T (&r)[D], const T (&a)[D], const T (&b)[D]) {
+  int k0 = 0;
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k + 1 < D; k += 2) {
+      const float2 o = __fadd2_rn(make_float2(a[k], a[k + 1]), make_float2(-b[k], -b[k + 1]));
+      r[k] = o.x; r[k + 1] = o.y;
+    }
+    k0 = D - D % 2;
+  }
+#pragma unroll
+  for (int k = k0; k < D; ++k) r[k] = a[k] - b[k];
+}
+
+// r = s * x + y
+template <typename T, int D>
+__device__ __forceinline__ void v_fma(T (&r)[D], T s, const T (&x)[D], const T (&y)[D]) {
+  int k0 = 0;
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k + 1 < D; k += 2) {
+      const float2 o = __ffma2_rn(make_float2(s, s), make_float2(x[k], x[k + 1]),
+                                  make_float2(y[k], y[k + 1]));
+      r[k] = o.x; r[k + 1] = o.y;
+    }
+    k0 = D - D % 2;
+  }
+#pragma unroll
+  for (int k = k0; k < D; ++k) r[k] = fma(s, x[k], y[k]);
+}
+
+// r = s * x - y
+template <typename T, int D>
+__device__ __forceinline__ void v_fms(T (&r)[D], T s, const T (&x)[D], const T (&y)[D]) {
+  int k0 = 0;
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k + 1 < D; k += 2) {
+      const float2 o = __ffma2_rn(make_float2(s, s), make_float2(x[k], x[k + 1]),
+                                  make_float2(-y[k], -y[k + 1]));
+      r[k] = o.x; r[k + 1] = o.y;
+    }
+    k0 = D - D % 2;
+  }
+#pragma unroll
+  for (int k = k0; k < D; ++k) r[k] = fma(s, x[k], -y[k]);
+}
+
+// acc += sum_k e_k^2 (pairs accumulated two-wide, folded at the end)
+template <typename T, int D>
+__device__ __forceinline__ T v_sumsq(const T (&e)[D]) {
+  T acc = T(0);
+  int k0 = 0;
+  if constexpr (sizeof(T) == 4) {
+    float2 a2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k + 1 < D; k += 2) {
+      const float2 v = make_float2(e[k], e[k + 1]);
+      a2 = __ffma2_rn(v, v, a2);
+    }
+    acc = a2.x + a2.y;
+    k0 = D - D % 2;
+  }
+#pragma unroll
+  for (int k = k0; k < D; ++k) acc = fma(e[k], e[k], acc);
+  return acc;
+}
+
 // a / b; FP32 uses the fast reciprocal-based division (2 ulp).
 template <typename T>
 __device__ __forceinline__ T fdiv(T a, T b) { return a / b; }
@@ -127,12 +199,26 @@ struct FamQuadcopter {
   __device__ __forceinline__ void prox(const Ctx& c, const PC& pc, const T (&x)[D],
                                        T (&v)[D]) const {
     const T lam = pc.lam, ial = pc.ial;
+    if constexpr (sizeof(T) == 4) {
+      // rows 0-5: (v - lam x_{6..11}) * ial, rows 9-10 scaled, two-wide
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v[k] = (v[k] - lam * x[6 + k]) * ial;
+      for (int k = 0; k < 6; k += 2) {
+        const float2 t = __ffma2_rn(make_float2(-lam, -lam), make_float2(x[6 + k], x[7 + k]),
+                                    make_float2(v[k], v[k + 1]));
+        const float2 o = __fmul2_rn(t, make_float2(ial, ial));
+        v[k] = o.x; v[k + 1] = o.y;
+      }
+      const float2 r = __fmul2_rn(make_float2(v[9], v[10]), make_float2(pc.irate, pc.irate));
+      v[9] = r.x; v[10] = r.y;
+      v[11] *= pc.irate;
+    } else {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v[3 + k] = (v[3 + k] - lam * x[9 + k]) * ial;
+      for (int k = 0; k < 3; ++k) v[k] = (v[k] - lam * x[6 + k]) * ial;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v[9 + k] *= pc.irate;
+      for (int k = 0; k < 3; ++k) v[3 + k] = (v[3 + k] - lam * x[9 + k]) * ial;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v[9 + k] *= pc.irate;
+    }
     const T w0 = v[6] - pc.lam_ah * c.a[0];
     const T w1 = v[7] - pc.lam_ah * c.a[1];
     const T w2 = v[8] - (pc.lam_ah * c.a[2] - pc.lam_gz);

@@ -36,6 +36,7 @@ struct Bucket {
   std::vector<int32_t> ids;     // host copy of the point ids
   int32_t* d_ids = nullptr;
   hj::WarpConfig cfg{0, 0};     // {0, 0}: shared-memory kernel
+  int inner_steps = 0;          // 0: the plan's option
 };
 
 int n_class(int N) {
@@ -88,6 +89,7 @@ hj_status launch_bucket(hj_ragged_plan_s* p, size_t bi, hj::WarpConfig cfg, cons
   hj_problem_s* prob = p->probs[b.prob];
   hj::SolveArgs<T> a = make_args<T>(prob, (int64_t)b.ids.size(), b.nmax, p->opts, xq, t, V, iters,
                                     status, traj_x, traj_p, nullptr, nullptr);
+  if (b.inner_steps > 0) a.inner_steps = b.inner_steps;
   a.idx = b.d_ids;
   a.Nv = p->d_N;
   a.xq_off = p->d_xq_off;
@@ -223,7 +225,7 @@ hj_status hj_ragged_plan_layout(hj_ragged_plan plan, int64_t* xq_offsets, int64_
 
 hj_status hj_ragged_plan_bucket(hj_ragged_plan plan, int32_t i, int32_t* problem, int32_t* n_max,
                                 int64_t* n_points, int32_t* warps_per_point,
-                                int32_t* nodes_per_lane) {
+                                int32_t* nodes_per_lane, int32_t* inner_steps) {
   if (plan == nullptr || i < 0 || i >= (int32_t)plan->buckets.size()) return HJ_ERR_INVALID_ARG;
   const Bucket& b = plan->buckets[i];
   if (problem) *problem = b.prob;
@@ -231,6 +233,7 @@ hj_status hj_ragged_plan_bucket(hj_ragged_plan plan, int32_t i, int32_t* problem
   if (n_points) *n_points = (int64_t)b.ids.size();
   if (warps_per_point) *warps_per_point = b.cfg.G;
   if (nodes_per_lane) *nodes_per_lane = b.cfg.NPL;
+  if (inner_steps) *inner_steps = b.inner_steps > 0 ? b.inner_steps : plan->opts.inner_steps;
   return HJ_OK;
 }
 
@@ -279,8 +282,9 @@ hj_status hj_ragged_solve(hj_ragged_plan plan, const double* xq, const double* t
 }
 
 hj_status hj_ragged_autotune(hj_ragged_plan plan, const double* xq, const double* t,
-                             int32_t repeats, void* stream) {
+                             int32_t repeats, int32_t max_inner_steps, void* stream) {
   if (plan == nullptr || xq == nullptr || t == nullptr || repeats < 1) return HJ_ERR_INVALID_ARG;
+  if (max_inner_steps < 1 || max_inner_steps > 8) return HJ_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const bool f64 = plan->opts.precision == HJ_PREC_FP64;
   double* V = nullptr;
@@ -301,11 +305,20 @@ hj_status hj_ragged_autotune(hj_ragged_plan plan, const double* xq, const double
     if (b.cfg.G == 0) continue;                       // shared-memory kernel: nothing to tune
     float best = -1.0f;
     hj::WarpConfig best_c = b.cfg;
+    int best_inner = plan->opts.inner_steps;
+    // inner gradient steps per x-update: only when the caller allows more than
+    // one (they change the iterates, not the fixed point) and H depends on x
+    const int inner_hi = (pr->family == HJ_FAMILY_QUADRATIC) ? plan->opts.inner_steps
+                         : (max_inner_steps > 1 ? max_inner_steps : plan->opts.inner_steps);
+    const int inner_lo = (max_inner_steps > 1 && pr->family != HJ_FAMILY_QUADRATIC)
+                         ? 1 : plan->opts.inner_steps;
+    for (int inner = inner_lo; inner <= inner_hi && r == HJ_OK; ++inner)
     for (int npl = 1; npl <= 2 && r == HJ_OK; ++npl) {
       for (int gi = 0; gi < 4 && r == HJ_OK; ++gi) {
         const hj::WarpConfig c{Gs[gi], npl};
         if (!hj::warp_config_available(pr->family, pr->d, c, f64) || b.nmax > 32 * c.G * c.NPL)
           continue;
+        b.inner_steps = inner;
         float tot = 0.0f;
         for (int rep = 0; rep <= repeats && r == HJ_OK; ++rep) {
           if (cudaMemsetAsync(plan->d_counters + bi, 0, sizeof(unsigned long long), s) !=
@@ -324,10 +337,11 @@ hj_status hj_ragged_autotune(hj_ragged_plan plan, const double* xq, const double
           cudaEventElapsedTime(&ms, e0, e1);
           if (rep > 0) tot += ms;
         }
-        if (r == HJ_OK && (best < 0.0f || tot < best)) { best = tot; best_c = c; }
+        if (r == HJ_OK && (best < 0.0f || tot < best)) { best = tot; best_c = c; best_inner = inner; }
       }
     }
     b.cfg = best_c;
+    b.inner_steps = best_inner;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);

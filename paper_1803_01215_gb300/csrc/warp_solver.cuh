@@ -53,7 +53,7 @@ struct WarpShared {
   alignas(16) T zs[kGroups][32 * G][DP];   // z (in the epilogue x) of each lane's last node
   alignas(16) T ps[kGroups][32 * G][DP];   // p of each lane's first node
   alignas(16) T x0s[kGroups][DP];          // z_0 (in the epilogue x_0), one coordinate per lane
-  double red[G][2];
+  T red[G][2];
   double vred[G];
   unsigned long long item;
 };
@@ -192,16 +192,15 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     for (int i = 0; i < NPL; ++i) {
       if (jbase + i <= N) {
         fam.context(x[i], ctx[i]);
-        T v[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          const T zm = (i == 0) ? zl[k] : z[i - 1][k];
-          v[k] = p[i][k] + sig * (z[i][k] - zm);
-        }
+        T v[D], dz[D];
+        if (i == 0) v_sub<T, D>(dz, z[i], zl);
+        else v_sub<T, D>(dz, z[i], z[i > 0 ? i - 1 : 0]);
+        v_fma<T, D>(v, sig, dz, p[i]);                       // p + sigma (z_j - z_{j-1})
         fam.prox(ctx[i], pc, x[i], v);
         if constexpr (CHK) {
-#pragma unroll
-          for (int k = 0; k < D; ++k) { const T e = v[k] - p[i][k]; rp += e * e; }
+          T e[D];
+          v_sub<T, D>(e, v, p[i]);
+          rp += v_sumsq<T, D>(e);
         }
 #pragma unroll
         for (int k = 0; k < D; ++k) p[i][k] = v[k];
@@ -228,32 +227,37 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
       if (jbase + i < N) {
-        T xn[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          const T pn = (i == NPL - 1) ? pr[k] : p[i + 1][k];
-          xn[k] = x[i][k] - tau * (p[i][k] - pn);
-        }
+        T xn[D], dp[D];
+        if (i == NPL - 1) v_sub<T, D>(dp, p[i], pr);
+        else v_sub<T, D>(dp, p[i], p[i + 1 < NPL ? i + 1 : i]);
+        v_fma<T, D>(xn, -tau, dp, x[i]);                     // x - tau (p_j - p_{j+1})
         if (F::kHasGradX) {
           T g[D];
           fam.gradx(ctx[i], x[i], p[i], g);
           T base[D];
 #pragma unroll
-          for (int k = 0; k < D; ++k) { base[k] = xn[k]; xn[k] = base[k] + taud * g[k]; }
+          for (int k = 0; k < D; ++k) base[k] = xn[k];
+          v_fma<T, D>(xn, taud, g, base);                    // + tau delta grad_x H
           for (int s = 1; s < a.inner_steps; ++s) {
             typename F::Ctx c2;
             fam.context(xn, c2);
             fam.gradx(c2, xn, p[i], g);
-#pragma unroll
-            for (int k = 0; k < D; ++k) xn[k] = base[k] + taud * g[k];
+            v_fma<T, D>(xn, taud, g, base);
           }
         }
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          if constexpr (CHK) { const T e = xn[k] - x[i][k]; rx += e * e; }
-          z[i][k] = relax<T, TH1>(xn[k], x[i][k], th);
-          x[i][k] = xn[k];
+        if constexpr (CHK) {
+          T e[D];
+          v_sub<T, D>(e, xn, x[i]);
+          rx += v_sumsq<T, D>(e);
         }
+        if constexpr (TH1) {
+          v_fms<T, D>(z[i], T(2), xn, x[i]);                // z = 2 x_new - x
+        } else {
+#pragma unroll
+          for (int k = 0; k < D; ++k) z[i][k] = relax<T, TH1>(xn[k], x[i][k], th);
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) x[i][k] = xn[k];
       }
     }
   };
@@ -270,22 +274,19 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     T rx = T(0), rp = T(0);
     step(std::integral_constant<bool, true>{}, rx, rp);
     k_it += plain + 1;
-    // lane partials summed across the warp in the iterate type; one warp: the
-    // test against tol_t is the FP64 test of that sum; several warps: the warp
-    // sums are added in FP64
-    const T wx = warp_sum<T>(rx), wp = warp_sum<T>(rp);
-    if constexpr (G == 1) {
-      if (!(isfinite(wx) && isfinite(wp))) { st = HJ_POINT_NONFINITE; break; }
-      if (wx < a.tol_t && wp < a.tol_t) { st = HJ_POINT_CONVERGED; break; }
-    } else {
-      if (lane == 0) { sh.red[wg][0] = (double)wx; sh.red[wg][1] = (double)wp; }
+    // lane partials summed across the warp (and the group's warps) in the
+    // iterate type; the test against tol_t is then exactly the FP64 test of
+    // that sum, so the loop needs no FP64 instruction
+    T sx = warp_sum<T>(rx), sp = warp_sum<T>(rp);
+    if constexpr (G > 1) {
+      if (lane == 0) { sh.red[wg][0] = sx; sh.red[wg][1] = sp; }
       __syncthreads();
-      double sx = 0.0, sp = 0.0;
+      sx = T(0); sp = T(0);
 #pragma unroll
       for (int w = 0; w < G; ++w) { sx += sh.red[w][0]; sp += sh.red[w][1]; }
-      if (!(isfinite(sx) && isfinite(sp))) { st = HJ_POINT_NONFINITE; break; }
-      if (sx < a.tol && sp < a.tol) { st = HJ_POINT_CONVERGED; break; }
     }
+    if (!(isfinite(sx) && isfinite(sp))) { st = HJ_POINT_NONFINITE; break; }
+    if (sx < a.tol_t && sp < a.tol_t) { st = HJ_POINT_CONVERGED; break; }
   }
 
   // ---- value (fval of Algorithm 1) in FP64, and outputs

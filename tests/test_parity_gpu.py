@@ -297,12 +297,13 @@ def test_autotune_picks_an_instantiated_shape():
     assert e.value.code == binding.HJ_ERR_UNSUPPORTED
 
 
-# ---------------------------------------------------------------- several points per CTA
+# ---------------------------------------------------------------- large batches, shared-memory kernel
 @pytest.mark.parametrize("d,B,precision", [(32, 700, "fp32"), (13, 700, "fp64"), (64, 330, "fp32")])
-def test_shared_memory_kernel_with_several_points_per_cta(d, B, precision):
-    """Batches large enough for the shared-memory kernel to hold 2 or 4 points per
-    CTA (slots refilled as points finish): every point element-wise against the
-    oracle after a fixed number of iterations, and values at the same stop."""
+def test_shared_memory_kernel_large_batches(d, B, precision):
+    """Batches larger than the persistent grid (CTAs take several points from the
+    work counter, points finish at different iterations): every point
+    element-wise against the oracle after a fixed number of iterations, and
+    values at the same stop."""
     w = _custom("tanh_drift", d, 24, B=B, seed=51)
     K = 60
     g = gpu(w, precision, tol=0.0, max_iter=K, check_every=K)

@@ -149,3 +149,18 @@ def test_ragged_invalid_arguments():
     bad_p = rw["prob_of"].copy(); bad_p[0] = 7
     with pytest.raises(binding.HJError):
         binding.RaggedPlan(probs, bad_p, rw["N_of"], opts)
+
+
+def test_ragged_autotune_of_inner_steps_keeps_the_fixed_point():
+    """Tuning the inner gradient steps changes the iterates but not the saddle:
+    values agree with the single-step solve to the stopping accuracy."""
+    rw = _small_mix(B=200, seed=16)
+    plan, xq, t = _plan(rw, "fp32", tol=1e-11)
+    ref = plan.solve(xq, t)
+    V0 = ref["V"].cpu().numpy()
+    plan.autotune(xq, t, repeats=1, max_inner_steps=3)
+    assert all(1 <= b["inner_steps"] <= 3 for b in plan.buckets())
+    out = plan.solve(xq, t)
+    ok = (out["status"].cpu().numpy() == 0) & (ref["status"].cpu().numpy() == 0)
+    assert np.mean(ok) >= 0.95
+    assert np.max(value_err(out["V"].cpu().numpy()[ok], V0[ok])) <= 1e-4
