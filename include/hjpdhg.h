@@ -159,6 +159,31 @@ hj_status hj_solve_grad(hj_problem prob, int64_t B, const double* t, int32_t N,
                         const double* dL_dV, double* dW, double* dc, double* ddyn, double* dxq,
                         void* stream);
 
+/* The same gradient, exact for the value after the iterations actually run:
+ * reverse-mode differentiation of Algorithm 1's K_b iterations of each point
+ * (K_b = iters[b] of the forward solve with the same options), with the
+ * iterates (x, p, z) checkpointed every checkpoint_every iterations and each
+ * iterate rebuilt from its checkpoint during the reverse sweep (no iterate is
+ * stored beyond the checkpoints).  The initial guess x^0 = x + r u and the
+ * pinned x_N = x both carry dV/dx.  At a converged point the result agrees
+ * with hj_solve_grad to the stopping accuracy.
+ *   xq, t, N, opts   (device, device, host, host) as in the forward solve.
+ *   iters            (device) [B] iterations of the forward solve.
+ *   max_iters        (host) an upper bound of iters[] (sizes the workspace);
+ *                    a point above it gets dxq = NaN.
+ *   dL_dV, dW, dc, ddyn, dxq  as hj_solve_grad (dxq required).
+ * Families: quadcopter (ddyn: m, a_h, g_z, eps) and quadratic with d <= 4;
+ * N <= 256, and N <= 128 for the quadcopter in FP64; opts->inner_steps == 1
+ * (HJ_ERR_UNSUPPORTED otherwise).
+ * Allocates a workspace of about 3 (N+1) d (max_iters/checkpoint_every + 1)
+ * values per CTA of a grid of 4 CTAs per SM, and synchronises `stream`.
+ * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_STEP_SIZE, HJ_ERR_UNSUPPORTED, HJ_ERR_OOM,
+ * HJ_ERR_CUDA.                                                               */
+hj_status hj_solve_grad_unrolled(hj_problem prob, int64_t B, const double* xq, const double* t,
+                                 int32_t N, const hj_solver_opts* opts, const int32_t* iters,
+                                 int32_t max_iters, int32_t checkpoint_every, const double* dL_dV,
+                                 double* dW, double* dc, double* ddyn, double* dxq, void* stream);
+
 /* Launch shape of the register-resident kernel (quadratic d <= 4, quadcopter,
  * tanh drift d in {2, 4}): a group of `warps_per_point` warps (1, 2, 4, 8)
  * solves one point, each lane holding `nodes_per_lane` time nodes (1 or 2; 1

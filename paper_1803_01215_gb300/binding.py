@@ -38,7 +38,8 @@ EXPORTED = ("hj_problem_create", "hj_problem_destroy", "hj_solve_batch",
             "hj_set_launch_shape", "hj_get_launch_shape", "hj_autotune",
             "hj_ragged_plan_create", "hj_ragged_plan_layout", "hj_ragged_plan_bucket",
             "hj_ragged_solve", "hj_ragged_autotune", "hj_ragged_plan_destroy",
-            "hj_solve_grad", "hj_solve_batch_static", "hj_static_scratch_bytes",
+            "hj_solve_grad", "hj_solve_grad_unrolled", "hj_solve_batch_static",
+            "hj_static_scratch_bytes",
             "hj_status_str", "hj_version")
 
 
@@ -75,6 +76,9 @@ def _lib():
             getattr(lib, name).restype = ctypes.c_int
         lib.hj_solve_grad.argtypes = [P, I64, P, I32, I32, P, P, P, P, P, P, P, P]
         lib.hj_solve_grad.restype = ctypes.c_int
+        lib.hj_solve_grad_unrolled.argtypes = [P, I64, P, P, I32, ctypes.POINTER(SolverOpts), P,
+                                               I32, I32, P, P, P, P, P, P]
+        lib.hj_solve_grad_unrolled.restype = ctypes.c_int
         lib.hj_status_str.restype = ctypes.c_char_p
         lib.hj_status_str.argtypes = [ctypes.c_int]
         lib.hj_version.restype = ctypes.c_int32
@@ -176,6 +180,32 @@ def solve_grad(problem, t, N, precision, traj_x, traj_p, dL_dV, want_dxq=True, s
                              _ptr(out["ddyn"]), _ptr(out["dxq"]), ctypes.c_void_p(s.cuda_stream))
     if r != HJ_OK:
         raise HJError(r, "hj_solve_grad")
+    out["ddyn"] = out["ddyn"][:n_dyn(problem)]
+    return out
+
+
+def solve_grad_unrolled(problem, xq, t, N, opts, iters, dL_dV, checkpoint_every=32,
+                        max_iters=None, stream=None):
+    """hj_solve_grad_unrolled: reverse sweep through the iterations each point ran
+    (iters from the forward solve), checkpoints every `checkpoint_every` iterations.
+    Returns dict(dW, dc, ddyn, dxq) of FP64 device tensors."""
+    dev = xq.device
+    d = problem.d
+    B = xq.shape[0]
+    if max_iters is None:
+        max_iters = int(iters.max().item()) if B else 0
+    out = dict(dW=torch.empty(d, dtype=torch.float64, device=dev),
+               dc=torch.empty(d, dtype=torch.float64, device=dev),
+               ddyn=torch.empty(max(n_dyn(problem), 1), dtype=torch.float64, device=dev),
+               dxq=torch.empty(B, d, dtype=torch.float64, device=dev))
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    r = _lib().hj_solve_grad_unrolled(problem.handle, B, _ptr(xq.contiguous()), _ptr(t.contiguous()),
+                                      int(N), ctypes.byref(opts), _ptr(iters.contiguous()),
+                                      int(max_iters), int(checkpoint_every), _ptr(dL_dV.contiguous()),
+                                      _ptr(out["dW"]), _ptr(out["dc"]), _ptr(out["ddyn"]),
+                                      _ptr(out["dxq"]), ctypes.c_void_p(s.cuda_stream))
+    if r != HJ_OK:
+        raise HJError(r, "hj_solve_grad_unrolled")
     out["ddyn"] = out["ddyn"][:n_dyn(problem)]
     return out
 

@@ -168,6 +168,67 @@ hj_status hj_solve_grad(hj_problem prob, int64_t B, const double* t, int32_t N,
   return hj::launch_value_grad<double>(prob->family, g, s);
 }
 
+hj_status hj_solve_grad_unrolled(hj_problem prob, int64_t B, const double* xq, const double* t,
+                                 int32_t N, const hj_solver_opts* opts, const int32_t* iters,
+                                 int32_t max_iters, int32_t checkpoint_every, const double* dL_dV,
+                                 double* dW, double* dc, double* ddyn, double* dxq, void* stream) {
+  if (prob == nullptr || opts == nullptr || B < 0 || N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;
+  const hj_status oc = check_opts(*opts);
+  if (oc != HJ_OK) return oc;
+  if (max_iters < 0 || checkpoint_every < 1) return HJ_ERR_INVALID_ARG;
+  if (opts->inner_steps != 1) return HJ_ERR_UNSUPPORTED;   // one gradient step per x-update
+  const bool qc = prob->family == HJ_FAMILY_QUADCOPTER;
+  if (!(qc || (prob->family == HJ_FAMILY_QUADRATIC && prob->d <= 4))) return HJ_ERR_UNSUPPORTED;
+  if (dW == nullptr || dc == nullptr || dxq == nullptr || (qc && ddyn == nullptr))
+    return HJ_ERR_INVALID_ARG;
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return HJ_ERR_CUDA;
+  if (cur != prob->device) return HJ_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(dW, 0, prob->d * sizeof(double), s) != cudaSuccess ||
+      cudaMemsetAsync(dc, 0, prob->d * sizeof(double), s) != cudaSuccess ||
+      (qc && cudaMemsetAsync(ddyn, 0, 4 * sizeof(double), s) != cudaSuccess))
+    return HJ_ERR_CUDA;
+  if (B == 0) return HJ_OK;
+  if (xq == nullptr || t == nullptr || iters == nullptr || dL_dV == nullptr)
+    return HJ_ERR_INVALID_ARG;
+  const bool f64 = opts->precision == HJ_PREC_FP64;
+  const size_t tsz = f64 ? sizeof(double) : sizeof(float);
+  const int grid = hj::adjoint_grid(B);
+  const size_t per_cta = (size_t)(max_iters / checkpoint_every + 1) * 3 * (N + 1) * prob->d * tsz;
+  void* work = nullptr;
+  if (cudaMalloc(&work, per_cta * grid) != cudaSuccess) return HJ_ERR_OOM;
+  if (cudaMemsetAsync(prob->counter, 0, sizeof(unsigned long long), s) != cudaSuccess) {
+    cudaFree(work);
+    return HJ_ERR_CUDA;
+  }
+  hj_status r;
+  auto fill = [&](auto& a) {
+    a.B = B; a.N = N; a.d = prob->d; a.K_cap = max_iters; a.C = checkpoint_every;
+    a.radius = opts->init_radius; a.seed = opts->seed; a.point_offset = opts->point_offset;
+    a.xq = xq; a.t = t; a.iters = iters; a.w = dL_dV;
+    a.W2 = prob->W2; a.W = prob->W; a.c = prob->c;
+    a.qc_m = prob->qc[0]; a.qc_ah = prob->qc[1]; a.qc_gz = prob->qc[2]; a.qc_eps = prob->qc[3];
+    a.dW = dW; a.dc = dc; a.ddyn = ddyn; a.dxq = dxq; a.counter = prob->counter;
+  };
+  if (f64) {
+    hj::AdjArgs<double> a{};
+    fill(a);
+    a.sig = opts->sigma; a.tau = opts->tau; a.th = opts->theta;
+    a.work = static_cast<double*>(work);
+    r = hj::launch_adjoint<double>(prob->family, a, grid, s);
+  } else {
+    hj::AdjArgs<float> a{};
+    fill(a);
+    a.sig = (float)opts->sigma; a.tau = (float)opts->tau; a.th = (float)opts->theta;
+    a.work = static_cast<float*>(work);
+    r = hj::launch_adjoint<float>(prob->family, a, grid, s);
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess && r == HJ_OK) r = HJ_ERR_CUDA;
+  cudaFree(work);
+  return r;
+}
+
 hj_status hj_set_launch_shape(hj_problem prob, int32_t precision, int32_t N,
                               int32_t warps_per_point, int32_t nodes_per_lane) {
   if (prob == nullptr || N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;

@@ -127,6 +127,35 @@ struct GradArgs {
 template <typename T>
 hj_status launch_value_grad(int family, const GradArgs<T>& g, cudaStream_t s);
 
+// Reverse sweep through the iterations (adjoint.cu).
+template <typename T>
+struct AdjArgs {
+  int64_t B;
+  int32_t N, d, K_cap, C;          // iterations bound, checkpoint spacing
+  T sig, tau, th;
+  double radius;
+  uint64_t seed;
+  int64_t point_offset;
+  const double* xq;                // [B][d]
+  const double* t;                 // [B]
+  const int32_t* iters;            // [B] K_b
+  const double* w;                 // [B] dL/dV_b
+  const double* W2;                // [d]
+  const double* W;                 // [d]
+  const double* c;                 // [d]
+  double qc_m, qc_ah, qc_gz, qc_eps;
+  T* work;                         // per CTA: (K_cap / C + 1) checkpoints of 3 (N+1) d
+  double* dW;                      // [d]
+  double* dc;                      // [d]
+  double* ddyn;                    // [4] quadcopter (m, a_h, g_z, eps)
+  double* dxq;                     // [B][d]; NaN for a point whose K_b is outside 0..K_cap
+  unsigned long long* counter;
+};
+
+template <typename T>
+hj_status launch_adjoint(int family, const AdjArgs<T>& a, int grid, cudaStream_t s);
+int adjoint_grid(int64_t B);
+
 // Kernel launchers (one per kernel family), defined in their .cu files.
 // Each returns HJ_OK, HJ_ERR_UNSUPPORTED (no instantiation for this shape) or
 // HJ_ERR_CUDA.

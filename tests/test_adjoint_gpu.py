@@ -113,3 +113,86 @@ def test_full_size_adjoint_sampled():
             sm["xq"] = sub["xq"].copy(); sm["xq"][0, k] -= h
             fd = (O.solve(sp, **TIGHT)["V"][0] - O.solve(sm, **TIGHT)["V"][0]) / (2 * h)
             assert abs(dxq[b, k] - fd) <= 2e-3 * max(1.0, abs(fd)), (b, k, dxq[b, k], fd)
+
+
+# ---------------------------------------------------------------- reverse sweep through the iterations
+def _fd_fixed(w, field, i, K, h=1e-5):
+    """Central difference of the oracle's mean value after exactly K iterations."""
+    def meanV(ww):
+        return float(np.mean(O.solve(ww, tol=0.0, max_iter=K, check_every=K)["V"]))
+    wp, wm = dict(w), dict(w)
+    vp = np.array(w[field], dtype=float).copy(); vp.reshape(-1)[i] += h
+    vm = np.array(w[field], dtype=float).copy(); vm.reshape(-1)[i] -= h
+    wp[field], wm[field] = vp, vm
+    return (meanV(wp) - meanV(wm)) / (2 * h)
+
+
+def _unrolled(w, precision, K, ckpt):
+    from paper_1803_01215_gb300 import binding
+    prob = binding.Problem.from_workload(w)
+    xq = torch.as_tensor(w["xq"], device="cuda")
+    t = torch.as_tensor(w["t"], device="cuda")
+    opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], tol=0.0, max_iter=K, check_every=K,
+                             precision=precision, seed=w["seed"], init_radius=w["init_radius"])
+    out = binding.solve_batch(prob, xq, t, int(w["N"]), opts)
+    B = xq.shape[0]
+    wts = torch.full((B,), 1.0 / B, dtype=torch.float64, device="cuda")
+    g = binding.solve_grad_unrolled(prob, xq, t, int(w["N"]), opts, out["iters"], wts,
+                                    checkpoint_every=ckpt)
+    return {k: v.cpu().numpy() for k, v in g.items()}
+
+
+@pytest.mark.parametrize("ckpt", [7, 32])
+def test_unrolled_adjoint_quadcopter_vs_finite_differences(ckpt):
+    """Exact gradient of the value after K = 40 iterations (not converged):
+    W, (m, a_h, g_z, eps) and x_q against central differences of the oracle
+    run for the same 40 iterations; checkpoint spacings that do and do not
+    divide K."""
+    w = W.quadcopter(B=3, seed=33, N=10, t=0.4)
+    K = 40
+    g = _unrolled(w, "fp64", K, ckpt)
+    def close(a, b):
+        return abs(a - b) <= 1e-6 * max(1.0, abs(b))
+    for i in (0, 3, 6, 11):
+        fd = _fd_fixed(w, "W", i, K)
+        assert close(g["dW"][i], fd), ("W", i, g["dW"][i], fd)
+    for i, name in enumerate(["m", "a_h", "g_z", "eps"]):
+        fd = _fd_fixed(w, "dyn", i, K)
+        assert close(g["ddyn"][i], fd), (name, g["ddyn"][i], fd)
+    for k in (0, 4, 7, 11):
+        fd = _fd_fixed(w, "xq", np.ravel_multi_index((2, k), w["xq"].shape), K)
+        assert close(g["dxq"][2, k], fd), ("xq", k, g["dxq"][2, k], fd)
+
+
+def test_unrolled_adjoint_quadratic_and_converged_agreement():
+    """H = |p|^2/2, d = 2: the unrolled gradient after K iterations matches finite
+    differences; run to convergence it matches the closed form x/(1+t)."""
+    w = W.quadratic_closed_form(B=6)
+    K = 25
+    g = _unrolled(w, "fp64", K, 8)
+    for k in range(2):
+        fd = _fd_fixed(w, "xq", np.ravel_multi_index((1, k), w["xq"].shape), K)
+        assert abs(g["dxq"][1, k] - fd) <= 1e-7 * max(1.0, abs(fd))
+    fd = _fd_fixed(w, "c", 0, K)
+    assert abs(g["dc"][0] - fd) <= 1e-7 * max(1.0, abs(fd))
+    gk = _unrolled(w, "fp64", 2000, 32)
+    np.testing.assert_allclose(gk["dxq"] * 6, w["xq"] / (1.0 + w["t"][:, None]), atol=1e-6)
+
+
+def test_unrolled_matches_envelope_at_convergence_fp32():
+    """The 12-D problem run to a tight stop: the reverse sweep and the envelope
+    gradient agree (both are the gradient of the converged value)."""
+    from paper_1803_01215_gb300 import binding
+    w = W.quadcopter(B=64, seed=34, N=16, t=0.5)
+    prob = binding.Problem.from_workload(w)
+    xq = torch.as_tensor(w["xq"], device="cuda")
+    t = torch.as_tensor(w["t"], device="cuda")
+    opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], tol=1e-10, max_iter=20000,
+                             check_every=16, seed=w["seed"])
+    out = binding.solve_batch(prob, xq, t, 16, opts, return_traj=True)
+    wts = torch.full((64,), 1.0 / 64, dtype=torch.float64, device="cuda")
+    ge = binding.solve_grad(prob, t, 16, "fp32", out["traj_x"], out["traj_p"], wts)
+    gu = binding.solve_grad_unrolled(prob, xq, t, 16, opts, out["iters"], wts, checkpoint_every=32)
+    for key in ("dW", "ddyn", "dxq"):
+        a, b = gu[key].cpu().numpy(), ge[key].cpu().numpy()
+        assert np.max(np.abs(a - b)) <= 2e-3 * max(1.0, np.max(np.abs(b))), key

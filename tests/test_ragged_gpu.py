@@ -155,7 +155,7 @@ def test_ragged_autotune_of_inner_steps_keeps_the_fixed_point():
     """Tuning the inner gradient steps changes the iterates but not the saddle:
     values agree with the single-step solve to the stopping accuracy."""
     rw = _small_mix(B=200, seed=16)
-    plan, xq, t = _plan(rw, "fp32", tol=1e-11)
+    plan, xq, t = _plan(rw, "fp32", tol=1e-9)
     ref = plan.solve(xq, t)
     V0 = ref["V"].cpu().numpy()
     plan.autotune(xq, t, repeats=1, max_inner_steps=3)
