@@ -262,13 +262,14 @@ __global__ void __launch_bounds__(32 * G) adjoint_kernel(const AdjArgs<T> a) {
 
     // ---- state of this lane: node j (x, p, z); lane 0 also node 0 (x0, z0)
     T x[D], p[D], z[D], x0[D], z0[D];
+    const InitGuess<T> ig(a.radius);                // the solver's initial guess
     auto init_state = [&]() {
       for (int k = 0; k < D; ++k) {
         const double xq = a.xq[b * D + k];
-        x[k] = (j < N) ? T(xq + a.radius * uniform_pm1(a.seed, gid, 0, j, k)) : T(xq);
-        p[k] = mine ? T(a.radius * uniform_pm1(a.seed, gid, 1, j, k)) : T(0);
+        x[k] = (j < N) ? ig.x(xq, a.seed, gid, j, k) : T(xq);
+        p[k] = mine ? ig.p(a.seed, gid, j, k) : T(0);
         z[k] = x[k];
-        x0[k] = T(xq + a.radius * uniform_pm1(a.seed, gid, 0, 0, k));
+        x0[k] = ig.x(xq, a.seed, gid, 0, k);
         z0[k] = x0[k];
       }
     };

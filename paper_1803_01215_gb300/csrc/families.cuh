@@ -9,6 +9,7 @@
 //   gradx(ctx, x, p, g)     g <- grad_x H(x, p)
 //   H64(x, p)               H in double from the iterates, for the value
 //                           (fval of Algorithm 1); converts element by element
+//   Ht(x, p)                H in the iterate type (the FP32 path's value terms)
 // All families have L = |u|^2/2, so H = <p, f0(x)> + |B(x)^T p|^2/2 (Section 2).
 #pragma once
 #include "hj_internal.cuh"
@@ -133,6 +134,12 @@ struct FamQuadratic {
 #pragma unroll
     for (int k = 0; k < D; ++k) h += (double)p[k] * (double)p[k];
     return 0.5 * h;
+  }
+  __device__ __forceinline__ T Ht(const T (&)[D], const T (&p)[D]) const {
+    T h = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) h += p[k] * p[k];
+    return T(0.5) * h;
   }
 };
 
@@ -262,6 +269,21 @@ struct FamQuadcopter {
     for (int k = 9; k < 12; ++k) rr += (double)p[k] * (double)p[k];
     return h + 0.5 * (u0 * u0 + rr) + 0.5 * eps64 * pp;
   }
+  __device__ __forceinline__ T Ht(const T (&x)[D], const T (&p)[D]) const {
+    T a[3], J[9];
+    thrust<T>(x[3], x[4], x[5], a, J);
+    T h = T(0), pp = T(0), rr = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) h += p[k] * x[6 + k] + p[3 + k] * x[9 + k];
+    const T s = a[0] * p[6] + a[1] * p[7] + a[2] * p[8];
+    h += ah * s - gz * p[8];
+    const T u0 = s * m_inv;
+#pragma unroll
+    for (int k = 0; k < D; ++k) pp += p[k] * p[k];
+#pragma unroll
+    for (int k = 9; k < 12; ++k) rr += p[k] * p[k];
+    return h + T(0.5) * (u0 * u0 + rr) + T(0.5) * eps * pp;
+  }
 };
 
 // ---------------------------------------------------------------- tanh drift, small D
@@ -315,6 +337,17 @@ struct FamTanhDrift {
       for (int k = 0; k < D; ++k) y += A64[i * D + k] * (double)x[k];
       const double pi = (double)p[i];
       h += pi * tanh(y) + 0.5 * pi * pi;
+    }
+    return h;
+  }
+  __device__ __forceinline__ T Ht(const T (&x)[D], const T (&p)[D]) const {
+    T h = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      T y = T(0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) y += A[i * D + k] * x[k];
+      h += p[i] * tanh_t<T>(y) + T(0.5) * p[i] * p[i];
     }
     return h;
   }

@@ -83,16 +83,52 @@ struct WarpConfig {
 // followed by the generator's xor-shift-multiply finaliser.  Used for the
 // random initial guess of Section 6; the counter layout is
 // point * 2^32 + stream * 2^31 + j * 2^12 + coord.
-__device__ __forceinline__ double uniform_pm1(uint64_t seed, uint64_t point, uint64_t stream,
-                                              uint64_t j, uint64_t coord) {
+__device__ __forceinline__ uint64_t splitmix_at(uint64_t seed, uint64_t point, uint64_t stream,
+                                                uint64_t j, uint64_t coord) {
   const uint64_t ctr = (point << 32) + (stream << 31) + (j << 12) + coord;
   uint64_t z = seed + (ctr + 1ull) * 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= (z >> 31);
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ double uniform_pm1(uint64_t seed, uint64_t point, uint64_t stream,
+                                              uint64_t j, uint64_t coord) {
+  const uint64_t z = splitmix_at(seed, point, stream, j, coord);
   const double u = (double)(z >> 11) * 0x1.0p-53;
   return 2.0 * u - 1.0;
 }
+
+// The initial guess of Section 6 in the iterate type: x = x_q + r u and p = r u.
+// FP64 evaluates both exactly as written (one rounding each).  FP32 takes the
+// generator's top 24 bits as u (exact in FP32, within 2^-23 of the 53-bit u)
+// and forms (float)x_q + (float)r * u, so no FP64 instruction runs per value.
+template <typename T>
+struct InitGuess {
+  double r;
+  __device__ explicit InitGuess(double radius) : r(radius) {}
+  __device__ __forceinline__ T x(double xq, uint64_t seed, uint64_t pt, uint64_t j,
+                                 uint64_t k) const {
+    return T(xq + r * uniform_pm1(seed, pt, 0, j, k));
+  }
+  __device__ __forceinline__ T p(uint64_t seed, uint64_t pt, uint64_t j, uint64_t k) const {
+    return T(r * uniform_pm1(seed, pt, 1, j, k));
+  }
+};
+template <>
+struct InitGuess<float> {
+  float r;
+  __device__ explicit InitGuess(double radius) : r((float)radius) {}
+  __device__ __forceinline__ static float u(uint64_t z) {
+    return (float)(uint32_t)(z >> 40) * 0x1.0p-23f - 1.0f;
+  }
+  __device__ __forceinline__ float x(float xq, uint64_t seed, uint64_t pt, uint64_t j,
+                                     uint64_t k) const {
+    return __fmaf_rn(r, u(splitmix_at(seed, pt, 0, j, k)), xq);
+  }
+  __device__ __forceinline__ float p(uint64_t seed, uint64_t pt, uint64_t j, uint64_t k) const {
+    return r * u(splitmix_at(seed, pt, 1, j, k));
+  }
+};
 
 template <typename U>
 __device__ __forceinline__ U warp_sum(U v) {

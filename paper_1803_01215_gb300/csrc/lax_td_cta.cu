@@ -124,8 +124,9 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
       if (k < d && j <= N) {
         const double xq = ref.xq[k];
         if (a.warm_x == nullptr) {
-          xv = (j < N) ? T(xq + a.radius * uniform_pm1(a.seed, pt, 0, j, k)) : T(xq);
-          pv = (j >= 1) ? T(a.radius * uniform_pm1(a.seed, pt, 1, j, k)) : T(0);
+          const InitGuess<T> ig(a.radius);
+          xv = (j < N) ? ig.x(xq, a.seed, pt, j, k) : T(xq);
+          pv = (j >= 1) ? ig.p(a.seed, pt, j, k) : T(0);
         } else {
           xv = (j < N) ? a.warm_x[ref.traj + (size_t)j * d + k] : T(xq);
           pv = (j >= 1) ? a.warm_p[ref.traj + (size_t)j * d + k] : T(0);
@@ -242,20 +243,34 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
       }
     }
 
-    // ---- value in FP64: g(x_0) + sum_j <p_j, x_j - x_{j-1}> - delta sum_j H(x_j, p_j)
+    // ---- value g(x_0) + sum_j <p_j, x_j - x_{j-1}> - delta sum_j H(x_j, p_j):
+    // FP64 iterates evaluate every term in FP64; FP32 iterates form each
+    // (coordinate, node) term in FP32 (A x from the FP32 copy of A); the sum is FP64
     double acc = 0.0;
     for (int e = tid; e < d * N; e += nthr) {
       const int j = 1 + e / d, i = e - (j - 1) * d;
-      double th_y = 0.0;
-      if (DRIFT) {
-        const double* Ar = a.A64 + (size_t)i * d;
-        double y = 0.0;
-        for (int k = 0; k < d; ++k) y += Ar[k] * (double)X[k * Np + j];
-        th_y = tanh(y);
+      if constexpr (sizeof(T) == 4) {
+        T th_y = T(0);
+        if (DRIFT) {
+          T y = T(0);
+          for (int k = 0; k < d; ++k) y += Am[i * dp + k] * X[k * Np + j];
+          th_y = tanh_c<T>(y);
+        }
+        const T pv = P[i * Np + j];
+        const T dx = X[i * Np + j] - X[i * Np + j - 1];
+        acc += (double)(pv * dx - delta_t * (pv * th_y + T(0.5) * pv * pv));
+      } else {
+        double th_y = 0.0;
+        if (DRIFT) {
+          const double* Ar = a.A64 + (size_t)i * d;
+          double y = 0.0;
+          for (int k = 0; k < d; ++k) y += Ar[k] * (double)X[k * Np + j];
+          th_y = tanh(y);
+        }
+        const double pv = (double)P[i * Np + j];
+        const double dx = (double)X[i * Np + j] - (double)X[i * Np + j - 1];
+        acc += pv * dx - delta * (pv * th_y + 0.5 * pv * pv);
       }
-      const double pv = (double)P[i * Np + j];
-      const double dx = (double)X[i * Np + j] - (double)X[i * Np + j - 1];
-      acc += pv * dx - delta * (pv * th_y + 0.5 * pv * pv);
     }
     if (tid < d) {
       const double e0 = (double)X[tid * Np] - a.c[tid];

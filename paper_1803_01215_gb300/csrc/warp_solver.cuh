@@ -137,6 +137,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   const int jbase = 1 + gl * NPL;
   {
     if (a.warm_x == nullptr) {
+      const InitGuess<T> ig(a.radius);
 #pragma unroll
       for (int i = 0; i < NPL; ++i) {
         const int j = jbase + i;
@@ -144,13 +145,13 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         for (int k = 0; k < D; ++k) {
           const double xq = pt.xq[k];
           T xv = T(0), pv = T(0);
-          if (j < N) xv = T(xq + a.radius * uniform_pm1(a.seed, gid, 0, j, k));
+          if (j < N) xv = ig.x(xq, a.seed, gid, j, k);
           else if (j == N) xv = T(xq);
-          if (j <= N) pv = T(a.radius * uniform_pm1(a.seed, gid, 1, j, k));
+          if (j <= N) pv = ig.p(a.seed, gid, j, k);
           x[i][k] = xv; p[i][k] = pv; z[i][k] = xv;
         }
       }
-      if (own0) x0 = T(pt.xq[k0] + a.radius * uniform_pm1(a.seed, gid, 0, 0, k0));
+      if (own0) x0 = ig.x(pt.xq[k0], a.seed, gid, 0, k0);
     } else {
       const T* wx = a.warm_x + pt.traj;
       const T* wp = a.warm_p + pt.traj;
@@ -289,7 +290,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     if (sx < a.tol_t && sp < a.tol_t) { st = HJ_POINT_CONVERGED; break; }
   }
 
-  // ---- value (fval of Algorithm 1) in FP64, and outputs
+  // ---- value (fval of Algorithm 1), summed in FP64, and outputs
   group_sync<G>();                                 // every lane is done with the slots
   slot_store<T, D>(zslot + gl * DP, x[NPL - 1]);
   if (own0) x0slot[k0] = x0;
@@ -302,13 +303,22 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
       if (jbase + i <= N) {
-        double s = 0.0;
+        if constexpr (sizeof(T) == 4) {
+          // FP32 iterates: each node's term <p_j, x_j - x_{j-1}> - delta H(x_j, p_j)
+          // in FP32, the sum over nodes in FP64
+          T s = T(0);
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-          const double xm = (double)((i == 0) ? xl[k] : x[i - 1][k]);
-          s += (double)p[i][k] * ((double)x[i][k] - xm);
+          for (int k = 0; k < D; ++k) s += p[i][k] * (x[i][k] - ((i == 0) ? xl[k] : x[i - 1][k]));
+          acc += (double)(s - delta_t * fam.Ht(x[i], p[i]));
+        } else {
+          double s = 0.0;
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const double xm = (double)((i == 0) ? xl[k] : x[i - 1][k]);
+            s += (double)p[i][k] * ((double)x[i][k] - xm);
+          }
+          acc += s - delta * fam.H64(x[i], p[i]);
         }
-        acc += s - delta * fam.H64(x[i], p[i]);
       }
     }
     if (own0) {
