@@ -208,6 +208,12 @@ WarpConfig default_warp_config(int family, int d, int Nmax, bool fp64);
 // Whether the warp kernel has an instantiation for (family, d, cfg, precision).
 bool warp_config_available(int family, int d, WarpConfig cfg, bool fp64);
 // Shared-memory CTA kernel: tanh drift (drift = true) or H = |p|^2/2 (drift = false).
+// Register-tiled FP32 tanh-drift kernel; HJ_ERR_UNSUPPORTED where it does not
+// apply (the shared-memory kernel then runs).  td_tile_group_warps: warps per
+// point for (d, N), 0 when the tiled kernel cannot hold the point.
+hj_status launch_td_tile_solver(const SolveArgs<float>& a, cudaStream_t s);
+int td_tile_group_warps(int d, int N);
+
 template <typename T>
 hj_status launch_td_cta_solver(const SolveArgs<T>& a, bool drift, cudaStream_t s);
 // Shared memory that kernel needs for (d, N); 0 if it does not fit.

@@ -348,6 +348,12 @@ template <typename T>
 hj_status launch_td_cta_solver(const SolveArgs<T>& a, bool drift, cudaStream_t s) {
   if (a.d < 1 || a.d > kMaxD || a.N < 1 || a.N > kMaxN || a.inner_steps != 1)
     return HJ_ERR_UNSUPPORTED;
+  if constexpr (sizeof(T) == 4) {
+    if (drift) {
+      const hj_status r = launch_td_tile_solver(a, s);
+      if (r != HJ_ERR_UNSUPPORTED) return r;
+    }
+  }
   if (!drift) {
     const size_t sm = smem_bytes<T, false>(a.d, a.N, false);
     return sm <= 227u * 1024u ? launch<T, false, false>(a, s, sm) : HJ_ERR_UNSUPPORTED;

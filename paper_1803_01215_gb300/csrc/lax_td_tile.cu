@@ -1,0 +1,420 @@
+// Register-tiled batched PDHG for the tanh-drift Hamiltonian with FP32 iterates:
+// H = <p, tanh(A x)> + |p|^2/2 (Algorithm 1 with the Section 5.3 updates).
+//
+// A group of G warps solves one query point.  Each thread owns a fixed tile of
+// 4 coordinates x 8 time nodes and keeps that tile's x, p and z in registers
+// for the whole solve (thread t of the group: within each block of 4*TIc
+// threads, i-tile = u / 4 and j-tile = 4 * block + u % 4, so a quarter-warp
+// covers 2 i-tiles x 4 j-tiles and its 16-byte operand loads stay cheap).  Only
+// what other threads need goes through shared memory:
+//   Xs[k][j-1]   the x iterate of nodes 1..N (operand of A x), published after
+//                the primal step;
+//   Ws[k][j-1]   W = (1 - a^2) p (operand of A^T W), published after the dual step;
+//   Zb, Pb       the z of each tile's last node and the p of its first node,
+//                the neighbour terms z_{j-1} and p_{j+1} across tile boundaries.
+// Per iteration:
+//   phase A  Y = A X over the tile (k-loop over 16-byte loads of A^T and Xs),
+//            then a = tanh(Y), the dual prox
+//            p_j <- (p_j + sigma (z_j - z_{j-1}) - lam a) / (1 + lam), lam = sigma delta,
+//            and W = (1 - a^2) p_j;
+//   phase B  G = A^T W, then x_j <- x_j - tau (p_j - p_{j+1}) + tau delta G_j,
+//            z_j = x_j + theta (x_j - x_j_old), and the g-prox of x_0 (held by
+//            the threads of the first node tile).
+// x_N stays pinned at the query point.  One group barrier after each phase
+// (__syncwarp when G = 1).  The squared increments are summed in FP32 on test
+// iterations and compared with tol rounded up to FP32; the value's (coordinate,
+// node) terms are FP32 and their sum FP64.  Groups take points from the work
+// counter (persistent grid); the CTA's groups share one copy of A and A^T.
+#include <cuda_runtime.h>
+
+#include "hj_internal.cuh"
+
+namespace hj {
+
+namespace {
+
+constexpr int kTI = 4;   // coordinates per tile
+constexpr int kTJ = 8;   // time nodes per tile
+
+struct TileLayout {
+  int d, dp, TIc, TJc, Ns;
+  size_t head_bytes;     // per-group item slots, g-prox constants
+  size_t a_floats;       // A^T and A
+  size_t grp_floats;     // Xs, Ws, Zb, Pb, reductions of one group
+  __host__ __device__ TileLayout(int d_, int Nmax, int G, int M) {
+    d = d_;
+    dp = (d + 3) & ~3;
+    TIc = dp / kTI;
+    TJc = (Nmax + kTJ - 1) / kTJ;
+    Ns = kTJ * TJc + 4;                              // row stride of Xs and Ws
+    head_bytes = (size_t)((M * 8 + 15) / 16) * 16 + 2 * (size_t)dp * sizeof(float);
+    a_floats = 2 * (size_t)d * dp;
+    grp_floats = 2 * (size_t)dp * Ns + 2 * (size_t)TJc * dp + 6 * (size_t)G;
+    grp_floats = (grp_floats + 3) & ~size_t(3);       // keep 16-byte alignment
+  }
+  __host__ __device__ size_t bytes(int M) const {
+    return head_bytes + (a_floats + (size_t)M * grp_floats) * sizeof(float);
+  }
+};
+
+// warps a point needs: tiles laid out in blocks of 4 j-tiles
+__host__ __device__ inline int tile_slots(int d, int Nmax) {
+  const int TIc = ((d + 3) & ~3) / kTI, TJc = (Nmax + kTJ - 1) / kTJ;
+  return 4 * TIc * ((TJc + 3) / 4);
+}
+
+template <int G>
+__device__ __forceinline__ void group_barrier(int grp) {
+  if constexpr (G == 1) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(32 * G) : "memory");
+  }
+}
+
+__device__ __forceinline__ void load8(const float* p, float (&v)[kTJ]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float4 b = *reinterpret_cast<const float4*>(p + 4);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void store8(float* p, const float (&v)[kTJ]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  *reinterpret_cast<float4*>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
+}
+
+// acc[r][c] = sum_k M[k][i0 + r] * S[k][c0 + c], k < d (M k-major with stride dp)
+__device__ __forceinline__ void tile_product(const float* M, const float* S, int d, int dp,
+                                             int Ns, int i0, int c0,
+                                             float (&acc)[kTI][kTJ]) {
+#pragma unroll
+  for (int r = 0; r < kTI; ++r)
+#pragma unroll
+    for (int c = 0; c < kTJ; ++c) acc[r][c] = 0.f;
+  const float* mp = M + i0;
+  const float* sp = S + c0;
+#pragma unroll 2
+  for (int k = 0; k < d; ++k) {
+    const float4 a = *reinterpret_cast<const float4*>(mp + (size_t)k * dp);
+    float s[kTJ];
+    load8(sp + (size_t)k * Ns, s);
+    const float av[kTI] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int r = 0; r < kTI; ++r)
+#pragma unroll
+      for (int c = 0; c < kTJ; ++c) acc[r][c] = fmaf(av[r], s[c], acc[r][c]);
+  }
+}
+
+template <int G, bool TH1>
+__global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float> a, int M) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const TileLayout L(a.d, a.N, G, M);
+  const int d = L.d, dp = L.dp, Ns = L.Ns;
+  unsigned long long* items = reinterpret_cast<unsigned long long*>(smem);
+  float* goff = reinterpret_cast<float*>(smem + (size_t)((M * 8 + 15) / 16) * 16);
+  float* ginv = goff + dp;
+  float* At = ginv + dp;                          // At[k*dp + i] = A[i][k]
+  float* Am = At + (size_t)d * dp;                // Am[k*dp + i] = A[k][i]
+  const int grp = (int)threadIdx.x / (32 * G);
+  float* Xs = Am + (size_t)d * dp + (size_t)grp * L.grp_floats;
+  float* Ws = Xs + (size_t)dp * Ns;
+  float* Zb = Ws + (size_t)dp * Ns;               // Zb[jt*dp + i]
+  float* Pb = Zb + (size_t)L.TJc * dp;            // Pb[jt*dp + i]
+  float* tred = Pb + (size_t)L.TJc * dp;          // [2G]
+  double* vred = reinterpret_cast<double*>(tred + 2 * G + ((2 * G) & 2));   // [G], 8-byte aligned
+
+  for (int e = threadIdx.x; e < d * dp; e += blockDim.x) {
+    const int k = e / dp, i = e - k * dp;
+    At[e] = (i < d) ? a.At[k * d + i] : 0.f;
+    Am[e] = (i < d) ? a.A[k * d + i] : 0.f;
+  }
+  for (int i = threadIdx.x; i < dp; i += blockDim.x) {
+    const double w2 = i < d ? a.W2[i] : 0.0, cc = i < d ? a.c[i] : 0.0;
+    goff[i] = (float)(a.tau * w2 * cc);
+    ginv[i] = (float)(1.0 / (1.0 + a.tau * w2));
+  }
+  __syncthreads();
+  if (grp >= M) return;                           // no thread of a partial group exists
+
+  const int t = (int)threadIdx.x - grp * 32 * G;  // thread within the group
+  const int lane = t & 31, wig = t >> 5;
+  const int blk = 4 * L.TIc;
+  const int u = t % blk, jg = t / blk;
+  const int it = u >> 2, jt = 4 * jg + (u & 3);
+  const bool tile_ok = it < L.TIc && jt < L.TJc;
+  const int i0 = it * kTI, c0 = jt * kTJ, j0 = 1 + c0;   // nodes j0..j0+7 <-> Xs columns c0..c0+7
+  const float sig = a.sigma_t, tau = a.tau_t, th = a.theta_t;
+
+  for (;;) {
+    group_barrier<G>(grp);
+    if (t == 0) items[grp] = atomicAdd(a.counter, 1ull);
+    group_barrier<G>(grp);
+    const int64_t item = (int64_t)items[grp];
+    if (item >= a.B) break;
+    const PointRef<float> ref = point_ref(a, item);
+    const int64_t b = ref.id;
+    const int N = ref.N;
+    if (N < 1 || N > a.N) {                      // the host never routes such a point here
+      if (t == 0) { a.status[b] = HJ_POINT_INVALID; a.iters[b] = 0; a.V[b] = 0.0; }
+      continue;
+    }
+    const bool act = tile_ok && c0 < N;           // the tile holds nodes of this point
+    const float delta_t = (float)a.t[b] / (float)N;
+    const float lam = sig * delta_t, taud = tau * delta_t;
+    const float ilam = 1.f / (1.f + lam);
+    const uint64_t pt = (uint64_t)(a.point_offset + b);
+
+    float x[kTI][kTJ], p[kTI][kTJ], z[kTI][kTJ], x0[kTI], z0[kTI];
+    {
+      const InitGuess<float> ig(a.radius);
+#pragma unroll
+      for (int r = 0; r < kTI; ++r) {
+        const int i = i0 + r;
+        const bool row = act && i < d;
+        const double xq = row ? ref.xq[i] : 0.0;
+#pragma unroll
+        for (int c = 0; c < kTJ; ++c) {
+          const int j = j0 + c;
+          float xv = 0.f, pv = 0.f;
+          if (row && j <= N) {
+            if (a.warm_x == nullptr) {
+              xv = (j < N) ? ig.x(xq, a.seed, pt, j, i) : (float)xq;
+              pv = ig.p(a.seed, pt, j, i);
+            } else {
+              xv = (j < N) ? a.warm_x[ref.traj + (size_t)j * d + i] : (float)xq;
+              pv = a.warm_p[ref.traj + (size_t)j * d + i];
+            }
+          }
+          x[r][c] = xv; p[r][c] = pv; z[r][c] = xv;
+        }
+        float x0v = 0.f;
+        if (row && jt == 0)
+          x0v = (a.warm_x == nullptr) ? ig.x(xq, a.seed, pt, 0, i) : a.warm_x[ref.traj + i];
+        x0[r] = x0v; z0[r] = x0v;
+      }
+    }
+    if (act) {
+#pragma unroll
+      for (int r = 0; r < kTI; ++r) {
+        store8(Xs + (size_t)(i0 + r) * Ns + c0, x[r]);
+        Zb[jt * dp + i0 + r] = z[r][kTJ - 1];
+      }
+    }
+    group_barrier<G>(grp);
+
+    // one iteration; CHK adds the squared increments (test iterations only)
+    auto step = [&](auto chk_tag, float& rx, float& rp) {
+      constexpr bool CHK = decltype(chk_tag)::value;
+      float acc[kTI][kTJ];
+      // ---- phase A: Y = A X, tanh, dual prox, W = (1 - a^2) p
+      if (act) {
+        float zL[kTI];
+#pragma unroll
+        for (int r = 0; r < kTI; ++r) zL[r] = (jt == 0) ? z0[r] : Zb[(jt - 1) * dp + i0 + r];
+        tile_product(At, Xs, d, dp, Ns, i0, c0, acc);
+#pragma unroll
+        for (int r = 0; r < kTI; ++r) {
+          const bool row = i0 + r < d;
+          float w[kTJ];
+#pragma unroll
+          for (int c = 0; c < kTJ; ++c) {
+            w[c] = 0.f;
+            if (row && j0 + c <= N) {
+              const float av = tanhf(acc[r][c]);
+              const float zl = (c == 0) ? zL[r] : z[r][c - 1];
+              const float v = p[r][c] + sig * (z[r][c] - zl);
+              const float pn = (v - lam * av) * ilam;
+              if constexpr (CHK) { const float e = pn - p[r][c]; rp += e * e; }
+              p[r][c] = pn;
+              w[c] = (1.f - av * av) * pn;
+            }
+          }
+          store8(Ws + (size_t)(i0 + r) * Ns + c0, w);
+          Pb[jt * dp + i0 + r] = p[r][0];
+        }
+      }
+      group_barrier<G>(grp);
+      // ---- phase B: G = A^T W, primal gradient step, relaxation; g-prox of x_0
+      if (act) {
+        float pR[kTI];
+#pragma unroll
+        for (int r = 0; r < kTI; ++r)
+          pR[r] = (c0 + kTJ < N) ? Pb[(jt + 1) * dp + i0 + r] : 0.f;
+        tile_product(Am, Ws, d, dp, Ns, i0, c0, acc);
+#pragma unroll
+        for (int r = 0; r < kTI; ++r) {
+          const int i = i0 + r;
+          if (i < d) {
+#pragma unroll
+            for (int c = 0; c < kTJ; ++c) {
+              if (j0 + c < N) {
+                const float pn = (c + 1 < kTJ) ? p[r][c + 1 < kTJ ? c + 1 : c] : pR[r];
+                const float xo = x[r][c];
+                const float xn = xo - tau * (p[r][c] - pn) + taud * acc[r][c];
+                if constexpr (CHK) { const float e = xn - xo; rx += e * e; }
+                z[r][c] = TH1 ? 2.f * xn - xo : xn + th * (xn - xo);
+                x[r][c] = xn;
+              }
+            }
+            if (jt == 0) {                        // x_0 <- prox_{tau g}(x_0 + tau p_1)
+              const float xo = x0[r];
+              const float xn = (xo + tau * p[r][0] + goff[i]) * ginv[i];
+              if constexpr (CHK) { const float e = xn - xo; rx += e * e; }
+              z0[r] = TH1 ? 2.f * xn - xo : xn + th * (xn - xo);
+              x0[r] = xn;
+            }
+          }
+          store8(Xs + (size_t)i * Ns + c0, x[r]);
+          Zb[jt * dp + i] = z[r][kTJ - 1];
+        }
+      }
+      group_barrier<G>(grp);
+    };
+
+    int k_it = 0;
+    int8_t st = HJ_POINT_MAX_ITER;
+    const int max_iter = a.max_iter, check_every = a.check_every;
+    while (k_it < max_iter) {
+      const int left = max_iter - k_it;
+      const int plain = (check_every - 1 < left - 1) ? check_every - 1 : left - 1;
+      float dx = 0.f, dpp = 0.f;
+      for (int r = 0; r < plain; ++r) step(std::integral_constant<bool, false>{}, dx, dpp);
+      float rx = 0.f, rp = 0.f;
+      step(std::integral_constant<bool, true>{}, rx, rp);
+      k_it += plain + 1;
+      // FP32 sums compared with tol rounded up to FP32: exactly the FP64 test of the sum
+      float sx = warp_sum<float>(rx), sp = warp_sum<float>(rp);
+      if constexpr (G > 1) {
+        if (lane == 0) { tred[2 * wig] = sx; tred[2 * wig + 1] = sp; }
+        group_barrier<G>(grp);
+        sx = 0.f; sp = 0.f;
+#pragma unroll
+        for (int w = 0; w < G; ++w) { sx += tred[2 * w]; sp += tred[2 * w + 1]; }
+        group_barrier<G>(grp);                    // tred is free for the next test
+      }
+      if (!(isfinite(sx) && isfinite(sp))) { st = HJ_POINT_NONFINITE; break; }
+      if (sx < a.tol_t && sp < a.tol_t) { st = HJ_POINT_CONVERGED; break; }
+    }
+
+    // ---- value: g(x_0) + sum_j <p_j, x_j - x_{j-1}> - delta sum_j H(x_j, p_j); FP32
+    // terms (A x from the FP32 copy of A), FP64 sum.  Xs holds the final x.
+    double vacc = 0.0;
+    if (act) {
+      float acc[kTI][kTJ];
+      tile_product(At, Xs, d, dp, Ns, i0, c0, acc);
+#pragma unroll
+      for (int r = 0; r < kTI; ++r) {
+        const int i = i0 + r;
+        if (i < d) {
+          const float xl0 = (jt == 0) ? x0[r] : Xs[(size_t)i * Ns + c0 - 1];
+#pragma unroll
+          for (int c = 0; c < kTJ; ++c) {
+            if (j0 + c <= N) {
+              const float pv = p[r][c];
+              const float dxv = x[r][c] - ((c == 0) ? xl0 : x[r][c > 0 ? c - 1 : 0]);
+              vacc += (double)(pv * dxv - delta_t * (pv * tanhf(acc[r][c]) + 0.5f * pv * pv));
+            }
+          }
+          if (jt == 0) {
+            const double e = (double)x0[r] - a.c[i];
+            vacc += 0.5 * a.W2[i] * e * e;
+          }
+        }
+      }
+    }
+    vacc = warp_sum<double>(vacc);
+    if constexpr (G > 1) {
+      if (lane == 0) vred[wig] = vacc;
+      group_barrier<G>(grp);
+      vacc = 0.0;
+#pragma unroll
+      for (int w = 0; w < G; ++w) vacc += vred[w];
+    }
+    if (t == 0) {
+      a.V[b] = vacc;
+      a.iters[b] = k_it;
+      a.status[b] = st;
+    }
+    if (act) {
+#pragma unroll
+      for (int r = 0; r < kTI; ++r) {
+        const int i = i0 + r;
+        if (i >= d) continue;
+#pragma unroll
+        for (int c = 0; c < kTJ; ++c) {
+          const int j = j0 + c;
+          if (j <= N) {
+            if (a.traj_x != nullptr) a.traj_x[ref.traj + (size_t)j * d + i] = x[r][c];
+            if (a.traj_p != nullptr) a.traj_p[ref.traj + (size_t)j * d + i] = p[r][c];
+          }
+        }
+        if (jt == 0) {
+          if (a.traj_x != nullptr) a.traj_x[ref.traj + i] = x0[r];
+          if (a.traj_p != nullptr) a.traj_p[ref.traj + i] = 0.f;
+        }
+      }
+    }
+  }
+}
+
+template <int G, bool TH1>
+hj_status launch_g(const SolveArgs<float>& a, int M, size_t smem, cudaStream_t s) {
+  auto kern = lax_td_tile_kernel<G, TH1>;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HJ_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return HJ_ERR_CUDA;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return HJ_ERR_CUDA;
+  const int threads = 32 * G * M;
+  int bps = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, threads, smem) != cudaSuccess)
+    return HJ_ERR_CUDA;
+  if (bps < 1) return HJ_ERR_UNSUPPORTED;
+  const int64_t ctas_needed = (a.B + M - 1) / M;
+  const int64_t cap = (int64_t)bps * nsm;
+  const int grid = (int)(ctas_needed < cap ? ctas_needed : cap);
+  kern<<<grid, threads, smem, s>>>(a, M);
+  return cudaGetLastError() == cudaSuccess ? HJ_OK : HJ_ERR_CUDA;
+}
+
+}  // namespace
+
+// Warps per point of the register-tiled kernel for (d, N), 0 when it does not apply.
+int td_tile_group_warps(int d, int N) {
+  if (d < 1 || d > kMaxD || N < 1 || N > kMaxN) return 0;
+  const int w = (tile_slots(d, N) + 31) / 32;
+  return w <= 1 ? 1 : w <= 2 ? 2 : w <= 4 ? 4 : w <= 8 ? 8 : 0;
+}
+
+// Runs the register-tiled kernel when it applies (FP32, tanh drift, a point in
+// at most 8 warps, shared memory within the opt-in limit); HJ_ERR_UNSUPPORTED
+// otherwise, and the caller takes the shared-memory kernel.
+hj_status launch_td_tile_solver(const SolveArgs<float>& a, cudaStream_t s) {
+  if (a.inner_steps != 1 || a.A == nullptr || a.At == nullptr) return HJ_ERR_UNSUPPORTED;
+  const int G = td_tile_group_warps(a.d, a.N);
+  if (G == 0) return HJ_ERR_UNSUPPORTED;
+  int dev = 0, max_optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HJ_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+      cudaSuccess)
+    return HJ_ERR_CUDA;
+  int M = G == 1 ? 4 : G == 2 ? 2 : 1;
+  size_t smem = TileLayout(a.d, a.N, G, M).bytes(M);
+  while (M > 1 && smem > (size_t)max_optin) {
+    M /= 2;
+    smem = TileLayout(a.d, a.N, G, M).bytes(M);
+  }
+  if (smem > (size_t)max_optin) return HJ_ERR_UNSUPPORTED;
+  const bool th1 = a.theta == 1.0;
+  switch (G) {
+    case 1: return th1 ? launch_g<1, true>(a, M, smem, s) : launch_g<1, false>(a, M, smem, s);
+    case 2: return th1 ? launch_g<2, true>(a, M, smem, s) : launch_g<2, false>(a, M, smem, s);
+    case 4: return th1 ? launch_g<4, true>(a, M, smem, s) : launch_g<4, false>(a, M, smem, s);
+    default: return th1 ? launch_g<8, true>(a, M, smem, s) : launch_g<8, false>(a, M, smem, s);
+  }
+}
+
+}  // namespace hj
