@@ -41,7 +41,7 @@ SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # kernel (lax_warp_kernel<float, FamQuadcopter, 12, 1, 2>) from the ncu capture
 # summarised in profiles/quadcopter12d_B4096_N64_fp32_warp_kernel.md; set to
 # None whenever that kernel changes until it is captured again.
-QC_TRAFFIC_BYTES = None
+QC_TRAFFIC_BYTES = 468224 + 0
 
 
 def workload_config():
@@ -199,9 +199,23 @@ def measure_other_configs(dev, flush, stream, peak):
                                                     wts, stream=stream)), 2, 1, flush, stream,
                         "timed_solve_grad")
     traj_bytes = 2 * B * 65 * 12 * 4
+    # the reverse sweep through the iterations each point ran, checkpoints every 32
+    binding.solve_batch(prob, xq, t, 64, opts, out=res, stream=stream)
+    kmax = int(res["iters"].max().item())
+    ge = binding.solve_grad(prob, t, 64, "fp32", res["traj_x"], res["traj_p"], wts, stream=stream)
+    gu = binding.solve_grad_unrolled(prob, xq, t, 64, opts, res["iters"], wts, checkpoint_every=32,
+                                     max_iters=kmax, stream=stream)
+    agree = max(float((gu[k] - ge[k]).abs().max() / ge[k].abs().max().clamp_min(1.0))
+                for k in ("dW", "ddyn", "dxq"))
+    u_ms = _events_time(lambda: binding.solve_grad_unrolled(prob, xq, t, 64, opts, res["iters"], wts,
+                                                            checkpoint_every=32, max_iters=kmax,
+                                                            stream=stream),
+                        2, 1, flush, stream, "timed_grad_unrolled")
     out["adjoint_quadcopter_B4096_N64"] = {
         "value_and_grad_per_s": B / (both * 1e-3), "ms_solve_plus_grad": both,
-        "ms_grad_kernel": g_ms, "grad_kernel_gbs": traj_bytes / (g_ms * 1e-3) / 1e9}
+        "ms_grad_kernel": g_ms, "grad_kernel_gbs": traj_bytes / (g_ms * 1e-3) / 1e9,
+        "ms_grad_unrolled_ckpt32": u_ms, "grad_unrolled_per_s": B / (u_ms * 1e-3),
+        "unrolled_vs_envelope_max_rel": agree, "max_iters": kmax}
     return out
 
 
