@@ -306,6 +306,18 @@ hj_status hj_solve_batch_static(int32_t family, int32_t d, const double* dyn, in
                                 double* V, int32_t* iters, int8_t* status, void* traj_x,
                                 void* traj_p, void* stream);
 
+/* Diagnostic, with no counterpart in the method: the device's FP32 FMA
+ * throughput, measured by one launch of independent FMA chains that fills every
+ * SM (after one warm-up launch).  It is the measured denominator of the
+ * roofline fraction of the FP32 iteration kernels, which the FP32 FMA pipe bounds.
+ *   iters   (host) >= 1; every thread runs 8 chains of 16 * iters FMAs
+ *           (50000 runs for ~50 ms on a GB300).
+ *   packed  (host) 0: scalar fmaf; 1: the packed two-wide FMA (2 FMAs each).
+ *   tflops  (host) out: 2 * FMAs / elapsed seconds / 1e12 (CUDA events).
+ * Allocates a small stream-ordered scratch buffer; synchronises `stream`.
+ * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_OOM, HJ_ERR_CUDA.                       */
+hj_status hj_probe_fp32_fma(int64_t iters, int32_t packed, double* tflops, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* hj_status_str(hj_status s);
 

@@ -39,7 +39,7 @@ EXPORTED = ("hj_problem_create", "hj_problem_destroy", "hj_solve_batch",
             "hj_ragged_plan_create", "hj_ragged_plan_layout", "hj_ragged_plan_bucket",
             "hj_ragged_solve", "hj_ragged_autotune", "hj_ragged_plan_destroy",
             "hj_solve_grad", "hj_solve_grad_unrolled", "hj_solve_batch_static",
-            "hj_static_scratch_bytes",
+            "hj_static_scratch_bytes", "hj_probe_fp32_fma",
             "hj_status_str", "hj_version")
 
 
@@ -79,6 +79,8 @@ def _lib():
         lib.hj_solve_grad_unrolled.argtypes = [P, I64, P, P, I32, ctypes.POINTER(SolverOpts), P,
                                                I32, I32, P, P, P, P, P, P]
         lib.hj_solve_grad_unrolled.restype = ctypes.c_int
+        lib.hj_probe_fp32_fma.argtypes = [I64, I32, ctypes.POINTER(ctypes.c_double), P]
+        lib.hj_probe_fp32_fma.restype = ctypes.c_int
         lib.hj_status_str.restype = ctypes.c_char_p
         lib.hj_status_str.argtypes = [ctypes.c_int]
         lib.hj_version.restype = ctypes.c_int32
@@ -141,6 +143,17 @@ def get_launch_shape(problem, precision, N):
     if r != HJ_OK:
         raise HJError(r, "hj_get_launch_shape")
     return g.value, n.value
+
+
+def probe_fp32_fma(iters=50000, packed=False, stream=None):
+    """hj_probe_fp32_fma: measured FP32 FMA throughput of the current device, TFLOP/s."""
+    out = ctypes.c_double(0.0)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    r = _lib().hj_probe_fp32_fma(int(iters), int(bool(packed)), ctypes.byref(out),
+                                 ctypes.c_void_p(s.cuda_stream))
+    if r != HJ_OK:
+        raise HJError(r, "hj_probe_fp32_fma")
+    return out.value
 
 
 def autotune(problem, xq, t, N, opts, repeats=2, stream=None):
