@@ -15,8 +15,11 @@ Contents
   lax_pdhg     Algorithm 1 (Lax formula, backward Euler) with the concrete
                updates of Section 5.3 and the loop of Appendix Algorithm A.1,
                and the value fval of Eq. (disclaxBE).
+  hopf_pdhg    Algorithm 2 (Hopf formula, backward Euler, Eq. dischopf) as the
+               appendix's Hopf tutorial algorithm: the joint prox of g* and
+               delta H at j = 1, x_0 eliminated through the conjugate of g.
 
-Pins: see tests/test_oracle_pins.py.  Closed form (quadratic H), discrete
+Pins: see tests/test_oracle_pins.py and tests/test_oracle_hopf_pins.py.  Closed form (quadratic H), discrete
 Riccati (linear drift), direct collocation (tanh drift), the discrete
 characteristic (KKT) equations with complex-step derivatives of an H written
 independently from the quadcopter dynamics, the primal/dual value identity, and
