@@ -155,15 +155,18 @@ def measure_other_configs(dev, flush, stream, peak):
     from paper_1803_01215_gb300 import binding
     out = {}
 
-    def run_uniform(w, precision, tag, npts=None):
+    def run_uniform(w, precision, tag, npts=None, formulation="lax", tune=False):
         if npts is not None:
             w = W.subset(w, np.arange(npts))
         prob = binding.Problem.from_workload(w)
         opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], tol=w["tol"],
                                  max_iter=w["max_iter"], check_every=w["check_every"],
-                                 seed=w["seed"], init_radius=w["init_radius"], precision=precision)
+                                 seed=w["seed"], init_radius=w["init_radius"], precision=precision,
+                                 formulation=formulation)
         xq = torch.as_tensor(w["xq"], device=dev)
         t = torch.as_tensor(w["t"], device=dev)
+        if tune:
+            binding.autotune(prob, xq, t, int(w["N"]), opts, repeats=1)
         res = binding.solve_batch(prob, xq, t, int(w["N"]), opts, return_traj=True)
         ms = _events_time(lambda: binding.solve_batch(prob, xq, t, int(w["N"]), opts, out=res,
                                                       stream=stream), 2, 1, flush, stream, tag)
@@ -190,6 +193,24 @@ def measure_other_configs(dev, flush, stream, peak):
             "fp64_2048_points": {"solves_per_s": conv64 / (ms64 * 1e-3), "ms_per_step": ms64,
                                  "converged": conv64},
             "fp32_over_fp64": (conv / ms) / (conv64 / ms64) if conv64 else None}
+
+    # the Hopf form (Algorithm 2) on the 12-D workload, autotuned launch shape;
+    # a solve counts when converged and within 1e-4 of the FP64 Hopf value
+    wqh = W.quadcopter()
+    ms, conv, iters, r32 = run_uniform(wqh, "fp32", "timed_hopf_qc", formulation="hopf", tune=True)
+    ms64, conv64, _, r64 = run_uniform(wqh, "fp64", "timed_hopf_qc_fp64", formulation="hopf",
+                                       tune=True)
+    ok = ((r32["status"] == 0) & (r64["status"] == 0)
+          & ((r32["V"] - r64["V"]).abs() <= 1e-4 * r64["V"].abs().clamp_min(1.0)))
+    n_ok = int(ok.sum().item())
+    flops = iters * 64 * QC_FLOPS_PER_NODE_ITER
+    out["hopf_quadcopter12d_B4096_N64"] = {
+        "fp32": {"solves_per_s": n_ok / (ms * 1e-3), "ms_per_step": ms, "converged_accurate": n_ok,
+                 "tflops": flops / (ms * 1e-3) / 1e12,
+                 "frac_of_fp32_peak": flops / (ms * 1e-3) / 1e12 / peak},
+        "fp64": {"solves_per_s": conv64 / (ms64 * 1e-3), "ms_per_step": ms64, "converged": conv64},
+        "fp32_over_fp64": (n_ok / ms) / (conv64 / ms64) if conv64 else None,
+        "note": "trajectories written (the headline step writes V and status only)"}
 
     rw = W.ragged_mix()
     probs = [binding.Problem.from_workload(p) for p in rw["problems"]]

@@ -60,6 +60,16 @@ enum {
  * value sum in FP64; FP64 runs everything in double.                        */
 enum { HJ_PREC_FP32 = 0, HJ_PREC_FP64 = 1 };
 
+/* Saddle problem solved (hj_solver_opts.formulation).
+ *   HJ_FORM_LAX   Algorithm 1, Eq. (disclaxBE): unknowns x_0..x_{N-1}, p_1..p_N.
+ *   HJ_FORM_HOPF  Algorithm 2, Eq. (dischopf): x_0 eliminated through the convex
+ *                 conjugate, min_{x_0} g(x_0) - <p_1, x_0> = -g*(p_1) with
+ *                 g*(p) = <p, c> + 1/2 sum_i p_i^2 / W_i^2 (every W_i nonzero);
+ *                 the j = 1 dual step is the joint prox of g* and delta H (the
+ *                 appendix's Hopf tutorial algorithm).  For convex g both have
+ *                 the same saddle value.                                        */
+enum { HJ_FORM_LAX = 0, HJ_FORM_HOPF = 1 };
+
 /* Per-point outcome written to status[].  HJ_POINT_INVALID marks a point whose
  * own N was outside the range of the kernel it was routed to (ragged batches:
  * N[b] outside 1..256); such a point is not iterated.                        */
@@ -100,16 +110,20 @@ hj_status hj_problem_destroy(hj_problem prob);
  *   init_radius  x_j^0 = x + r u, p_j^0 = r u', u, u' in [-1, 1)^d (Section 6).
  *   point_offset global index of the batch's first point: the initial guess of
  *                point b depends on (seed, point_offset + b) only, so a batch
- *                split into slices reproduces the unsplit run.                */
+ *                split into slices reproduces the unsplit run.
+ *   formulation  HJ_FORM_LAX (0, the default of a zeroed struct) or HJ_FORM_HOPF;
+ *                Hopf needs every W_i nonzero (HJ_ERR_INVALID_ARG otherwise).  */
 typedef struct {
   double sigma, tau, theta, tol;
   int32_t max_iter, check_every, inner_steps, precision;
   uint64_t seed;
   double init_radius;
   int64_t point_offset;
+  int32_t formulation;
 } hj_solver_opts;
 
-/* Solve B independent points with a common N (Algorithm 1, Eq. (disclaxBE)).
+/* Solve B independent points with a common N (Algorithm 1, Eq. (disclaxBE); with
+ * opts->formulation = HJ_FORM_HOPF, Algorithm 2, Eq. (dischopf)).
  *   xq       (device) [B][d] double: query points x (x_N is pinned to them).
  *   t        (device) [B] double: horizons t > 0; delta = t / N per point.
  *   N        number of time steps, 1..256 (nodes j = 0..N).
@@ -117,11 +131,13 @@ typedef struct {
  *            summed in FP64.
  *   iters    (device) [B] int32 out: iterations run.
  *   status   (device) [B] int8 out: HJ_POINT_*.
- *   traj_x   (device, may be NULL) [B][N+1][d] out: x_0..x_N.
+ *   traj_x   (device, may be NULL) [B][N+1][d] out: x_0..x_N (Hopf: x_0 is the
+ *            minimiser grad g*(p_1) = c + p_1 / W^2 of g(x_0) - <p_1, x_0>).
  *   traj_p   (device, may be NULL) [B][N+1][d] out: p_0 (= 0), p_1..p_N.
  *   warm_x, warm_p (device, may both be NULL) [B][N+1][d] in: initial iterate
  *            instead of the random guess (resume); warm_x[b][N] is ignored
- *            (x_N = x) and warm_p[b][0] is ignored (p_0 = 0).
+ *            (x_N = x) and warm_p[b][0] is ignored (p_0 = 0); Hopf also
+ *            ignores warm_x[b][0].
  *   The trajectory and warm-start arrays have the element type of `precision`.
  * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_STEP_SIZE, HJ_ERR_UNSUPPORTED, HJ_ERR_CUDA.
  * Calls that share one handle must be ordered on one stream (the handle owns
@@ -142,6 +158,9 @@ hj_status hj_solve_batch(hj_problem prob, int64_t B,
  *   dV/dtheta = -delta sum_{j=1..N} dH/dtheta(x_j, p_j)     (theta = dyn parameters),
  *   dV/dx_q   = p_N - delta grad_x H(x_N, p_N)              (x_N = x_q is pinned),
  * which for H independent of x is the costate p_N (Section 2: p = grad_x phi).
+ * The same formulas hold at a Hopf saddle with x_0 = grad g*(p_1), the node 0
+ * that hj_solve_batch writes for HJ_FORM_HOPF (-g*(p_1) has the derivatives
+ * p_1^2 / W^3 and -p_1 in W and c).
  *   t        (device) [B] horizons; traj_x, traj_p (device) [B][N+1][d] in the
  *            precision's type (as written by hj_solve_batch).
  *   dL_dV    (device) [B] weights w_b (e.g. 1/B for the mean value).
@@ -174,7 +193,7 @@ hj_status hj_solve_grad(hj_problem prob, int64_t B, const double* t, int32_t N,
  *   dL_dV, dW, dc, ddyn, dxq  as hj_solve_grad (dxq required).
  * Families: quadcopter (ddyn: m, a_h, g_z, eps) and quadratic with d <= 4;
  * N <= 256, and N <= 128 for the quadcopter in FP64; opts->inner_steps == 1
- * (HJ_ERR_UNSUPPORTED otherwise).
+ * and opts->formulation == HJ_FORM_LAX (HJ_ERR_UNSUPPORTED otherwise).
  * Allocates a workspace of about 3 (N+1) d (max_iters/checkpoint_every + 1)
  * values per CTA of a grid of 4 CTAs per SM, and synchronises `stream`.
  * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_STEP_SIZE, HJ_ERR_UNSUPPORTED, HJ_ERR_OOM,

@@ -61,6 +61,8 @@ hj_status hj_problem_create(hj_problem* out, int32_t family, int32_t d, const do
   if (p == nullptr) return HJ_ERR_OOM;
   p->family = family;
   p->d = d;
+  for (int i = 0; i < d; ++i)
+    if (W[i] == 0.0) p->w_nonzero = false;
   if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return HJ_ERR_CUDA; }
   std::vector<double> w2(d);
   for (int i = 0; i < d; ++i) w2[i] = W[i] * W[i];
@@ -113,6 +115,7 @@ hj_status hj_solve_batch(hj_problem prob, int64_t B, const double* xq, const dou
   const hj_solver_opts& o = *opts;
   const hj_status oc = check_opts(o);
   if (oc != HJ_OK) return oc;
+  if (check_formulation(prob, o) != HJ_OK) return HJ_ERR_INVALID_ARG;
   if ((warm_x == nullptr) != (warm_p == nullptr)) return HJ_ERR_INVALID_ARG;
   if (o.point_offset + B > (int64_t(1) << 32)) return HJ_ERR_INVALID_ARG;
   if (B == 0) return HJ_OK;
@@ -177,6 +180,7 @@ hj_status hj_solve_grad_unrolled(hj_problem prob, int64_t B, const double* xq, c
   if (oc != HJ_OK) return oc;
   if (max_iters < 0 || checkpoint_every < 1) return HJ_ERR_INVALID_ARG;
   if (opts->inner_steps != 1) return HJ_ERR_UNSUPPORTED;   // one gradient step per x-update
+  if (opts->formulation != HJ_FORM_LAX) return HJ_ERR_UNSUPPORTED;   // the Lax iteration only
   const bool qc = prob->family == HJ_FAMILY_QUADCOPTER;
   if (!(qc || (prob->family == HJ_FAMILY_QUADRATIC && prob->d <= 4))) return HJ_ERR_UNSUPPORTED;
   if (dW == nullptr || dc == nullptr || dxq == nullptr || (qc && ddyn == nullptr))
@@ -261,6 +265,7 @@ hj_status hj_autotune(hj_problem prob, int64_t B, const double* xq, const double
   if (N < 1 || N > hj::kMaxN || repeats < 1) return HJ_ERR_INVALID_ARG;
   const hj_status oc = check_opts(*opts);
   if (oc != HJ_OK) return oc;
+  if (check_formulation(prob, *opts) != HJ_OK) return HJ_ERR_INVALID_ARG;
   const bool f64 = opts->precision == HJ_PREC_FP64;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   double* V = nullptr;

@@ -10,6 +10,9 @@
 //   H64(x, p)               H in double from the iterates, for the value
 //                           (fval of Algorithm 1); converts element by element
 //   Ht(x, p)                H in the iterate type (the FP32 path's value terms)
+//   prox_first(ctx, pc, x, v, hs, hc)
+//                           the Hopf form's node-1 dual step: the prox of
+//                           sigma g* + lam H, hs = sigma / W^2, hc = sigma c
 // All families have L = |u|^2/2, so H = <p, f0(x)> + |B(x)^T p|^2/2 (Section 2).
 #pragma once
 #include "hj_internal.cuh"
@@ -116,14 +119,21 @@ struct FamQuadratic {
   static constexpr bool kHasGradX = false;
   struct Shared {};
   struct Ctx {};
-  struct PC { T s; };
+  struct PC { T s, lam; };
   __device__ static void load_shared(const SolveArgs<T>&, Shared&) {}
   __device__ FamQuadratic(const SolveArgs<T>&, const Shared&) {}
-  __device__ __forceinline__ PC point(T lam) const { return PC{T(1) / (T(1) + lam)}; }
+  __device__ __forceinline__ PC point(T lam) const { return PC{T(1) / (T(1) + lam), lam}; }
   __device__ __forceinline__ void context(const T (&)[D], Ctx&) const {}
   __device__ __forceinline__ void prox(const Ctx&, const PC& pc, const T (&)[D], T (&v)[D]) const {
 #pragma unroll
     for (int k = 0; k < D; ++k) v[k] *= pc.s;
+  }
+  // Hopf form, node 1: argmin_p sigma g*(p) + lam H + |p - v|^2/2 with
+  // g*(p) = <p, c> + 1/2 sum p_k^2 / W_k^2; hs = sigma / W^2, hc = sigma c.
+  __device__ __forceinline__ void prox_first(const Ctx&, const PC& pc, const T (&)[D], T (&v)[D],
+                                             const T* hs, const T* hc) const {
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = fdiv<T>(v[k] - hc[k], T(1) + pc.lam + hs[k]);
   }
   __device__ __forceinline__ void gradx(const Ctx&, const T (&)[D], const T (&)[D], T (&g)[D]) const {
 #pragma unroll
@@ -238,6 +248,34 @@ struct FamQuadcopter {
     v[8] = (w2 - f * b2) * ial;
   }
 
+  // Hopf form, node 1: the prox above with sigma g*(p) added, g*(p) = <p, c> +
+  // 1/2 sum p_k^2 / W_k^2 (hs = sigma / W^2, hc = sigma c):
+  //   (diag(1 + lam eps + hs) + lam B B^T) p = v - hc - lam f0.
+  // Rows 6-8 are a rank-1 update of the diagonal L = diag(1 + lam eps + hs_6..8):
+  //   p = L^-1 w - L^-1 b (lam b^T L^-1 w) / (1 + lam b^T L^-1 b).
+  __device__ __forceinline__ void prox_first(const Ctx& c, const PC& pc, const T (&x)[D],
+                                             T (&v)[D], const T* hs, const T* hc) const {
+    const T lam = pc.lam;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = fdiv<T>(v[k] - hc[k] - lam * x[6 + k], pc.al + hs[k]);
+#pragma unroll
+    for (int k = 9; k < 12; ++k) v[k] = fdiv<T>(v[k] - hc[k], pc.al + lam + hs[k]);
+    T y[3], q[3], b[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const T il = fdiv<T>(T(1), pc.al + hs[6 + r]);
+      const T w = v[6 + r] - hc[6 + r] - (pc.lam_ah * c.a[r] - (r == 2 ? pc.lam_gz : T(0)));
+      b[r] = c.a[r] * m_inv;
+      y[r] = il * w;
+      q[r] = il * b[r];
+    }
+    const T by = b[0] * y[0] + b[1] * y[1] + b[2] * y[2];
+    const T bq = b[0] * q[0] + b[1] * q[1] + b[2] * q[2];
+    const T f = fdiv<T>(lam * by, T(1) + lam * bq);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) v[6 + r] = y[r] - f * q[r];
+  }
+
   __device__ __forceinline__ void gradx(const Ctx& c, const T (&)[D], const T (&p)[D],
                                         T (&g)[D]) const {
     const T u0 = (c.a[0] * p[6] + c.a[1] * p[7] + c.a[2] * p[8]) * m_inv;
@@ -314,6 +352,14 @@ struct FamTanhDrift {
                                        T (&v)[D]) const {
 #pragma unroll
     for (int k = 0; k < D; ++k) v[k] = (v[k] - pc.lam * c.a[k]) * pc.s;
+  }
+  // Hopf form, node 1 (hs = sigma / W^2, hc = sigma c):
+  //   (1 + lam + hs_k) p_k = v_k - hc_k - lam a_k.
+  __device__ __forceinline__ void prox_first(const Ctx& c, const PC& pc, const T (&)[D],
+                                             T (&v)[D], const T* hs, const T* hc) const {
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      v[k] = fdiv<T>(v[k] - hc[k] - pc.lam * c.a[k], T(1) + pc.lam + hs[k]);
   }
   __device__ __forceinline__ void gradx(const Ctx& c, const T (&)[D], const T (&p)[D],
                                         T (&g)[D]) const {

@@ -26,6 +26,7 @@ struct SolveArgs {
   // (double)s < tol exactly when s < tol_t, so the test needs no FP64 operation.
   T tol_t;
   int32_t max_iter, check_every, inner_steps;
+  int32_t formulation;   // HJ_FORM_LAX or HJ_FORM_HOPF
   uint64_t seed;
   double radius;
   int64_t point_offset;
@@ -203,6 +204,13 @@ template <typename T>
 hj_status launch_warp_quadcopter(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 template <typename T>
 hj_status launch_warp_tanh(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
+// the same launchers for the Hopf form (Algorithm 2)
+template <typename T>
+hj_status launch_warp_quadratic_hopf(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
+template <typename T>
+hj_status launch_warp_quadcopter_hopf(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
+template <typename T>
+hj_status launch_warp_tanh_hopf(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 // Default launch shape for (family, d, Nmax); {0, 0} when no warp kernel fits.
 WarpConfig default_warp_config(int family, int d, int Nmax, bool fp64);
 // Whether the warp kernel has an instantiation for (family, d, cfg, precision).

@@ -65,7 +65,7 @@ struct Layout {
 
 // TWO: keep both A^T and A in shared memory (vector loads in both products);
 // otherwise only A, and the first product reads it with strided scalar loads.
-template <typename T, bool TWO, bool DRIFT>
+template <typename T, bool TWO, bool DRIFT, bool HOPF>
 __global__ void __launch_bounds__(512)
 lax_td_cta_kernel(const SolveArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -80,6 +80,8 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
   T* Wk = Z + L.s_elems;
   double* red = reinterpret_cast<double*>(Wk + L.s_elems);  // [2 * nwarps] value epilogue
   T* tred = reinterpret_cast<T*>(red);                      // [2 * nwarps] stopping test
+  T* hsv = reinterpret_cast<T*>(red + 32);                  // Hopf form: sigma / W^2, sigma c
+  T* hcv = hsv + dp;
   __shared__ unsigned long long s_point;
 
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -93,6 +95,10 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
     }
   }
 
+  for (int i = threadIdx.x; i < dp; i += blockDim.x) {
+    hsv[i] = (HOPF && i < d) ? T(a.sigma / a.W2[i]) : T(0);
+    hcv[i] = (i < d) ? T(a.sigma * a.c[i]) : T(0);
+  }
   const T sig = a.sigma_t, tau = a.tau_t, th = a.theta_t;
 
   for (;;) {
@@ -121,7 +127,7 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
     for (int e = tid; e < dp * Np; e += nthr) {
       const int k = e / Np, j = e - k * Np;
       T xv = T(0), pv = T(0);
-      if (k < d && j <= N) {
+      if (k < d && j <= N && !(HOPF && j == 0)) {         // Hopf: x_0 is not a variable (0)
         const double xq = ref.xq[k];
         if (a.warm_x == nullptr) {
           const InitGuess<T> ig(a.radius);
@@ -175,7 +181,9 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
               const int e = i * Np + j;
               const T av = DRIFT ? tanh_c<T>(acc[r][c]) : T(0);
               const T v = P[e] + sig * (Z[e] - Z[e - 1]);
-              const T pn = (v - lam * av) * ilam;
+              const T pn = (HOPF && j == 1)         // Hopf node 1: prox of sigma g* + lam H
+                               ? (v - hcv[i] - lam * av) / (T(1) + lam + hsv[i])
+                               : (v - lam * av) * ilam;
               if (chk) { const T df = pn - P[e]; rp += df * df; }
               P[e] = pn;
               Wk[e] = (T(1) - av * av) * pn;
@@ -219,7 +227,7 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
           }
         }
       }
-      if (tid < d) {
+      if (!HOPF && tid < d) {
         const int e = tid * Np;
         const T w2 = T(a.W2[tid]), cc = T(a.c[tid]);
         const T xo = X[e];
@@ -273,8 +281,13 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
       }
     }
     if (tid < d) {
-      const double e0 = (double)X[tid * Np] - a.c[tid];
-      acc += 0.5 * a.W2[tid] * e0 * e0;
+      if (HOPF) {                                         // -g*(p_1)
+        const double p1 = (double)P[tid * Np + 1];
+        acc -= p1 * a.c[tid] + 0.5 * p1 * p1 / a.W2[tid];
+      } else {
+        const double e0 = (double)X[tid * Np] - a.c[tid];
+        acc += 0.5 * a.W2[tid] * e0 * e0;
+      }
     }
     acc = warp_sum<double>(acc);
     __syncthreads();
@@ -290,7 +303,10 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
     if (a.traj_x != nullptr || a.traj_p != nullptr) {
       for (int e = tid; e < (N + 1) * d; e += nthr) {
         const int j = e / d, i = e - j * d;
-        if (a.traj_x != nullptr) a.traj_x[ref.traj + e] = X[i * Np + j];
+        if (a.traj_x != nullptr)                          // Hopf: x_0 = c + p_1 / W^2
+          a.traj_x[ref.traj + e] = (HOPF && j == 0)
+                                       ? T(a.c[i] + (double)P[i * Np + 1] / a.W2[i])
+                                       : X[i * Np + j];
         if (a.traj_p != nullptr) a.traj_p[ref.traj + e] = (j == 0) ? T(0) : P[i * Np + j];
       }
     }
@@ -301,12 +317,12 @@ template <typename T, bool TWO>
 size_t smem_bytes(int d, int N, bool drift) {
   const Layout L(d, N);
   const size_t na = drift ? (TWO ? 2 : 1) : 0;
-  return (na * L.a_elems + 4 * L.s_elems) * sizeof(T) + 2 * 16 * sizeof(double);
+  return (na * L.a_elems + 4 * L.s_elems + 2 * L.dp) * sizeof(T) + 2 * 16 * sizeof(double);
 }
 
-template <typename T, bool TWO, bool DRIFT>
-hj_status launch(const SolveArgs<T>& a, cudaStream_t s, size_t smem) {
-  auto kern = lax_td_cta_kernel<T, TWO, DRIFT>;
+template <typename T, bool TWO, bool DRIFT, bool HOPF>
+hj_status launch_form(const SolveArgs<T>& a, cudaStream_t s, size_t smem) {
+  auto kern = lax_td_cta_kernel<T, TWO, DRIFT, HOPF>;
   int dev = 0, nsm = 0, max_optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return HJ_ERR_CUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -332,6 +348,12 @@ hj_status launch(const SolveArgs<T>& a, cudaStream_t s, size_t smem) {
   const int grid = (int)(a.B < cap ? a.B : cap);
   kern<<<grid, threads, smem, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? HJ_OK : HJ_ERR_CUDA;
+}
+
+template <typename T, bool TWO, bool DRIFT>
+hj_status launch(const SolveArgs<T>& a, cudaStream_t s, size_t smem) {
+  return a.formulation == HJ_FORM_HOPF ? launch_form<T, TWO, DRIFT, true>(a, s, smem)
+                                       : launch_form<T, TWO, DRIFT, false>(a, s, smem);
 }
 
 }  // namespace

@@ -38,7 +38,7 @@ constexpr int kTJ = 8;   // time nodes per tile
 
 struct TileLayout {
   int d, dp, TIc, TJc, Ns;
-  size_t head_bytes;     // per-group item slots, g-prox constants
+  size_t head_bytes;     // per-group item slots, g-prox and Hopf node-1 constants
   size_t a_floats;       // A^T and A
   size_t grp_floats;     // Xs, Ws, Zb, Pb, reductions of one group
   __host__ __device__ TileLayout(int d_, int Nmax, int G, int M) {
@@ -47,7 +47,7 @@ struct TileLayout {
     TIc = dp / kTI;
     TJc = (Nmax + kTJ - 1) / kTJ;
     Ns = kTJ * TJc + 4;                              // row stride of Xs and Ws
-    head_bytes = (size_t)((M * 8 + 15) / 16) * 16 + 2 * (size_t)dp * sizeof(float);
+    head_bytes = (size_t)((M * 8 + 15) / 16) * 16 + 4 * (size_t)dp * sizeof(float);
     a_floats = 2 * (size_t)d * dp;
     grp_floats = 2 * (size_t)dp * Ns + 2 * (size_t)TJc * dp + 6 * (size_t)G;
     grp_floats = (grp_floats + 3) & ~size_t(3);       // keep 16-byte alignment
@@ -106,7 +106,7 @@ __device__ __forceinline__ void tile_product(const float* M, const float* S, int
   }
 }
 
-template <int G, bool TH1>
+template <int G, bool TH1, bool HOPF>
 __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float> a, int M) {
   extern __shared__ __align__(16) unsigned char smem[];
   const TileLayout L(a.d, a.N, G, M);
@@ -114,7 +114,9 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
   unsigned long long* items = reinterpret_cast<unsigned long long*>(smem);
   float* goff = reinterpret_cast<float*>(smem + (size_t)((M * 8 + 15) / 16) * 16);
   float* ginv = goff + dp;
-  float* At = ginv + dp;                          // At[k*dp + i] = A[i][k]
+  float* hs = ginv + dp;                          // Hopf form: sigma / W^2 and sigma c
+  float* hc = hs + dp;
+  float* At = hc + dp;                            // At[k*dp + i] = A[i][k]
   float* Am = At + (size_t)d * dp;                // Am[k*dp + i] = A[k][i]
   const int grp = (int)threadIdx.x / (32 * G);
   float* Xs = Am + (size_t)d * dp + (size_t)grp * L.grp_floats;
@@ -133,6 +135,8 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
     const double w2 = i < d ? a.W2[i] : 0.0, cc = i < d ? a.c[i] : 0.0;
     goff[i] = (float)(a.tau * w2 * cc);
     ginv[i] = (float)(1.0 / (1.0 + a.tau * w2));
+    hs[i] = (HOPF && i < d) ? (float)(a.sigma / w2) : 0.f;
+    hc[i] = (float)(a.sigma * cc);
   }
   __syncthreads();
   if (grp >= M) return;                           // no thread of a partial group exists
@@ -188,8 +192,8 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
           }
           x[r][c] = xv; p[r][c] = pv; z[r][c] = xv;
         }
-        float x0v = 0.f;
-        if (row && jt == 0)
+        float x0v = 0.f;                          // Hopf: x_0 is not a variable (0)
+        if (row && jt == 0 && !HOPF)
           x0v = (a.warm_x == nullptr) ? ig.x(xq, a.seed, pt, 0, i) : a.warm_x[ref.traj + i];
         x0[r] = x0v; z0[r] = x0v;
       }
@@ -224,7 +228,9 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
               const float av = tanhf(acc[r][c]);
               const float zl = (c == 0) ? zL[r] : z[r][c - 1];
               const float v = p[r][c] + sig * (z[r][c] - zl);
-              const float pn = (v - lam * av) * ilam;
+              const float pn = (HOPF && c == 0 && jt == 0)  // Hopf node 1: prox of sigma g* + lam H
+                                   ? __fdividef(v - hc[i0 + r] - lam * av, 1.f + lam + hs[i0 + r])
+                                   : (v - lam * av) * ilam;
               if constexpr (CHK) { const float e = pn - p[r][c]; rp += e * e; }
               p[r][c] = pn;
               w[c] = (1.f - av * av) * pn;
@@ -257,7 +263,7 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
                 x[r][c] = xn;
               }
             }
-            if (jt == 0) {                        // x_0 <- prox_{tau g}(x_0 + tau p_1)
+            if (jt == 0 && !HOPF) {               // x_0 <- prox_{tau g}(x_0 + tau p_1)
               const float xo = x0[r];
               const float xn = (xo + tau * p[r][0] + goff[i]) * ginv[i];
               if constexpr (CHK) { const float e = xn - xo; rx += e * e; }
@@ -317,8 +323,13 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
             }
           }
           if (jt == 0) {
-            const double e = (double)x0[r] - a.c[i];
-            vacc += 0.5 * a.W2[i] * e * e;
+            if (HOPF) {                           // -g*(p_1)
+              const double p1 = (double)p[r][0];
+              vacc -= p1 * a.c[i] + 0.5 * p1 * p1 / a.W2[i];
+            } else {
+              const double e = (double)x0[r] - a.c[i];
+              vacc += 0.5 * a.W2[i] * e * e;
+            }
           }
         }
       }
@@ -350,7 +361,8 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
           }
         }
         if (jt == 0) {
-          if (a.traj_x != nullptr) a.traj_x[ref.traj + i] = x0[r];
+          if (a.traj_x != nullptr)                // Hopf: x_0 = grad g*(p_1) = c + p_1 / W^2
+            a.traj_x[ref.traj + i] = HOPF ? (float)(a.c[i] + (double)p[r][0] / a.W2[i]) : x0[r];
           if (a.traj_p != nullptr) a.traj_p[ref.traj + i] = 0.f;
         }
       }
@@ -358,9 +370,9 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
   }
 }
 
-template <int G, bool TH1>
+template <int G, bool TH1, bool HOPF>
 hj_status launch_g(const SolveArgs<float>& a, int M, size_t smem, cudaStream_t s) {
-  auto kern = lax_td_tile_kernel<G, TH1>;
+  auto kern = lax_td_tile_kernel<G, TH1, HOPF>;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return HJ_ERR_CUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -409,11 +421,19 @@ hj_status launch_td_tile_solver(const SolveArgs<float>& a, cudaStream_t s) {
   }
   if (smem > (size_t)max_optin) return HJ_ERR_UNSUPPORTED;
   const bool th1 = a.theta == 1.0;
+  if (a.formulation == HJ_FORM_HOPF) {
+    switch (G) {
+      case 1: return th1 ? launch_g<1, true, true>(a, M, smem, s) : launch_g<1, false, true>(a, M, smem, s);
+      case 2: return th1 ? launch_g<2, true, true>(a, M, smem, s) : launch_g<2, false, true>(a, M, smem, s);
+      case 4: return th1 ? launch_g<4, true, true>(a, M, smem, s) : launch_g<4, false, true>(a, M, smem, s);
+      default: return th1 ? launch_g<8, true, true>(a, M, smem, s) : launch_g<8, false, true>(a, M, smem, s);
+    }
+  }
   switch (G) {
-    case 1: return th1 ? launch_g<1, true>(a, M, smem, s) : launch_g<1, false>(a, M, smem, s);
-    case 2: return th1 ? launch_g<2, true>(a, M, smem, s) : launch_g<2, false>(a, M, smem, s);
-    case 4: return th1 ? launch_g<4, true>(a, M, smem, s) : launch_g<4, false>(a, M, smem, s);
-    default: return th1 ? launch_g<8, true>(a, M, smem, s) : launch_g<8, false>(a, M, smem, s);
+    case 1: return th1 ? launch_g<1, true, false>(a, M, smem, s) : launch_g<1, false, false>(a, M, smem, s);
+    case 2: return th1 ? launch_g<2, true, false>(a, M, smem, s) : launch_g<2, false, false>(a, M, smem, s);
+    case 4: return th1 ? launch_g<4, true, false>(a, M, smem, s) : launch_g<4, false, false>(a, M, smem, s);
+    default: return th1 ? launch_g<8, true, false>(a, M, smem, s) : launch_g<8, false, false>(a, M, smem, s);
   }
 }
 

@@ -13,6 +13,7 @@
 struct hj_problem_s {
   int family = 0, d = 0, device = 0;
   double qc[4] = {0, 0, 0, 0};        // m, a_h, g_z, eps
+  bool w_nonzero = true;              // every W_i != 0 (g* finite: the Hopf form)
   double* W2 = nullptr;               // [d]  W_i^2
   double* W = nullptr;                // [d]  W_i as given (sign kept for dV/dW)
   double* c = nullptr;                // [d]
@@ -115,6 +116,7 @@ hj::SolveArgs<T> make_args(const hj_problem_s* prob, int64_t B, int32_t N,
   if ((double)a.tol_t < o.tol) a.tol_t = std::nextafter(a.tol_t, T(INFINITY));
   a.max_iter = o.max_iter; a.check_every = o.check_every; a.inner_steps = o.inner_steps;
   a.seed = o.seed; a.radius = o.init_radius; a.point_offset = o.point_offset;
+  a.formulation = o.formulation;
   a.xq = xq; a.t = t; a.V = V; a.iters = iters; a.status = status;
   a.W2 = prob->W2; a.c = prob->c; a.A64 = prob->Ad;
   a.qc_m = prob->qc[0]; a.qc_ah = prob->qc[1]; a.qc_gz = prob->qc[2]; a.qc_eps = prob->qc[3];
@@ -130,10 +132,16 @@ inline hj_status check_opts(const hj_solver_opts& o) {
     return HJ_ERR_INVALID_ARG;
   if (o.max_iter < 1 || o.check_every < 1 || o.inner_steps < 1) return HJ_ERR_INVALID_ARG;
   if (o.precision != HJ_PREC_FP32 && o.precision != HJ_PREC_FP64) return HJ_ERR_INVALID_ARG;
+  if (o.formulation != HJ_FORM_LAX && o.formulation != HJ_FORM_HOPF) return HJ_ERR_INVALID_ARG;
   if (!(std::isfinite(o.init_radius) && o.init_radius >= 0.0) || o.point_offset < 0)
     return HJ_ERR_INVALID_ARG;
   if (4.0 * o.sigma * o.tau >= 1.0) return HJ_ERR_STEP_SIZE;
   return HJ_OK;
+}
+
+// The Hopf form needs g* finite: every W_i nonzero.
+inline hj_status check_formulation(const hj_problem_s* p, const hj_solver_opts& o) {
+  return (o.formulation == HJ_FORM_HOPF && !p->w_nonzero) ? HJ_ERR_INVALID_ARG : HJ_OK;
 }
 
 template <typename T>

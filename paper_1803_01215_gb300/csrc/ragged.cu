@@ -123,8 +123,10 @@ hj_status hj_ragged_plan_create(hj_ragged_plan* out, int32_t n_prob, const hj_pr
   if (opts->point_offset + B > (int64_t(1) << 32)) return HJ_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return HJ_ERR_CUDA;
-  for (int i = 0; i < n_prob; ++i)
+  for (int i = 0; i < n_prob; ++i) {
     if (probs[i] == nullptr || probs[i]->device != dev) return HJ_ERR_INVALID_ARG;
+    if (check_formulation(probs[i], *opts) != HJ_OK) return HJ_ERR_INVALID_ARG;
+  }
   for (int64_t b = 0; b < B; ++b) {
     if (prob_of[b] < 0 || prob_of[b] >= n_prob) return HJ_ERR_INVALID_ARG;
     if (N_of[b] < 1 || N_of[b] > hj::kMaxN) return HJ_ERR_INVALID_ARG;

@@ -95,6 +95,9 @@ hj_status hj_solve_batch_static(int32_t family, int32_t d, const double* dyn, in
   if (N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;
   const hj_status oc = check_opts(*opts);
   if (oc != HJ_OK) return oc;
+  if (opts->formulation == HJ_FORM_HOPF)
+    for (int i = 0; i < d; ++i)
+      if (W[i] == 0.0) return HJ_ERR_INVALID_ARG;
   if (opts->point_offset + B > (int64_t(1) << 32)) return HJ_ERR_INVALID_ARG;
   const bool has_A = family == HJ_FAMILY_TANH_DRIFT;
   const size_t tsize = opts->precision == HJ_PREC_FP32 ? sizeof(float) : sizeof(double);
@@ -143,6 +146,7 @@ hj_status hj_solve_batch_static(int32_t family, int32_t d, const double* dyn, in
   hj_problem_s view;
   view.family = family;
   view.d = d;
+  view.w_nonzero = true;
   view.device = dev;
   for (int i = 0; i < 4; ++i) view.qc[i] = (family == HJ_FAMILY_QUADCOPTER) ? dyn[i] : 0.0;
   view.W2 = reinterpret_cast<double*>(base + L.W2);

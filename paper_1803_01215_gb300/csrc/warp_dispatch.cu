@@ -37,10 +37,14 @@ template <typename T>
 hj_status launch_warp_solver(int family, const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s) {
   if (!warp_config_available(family, a.d, cfg, sizeof(T) == 8)) return HJ_ERR_UNSUPPORTED;
   if (a.N > 32 * cfg.G * cfg.NPL) return HJ_ERR_UNSUPPORTED;
+  const bool hopf = a.formulation == HJ_FORM_HOPF;
   switch (family) {
-    case HJ_FAMILY_QUADRATIC: return launch_warp_quadratic<T>(a, cfg, s);
-    case HJ_FAMILY_QUADCOPTER: return launch_warp_quadcopter<T>(a, cfg, s);
-    case HJ_FAMILY_TANH_DRIFT: return launch_warp_tanh<T>(a, cfg, s);
+    case HJ_FAMILY_QUADRATIC:
+      return hopf ? launch_warp_quadratic_hopf<T>(a, cfg, s) : launch_warp_quadratic<T>(a, cfg, s);
+    case HJ_FAMILY_QUADCOPTER:
+      return hopf ? launch_warp_quadcopter_hopf<T>(a, cfg, s) : launch_warp_quadcopter<T>(a, cfg, s);
+    case HJ_FAMILY_TANH_DRIFT:
+      return hopf ? launch_warp_tanh_hopf<T>(a, cfg, s) : launch_warp_tanh<T>(a, cfg, s);
     default: return HJ_ERR_UNSUPPORTED;
   }
 }

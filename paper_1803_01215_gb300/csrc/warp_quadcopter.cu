@@ -6,7 +6,7 @@ namespace hj {
 template <typename T>
 hj_status launch_warp_quadcopter(const SolveArgs<T>& a, WarpConfig c, cudaStream_t s) {
   switch (a.d) {
-    case 12: return launch_warp_shape<T, FamQuadcopter, 12>(a, c, s);
+    case 12: return launch_warp_shape<T, FamQuadcopter, 12, false>(a, c, s);
     default: return HJ_ERR_UNSUPPORTED;
   }
 }

@@ -6,10 +6,10 @@ namespace hj {
 template <typename T>
 hj_status launch_warp_quadratic(const SolveArgs<T>& a, WarpConfig c, cudaStream_t s) {
   switch (a.d) {
-    case 1: return launch_warp_shape<T, FamQuadratic, 1>(a, c, s);
-    case 2: return launch_warp_shape<T, FamQuadratic, 2>(a, c, s);
-    case 3: return launch_warp_shape<T, FamQuadratic, 3>(a, c, s);
-    case 4: return launch_warp_shape<T, FamQuadratic, 4>(a, c, s);
+    case 1: return launch_warp_shape<T, FamQuadratic, 1, false>(a, c, s);
+    case 2: return launch_warp_shape<T, FamQuadratic, 2, false>(a, c, s);
+    case 3: return launch_warp_shape<T, FamQuadratic, 3, false>(a, c, s);
+    case 4: return launch_warp_shape<T, FamQuadratic, 4, false>(a, c, s);
     default: return HJ_ERR_UNSUPPORTED;
   }
 }

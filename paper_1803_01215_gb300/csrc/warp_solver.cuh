@@ -49,6 +49,8 @@ struct WarpShared {
   typename F::Shared fam;
   alignas(16) T g_off[DP];
   alignas(16) T g_inv[DP];
+  alignas(16) T hs[DP];                    // Hopf form: sigma / W^2 and sigma c (node-1 prox)
+  alignas(16) T hc[DP];
   double w2d[D], cd[D];
   alignas(16) T zs[kGroups][32 * G][DP];   // z (in the epilogue x) of each lane's last node
   alignas(16) T ps[kGroups][32 * G][DP];   // p of each lane's first node
@@ -111,7 +113,7 @@ __device__ __forceinline__ T relax(T xn, T xo, T th) {
   else return xn + th * (xn - xo);
 }
 
-template <typename T, class F, int D, int NPL, int G, bool TH1>
+template <typename T, class F, int D, int NPL, int G, bool TH1, bool HOPF>
 __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam, int64_t item,
                                             int lane, int wg, WarpShared<T, F, D, G>& sh) {
   const PointRef<T> pt = point_ref(a, item);
@@ -151,7 +153,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
           x[i][k] = xv; p[i][k] = pv; z[i][k] = xv;
         }
       }
-      if (own0) x0 = ig.x(pt.xq[k0], a.seed, gid, 0, k0);
+      if (own0 && !HOPF) x0 = ig.x(pt.xq[k0], a.seed, gid, 0, k0);
     } else {
       const T* wx = a.warm_x + pt.traj;
       const T* wp = a.warm_p + pt.traj;
@@ -167,7 +169,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
           x[i][k] = xv; p[i][k] = pv; z[i][k] = xv;
         }
       }
-      if (own0) x0 = wx[k0];
+      if (own0 && !HOPF) x0 = wx[k0];
     }
     z0 = x0;
   }
@@ -197,7 +199,10 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         if (i == 0) v_sub<T, D>(dz, z[i], zl);
         else v_sub<T, D>(dz, z[i], z[i > 0 ? i - 1 : 0]);
         v_fma<T, D>(v, sig, dz, p[i]);                       // p + sigma (z_j - z_{j-1})
-        fam.prox(ctx[i], pc, x[i], v);
+        if (HOPF && i == 0 && gl == 0)                       // Hopf: node 1 also carries g*
+          fam.prox_first(ctx[i], pc, x[i], v, sh.hs, sh.hc);
+        else
+          fam.prox(ctx[i], pc, x[i], v);
         if constexpr (CHK) {
           T e[D];
           v_sub<T, D>(e, v, p[i]);
@@ -217,7 +222,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
 #pragma unroll
       for (int k = 0; k < D; ++k) pr[k] = T(0);    // the last lane never updates an x with it
     }
-    if (own0) {
+    if (own0 && !HOPF) {
       // x_0 <- prox_{tau g}(x_0 + tau p_1), coordinate k0; p_1 is lane 0's slot
       const T xn = (x0 + tau * pslot[k0] + goff) * ginv;      // (D^T p)_0 = -p_1
       if constexpr (CHK) { const T e = xn - x0; rx += e * e; }
@@ -322,8 +327,13 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
       }
     }
     if (own0) {
-      const double e = (double)x0 - sh.cd[k0];
-      acc += 0.5 * sh.w2d[k0] * e * e;                // g(x_0), coordinate k0
+      if constexpr (HOPF) {                           // -g*(p_1), coordinate k0 (x_0 = 0 above)
+        const double p1 = (double)pslot[k0];
+        acc -= p1 * sh.cd[k0] + 0.5 * p1 * p1 / sh.w2d[k0];
+      } else {
+        const double e = (double)x0 - sh.cd[k0];
+        acc += 0.5 * sh.w2d[k0] * e * e;              // g(x_0), coordinate k0
+      }
     }
   }
   acc = warp_sum<double>(acc);
@@ -346,7 +356,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
       if (jbase + i <= N)
 #pragma unroll
         for (int k = 0; k < D; ++k) o[(size_t)(jbase + i) * D + k] = x[i][k];
-    if (own0) o[k0] = x0;
+    if (own0) o[k0] = HOPF ? T(sh.cd[k0] + (double)pslot[k0] / sh.w2d[k0]) : x0;
   }
   if (a.traj_p != nullptr) {
     T* o = a.traj_p + pt.traj;
@@ -359,7 +369,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   }
 }
 
-template <typename T, class F, int D, int NPL, int G, bool TH1>
+template <typename T, class F, int D, int NPL, int G, bool TH1, bool HOPF>
 __global__ void __launch_bounds__(warp_block_threads<G>())
 lax_warp_kernel(const SolveArgs<T> a) {
   __shared__ WarpShared<T, F, D, G> sh;
@@ -369,6 +379,8 @@ lax_warp_kernel(const SolveArgs<T> a) {
     if (k < D) { sh.w2d[k] = w2; sh.cd[k] = c; }
     sh.g_off[k] = T(a.tau * w2 * c);
     sh.g_inv[k] = T(1.0 / (1.0 + a.tau * w2));
+    sh.hs[k] = (HOPF && k < D) ? T(a.sigma / w2) : T(0);
+    sh.hc[k] = T(a.sigma * c);
   }
   __syncthreads();
   const F fam(a, sh.fam);
@@ -387,15 +399,15 @@ lax_warp_kernel(const SolveArgs<T> a) {
       item = (int64_t)sh.item;
     }
     if (item >= a.B) break;
-    solve_point<T, F, D, NPL, G, TH1>(a, fam, item, lane, wg, sh);
+    solve_point<T, F, D, NPL, G, TH1, HOPF>(a, fam, item, lane, wg, sh);
   }
 }
 
-template <typename T, class F, int D, int NPL, int G, bool TH1>
+template <typename T, class F, int D, int NPL, int G, bool TH1, bool HOPF>
 hj_status launch_warp_cfg_th(const SolveArgs<T>& a, cudaStream_t s) {
   static int blocks_per_sm = -1;
   static int num_sms = 0;
-  auto kern = lax_warp_kernel<T, F, D, NPL, G, TH1>;
+  auto kern = lax_warp_kernel<T, F, D, NPL, G, TH1, HOPF>;
   constexpr int threads = warp_block_threads<G>();
   if (blocks_per_sm < 0) {
     int dev = 0;
@@ -417,33 +429,33 @@ hj_status launch_warp_cfg_th(const SolveArgs<T>& a, cudaStream_t s) {
 }
 
 // theta = 1 (the paper's choice) gets its own kernel
-template <typename T, class F, int D, int NPL, int G>
+template <typename T, class F, int D, int NPL, int G, bool HOPF>
 hj_status launch_warp_cfg(const SolveArgs<T>& a, cudaStream_t s) {
-  return a.theta == 1.0 ? launch_warp_cfg_th<T, F, D, NPL, G, true>(a, s)
-                        : launch_warp_cfg_th<T, F, D, NPL, G, false>(a, s);
+  return a.theta == 1.0 ? launch_warp_cfg_th<T, F, D, NPL, G, true, HOPF>(a, s)
+                        : launch_warp_cfg_th<T, F, D, NPL, G, false, HOPF>(a, s);
 }
 
 // Every (G, NPL) the library instantiates: FP32 G in {1,2,4,8} x NPL in {1,2};
 // FP64 G in {1,2,4,8} x NPL = 1.
-template <typename T, template <typename, int> class F, int D>
+template <typename T, template <typename, int> class F, int D, bool HOPF>
 hj_status launch_warp_shape(const SolveArgs<T>& a, WarpConfig c, cudaStream_t s) {
   constexpr bool f64 = sizeof(T) == 8;
   if (c.NPL == 1) {
     switch (c.G) {
-      case 1: return launch_warp_cfg<T, F<T, D>, D, 1, 1>(a, s);
-      case 2: return launch_warp_cfg<T, F<T, D>, D, 1, 2>(a, s);
-      case 4: return launch_warp_cfg<T, F<T, D>, D, 1, 4>(a, s);
-      case 8: return launch_warp_cfg<T, F<T, D>, D, 1, 8>(a, s);
+      case 1: return launch_warp_cfg<T, F<T, D>, D, 1, 1, HOPF>(a, s);
+      case 2: return launch_warp_cfg<T, F<T, D>, D, 1, 2, HOPF>(a, s);
+      case 4: return launch_warp_cfg<T, F<T, D>, D, 1, 4, HOPF>(a, s);
+      case 8: return launch_warp_cfg<T, F<T, D>, D, 1, 8, HOPF>(a, s);
       default: return HJ_ERR_UNSUPPORTED;
     }
   }
   if constexpr (!f64) {
     if (c.NPL == 2) {
       switch (c.G) {
-        case 1: return launch_warp_cfg<T, F<T, D>, D, 2, 1>(a, s);
-        case 2: return launch_warp_cfg<T, F<T, D>, D, 2, 2>(a, s);
-        case 4: return launch_warp_cfg<T, F<T, D>, D, 2, 4>(a, s);
-        case 8: return launch_warp_cfg<T, F<T, D>, D, 2, 8>(a, s);
+        case 1: return launch_warp_cfg<T, F<T, D>, D, 2, 1, HOPF>(a, s);
+        case 2: return launch_warp_cfg<T, F<T, D>, D, 2, 2, HOPF>(a, s);
+        case 4: return launch_warp_cfg<T, F<T, D>, D, 2, 4, HOPF>(a, s);
+        case 8: return launch_warp_cfg<T, F<T, D>, D, 2, 8, HOPF>(a, s);
         default: return HJ_ERR_UNSUPPORTED;
       }
     }

@@ -6,8 +6,8 @@ namespace hj {
 template <typename T>
 hj_status launch_warp_tanh(const SolveArgs<T>& a, WarpConfig c, cudaStream_t s) {
   switch (a.d) {
-    case 2: return launch_warp_shape<T, FamTanhDrift, 2>(a, c, s);
-    case 4: return launch_warp_shape<T, FamTanhDrift, 4>(a, c, s);
+    case 2: return launch_warp_shape<T, FamTanhDrift, 2, false>(a, c, s);
+    case 4: return launch_warp_shape<T, FamTanhDrift, 4, false>(a, c, s);
     default: return HJ_ERR_UNSUPPORTED;
   }
 }
