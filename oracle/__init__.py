@@ -11,7 +11,9 @@ Contents
                initial guess (Section 6: x^0 within 0.1 of the target in the
                max-norm, p^0 within 0.1 of zero).
   families     the Hamiltonians H(x, p), their p-proximal maps, gradients and
-               the quadratic terminal cost g (Section 2, H = max_u{<f,p> - L}).
+               the quadratic terminal cost g (Section 2, H = max_u{<f,p> - L}),
+               including the eikonal family c(x)|p|_2 of Section 6.1 (shrink_2
+               dual step; the negative equation through phi = -psi).
   lax_pdhg     Algorithm 1 (Lax formula, backward Euler) with the concrete
                updates of Section 5.3 and the loop of Appendix Algorithm A.1,
                and the value fval of Eq. (disclaxBE).
@@ -19,7 +21,8 @@ Contents
                appendix's Hopf tutorial algorithm: the joint prox of g* and
                delta H at j = 1, x_0 eliminated through the conjugate of g.
 
-Pins: see tests/test_oracle_pins.py and tests/test_oracle_hopf_pins.py.  Closed form (quadratic H), discrete
+Pins: see tests/test_oracle_pins.py, tests/test_oracle_hopf_pins.py and
+tests/test_oracle_eikonal_pins.py.  Closed form (quadratic H), discrete
 Riccati (linear drift), direct collocation (tanh drift), the discrete
 characteristic (KKT) equations with complex-step derivatives of an H written
 independently from the quadcopter dynamics, the primal/dual value identity, and

@@ -171,11 +171,57 @@ class Quadcopter:
         return np.linalg.solve(M, rhs[..., None])[..., 0]
 
 
-class QuadCost:
-    """g(x) = 1/2 sum_i W_i^2 (x_i - c_i)^2 (terminal / initial cost)."""
+class Eikonal:
+    """H(x, p) = c(x) |p|_2 with the speed of Section 6.1,
+    c(x) = c0 + c1 exp(-c2 |x - x_b|^2) (a bump of height c1 at x_b on a floor c0).
 
-    def __init__(self, W, c):
-        self.w2 = np.asarray(W, dtype=np.float64) ** 2
+    The dual proximal map is the shrink_2 operator of Section 6.1:
+    argmin_p lam c(x) |p| + |p - v|^2 / 2 = v max(|v| - lam c(x), 0) / |v|.
+    grad_x H = |p| grad c(x); H is not differentiable in p at p = 0, and
+    grad_p H is only used away from it.
+    """
+
+    def __init__(self, c0, c1, c2, xb):
+        self.c0, self.c1, self.c2 = float(c0), float(c1), float(c2)
+        self.xb = np.asarray(xb, dtype=np.float64)
+        self.d = self.xb.shape[0]
+
+    def speed(self, x):
+        """c(x) and grad c(x)."""
+        y = x - self.xb
+        e = np.exp(-self.c2 * np.sum(y * y, axis=-1))
+        return self.c0 + self.c1 * e, (-2.0 * self.c1 * self.c2 * e)[..., None] * y
+
+    def H(self, x, p):
+        c, _ = self.speed(x)
+        return c * np.sqrt(np.sum(p * p, axis=-1))
+
+    def grad_p(self, x, p):
+        c, _ = self.speed(x)
+        n = np.sqrt(np.sum(p * p, axis=-1))
+        return np.where(n[..., None] > 0, c[..., None] * p / np.where(n > 0, n, 1.0)[..., None], 0.0)
+
+    def grad_x(self, x, p):
+        _, gc = self.speed(x)
+        return np.sqrt(np.sum(p * p, axis=-1))[..., None] * gc
+
+    def prox_p(self, x, v, lam):
+        c, _ = self.speed(x)
+        n = np.sqrt(np.sum(v * v, axis=-1))
+        keep = np.maximum(n - lam * c, 0.0) / np.where(n > 0, n, 1.0)
+        return keep[..., None] * v
+
+
+class QuadCost:
+    """g(x) = 1/2 sum_i W_i^2 (x_i - c_i)^2 (terminal / initial cost).
+
+    sign = -1 gives the concave -g: the eikonal family's negative equation is
+    solved as the positive one with initial data -g (Section 6.1), whose
+    proximal map ("stretch") needs 1 - tau W_i^2 > 0.
+    """
+
+    def __init__(self, W, c, sign=1.0):
+        self.w2 = float(sign) * np.asarray(W, dtype=np.float64) ** 2
         self.c = np.asarray(c, dtype=np.float64)
 
     def g(self, x):
@@ -198,4 +244,7 @@ def make_family(w, activation="tanh"):
         return TanhDrift(dyn.reshape(d, d), activation=activation)
     if fam == "quadcopter":
         return Quadcopter(*dyn[:4])
+    if fam == "eikonal":
+        # dyn = (s, c0, c1, c2, x_b): s = +1 the positive equation, -1 the negative
+        return Eikonal(dyn[1], dyn[2], dyn[3], dyn[4:4 + d])
     raise ValueError(fam)

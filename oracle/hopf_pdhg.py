@@ -81,6 +81,8 @@ def solve_hopf(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter
     Same arguments and result layout as lax_pdhg.solve; x[:, 0, :] holds
     grad g*(p_1) and p[:, 0, :] = 0.
     """
+    if w["family"] == "eikonal":
+        raise ValueError("the Hopf form here needs H quadratic in p (not the eikonal family)")
     fam = make_family(w, activation=activation)
     cost = QuadCost(w["W"], w["c"])
     if np.any(cost.w2 == 0.0):

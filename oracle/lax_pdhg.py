@@ -26,6 +26,11 @@ Readings of the paper taken here (each also listed in the design notes):
   * p_N is a free dual variable updated like the others; x_N is pinned.
 Initial guess (Section 6): x_j^0 = x_target + r u (j < N), p_j^0 = r u' (j >= 1), with
 u, u' in [-1, 1) from the counter-based generator in counter_rng.
+
+Negative eikonal equation (Section 6.1): phi_t - c(x)|grad phi| = 0 with initial
+data g is solved as -psi, psi the positive equation's solution with initial
+data -g (concave: its proximal map is the "stretch" of Section 6.1); the
+returned V and p are those of phi (V = -V_psi, p = -p_psi), x is shared.
 """
 import numpy as np
 
@@ -33,6 +38,13 @@ from .counter_rng import uniform_pm1
 from .families import QuadCost, make_family
 
 CONVERGED, MAX_ITER, NONFINITE = 0, 1, 2
+
+
+def eikonal_sign(w):
+    """-1 for the negative eikonal equation (dyn[0] = -1), else +1."""
+    if w["family"] == "eikonal" and float(np.asarray(w["dyn"])[0]) < 0:
+        return -1.0
+    return 1.0
 
 
 def initial_guess(xq, N, seed, radius, point_index):
@@ -65,7 +77,8 @@ def solve(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter=None
     rx [B], rp [B]) where rx, rp are the last squared increments.
     """
     fam = make_family(w, activation=activation)
-    cost = QuadCost(w["W"], w["c"])
+    sign = eikonal_sign(w)
+    cost = QuadCost(w["W"], w["c"], sign=sign)
     N = int(w["N"] if N is None else N)
     sigma = float(w["sigma"] if sigma is None else sigma)
     tau = float(w["tau"] if tau is None else tau)
@@ -135,7 +148,7 @@ def solve(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter=None
                 x, p, z, delta = x[keep], p[keep], z[keep], delta[keep]
                 lam = lam[keep]
     V = lax_value(fam, cost, x_all, p_all, delta_all)
-    return dict(V=V, iters=iters, status=status, x=x_all, p=p_all,
+    return dict(V=sign * V, iters=iters, status=status, x=x_all, p=sign * p_all,
                 rx=rx_all, rp=rp_all)
 
 
