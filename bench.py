@@ -212,6 +212,23 @@ def measure_other_configs(dev, flush, stream, peak):
         "fp32_over_fp64": (n_ok / ms) / (conv64 / ms64) if conv64 else None,
         "note": "trajectories written (the headline step writes V and status only)"}
 
+    # Section 6.1's dimensional scaling: the negative eikonal equation at t = 0.2
+    # (delta = 0.02, N = 10, sigma = 100) on the 2-D slice grid [-3, 3]^2 (mesh
+    # 0.1, 3721 points) embedded in d dimensions, FP32.  Algorithmic flops per
+    # (node, coordinate, iteration): 20 (the two node sums 8, dual step 4, x-step 6,
+    # relaxation 2); the paper's own fit of its single-core C++ time per point,
+    # 1.14e-4 d + 0.0021 s, is context only.
+    eik = {}
+    for d in (10, 100, 1000, 2000):
+        we = W.eikonal(d=d, sign=-1, t=0.2)
+        ms, conv, iters, _ = run_uniform(we, "fp32", f"timed_eikonal_d{d}")
+        flops = iters * 10 * d * 20
+        eik[f"d{d}"] = {"solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
+                        "points": len(we["xq"]), "mean_iters": iters / len(we["xq"]),
+                        "tflops": flops / (ms * 1e-3) / 1e12,
+                        "paper_cpu_fit_s_per_point": 1.14e-4 * d + 0.0021}
+    out["eikonal_negative_t0.2_slice3721_fp32"] = eik
+
     rw = W.ragged_mix()
     probs = [binding.Problem.from_workload(p) for p in rw["problems"]]
     ropts = binding.make_opts(sigma=rw["sigma"], tau=rw["tau"], tol=rw["tol"],

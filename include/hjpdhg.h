@@ -53,7 +53,16 @@ enum {
    * dyn (host, 4 doubles): m, a_h (hover thrust per unit mass), g_z, eps.  d = 12. */
   HJ_FAMILY_QUADCOPTER = 1,
   /* H = <p, tanh(A x)> + |p|^2/2.  dyn (host): A, d*d doubles, row-major.       */
-  HJ_FAMILY_TANH_DRIFT = 2
+  HJ_FAMILY_TANH_DRIFT = 2,
+  /* Eikonal equation of Section 6.1, phi_t + s c(x)|grad phi|_2 = 0: H = s c(x)|p|_2
+   * with the speed c(x) = c0 + c1 exp(-c2 |x - x_b|^2) (the paper's bump: c0 = 1,
+   * c1 = 3, c2 = 4, x_b = (1, 1, 0, ...)).  dyn (host, 4 + d doubles):
+   * s (+1 or -1), c0 > 0, c1 >= 0, c2 >= 0, x_b[d].  d = 1..4096.  The dual step
+   * is the shrink_2 operator.  s = -1 is solved as in Section 6.1: phi = -psi
+   * with psi the s = +1 solution for the initial data -g (concave; its x_0
+   * proximal map needs tau W_i^2 < 1, HJ_ERR_STEP_SIZE otherwise), and V and
+   * the returned p are those of phi.  Lax form only.                        */
+  HJ_FAMILY_EIKONAL = 3
 };
 
 /* Iterate precision.  FP32 iterates keep the increment reductions and the
@@ -78,9 +87,11 @@ enum { HJ_POINT_CONVERGED = 0, HJ_POINT_MAX_ITER = 1, HJ_POINT_NONFINITE = 2,
 
 typedef struct hj_problem_s* hj_problem;
 
-/* Create a problem: Hamiltonian family + terminal cost g(x) = 1/2 sum_i W_i^2 (x_i - c_i)^2.
+/* Create a problem: Hamiltonian family + terminal cost g(x) = 1/2 sum_i W_i^2 (x_i - c_i)^2
+ * (a constant added to g adds the same constant to V: the caller adds it).
  *   out      (host) receives the handle; set to NULL on error.
- *   family   HJ_FAMILY_*;  d state dimension (1..128; 12 for the quadcopter).
+ *   family   HJ_FAMILY_*;  d state dimension (1..128; 12 for the quadcopter;
+ *            1..4096 for the eikonal family).
  *   dyn      (host) n_dyn doubles, layout per family above (may be NULL if n_dyn = 0).
  *   W, c     (host) d doubles each.
  * Copies every parameter to device memory owned by the handle (allocates on the
@@ -172,7 +183,8 @@ hj_status hj_solve_batch(hj_problem prob, int64_t B,
  * the gradient of the value at the given iterates; it equals the derivative of
  * the converged value to the accuracy the iterates satisfy the saddle
  * conditions (Appendix A.1 stopping rule).
- * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_UNSUPPORTED (tanh drift with d > 128), HJ_ERR_CUDA. */
+ * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_UNSUPPORTED (tanh drift with d > 128; the
+ * eikonal family, whose H is not differentiable in p at 0), HJ_ERR_CUDA.     */
 hj_status hj_solve_grad(hj_problem prob, int64_t B, const double* t, int32_t N,
                         int32_t precision, const void* traj_x, const void* traj_p,
                         const double* dL_dV, double* dW, double* dc, double* ddyn, double* dxq,

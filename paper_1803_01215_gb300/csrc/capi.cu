@@ -1,6 +1,7 @@
 // C ABI of the solver: argument validation, problem handles, kernel dispatch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -37,7 +38,8 @@ hj_status hj_problem_create(hj_problem* out, int32_t family, int32_t d, const do
                             int64_t n_dyn, const double* W, const double* c) {
   if (out == nullptr) return HJ_ERR_INVALID_ARG;
   *out = nullptr;
-  if (d < 1 || d > hj::kMaxD || W == nullptr || c == nullptr || n_dyn < 0)
+  if (d < 1 || d > (family == HJ_FAMILY_EIKONAL ? hj::kMaxDEik : hj::kMaxD) || W == nullptr ||
+      c == nullptr || n_dyn < 0)
     return HJ_ERR_INVALID_ARG;
   if (n_dyn > 0 && dyn == nullptr) return HJ_ERR_INVALID_ARG;
   switch (family) {
@@ -51,6 +53,12 @@ hj_status hj_problem_create(hj_problem* out, int32_t family, int32_t d, const do
     case HJ_FAMILY_TANH_DRIFT:
       if (n_dyn != (int64_t)d * d) return HJ_ERR_INVALID_ARG;
       break;
+    case HJ_FAMILY_EIKONAL:
+      if (n_dyn != 4 + (int64_t)d) return HJ_ERR_INVALID_ARG;
+      if (!(dyn[0] == 1.0 || dyn[0] == -1.0) || !(dyn[1] > 0.0) || !(dyn[2] >= 0.0) ||
+          !(dyn[3] >= 0.0))
+        return HJ_ERR_INVALID_ARG;
+      break;
     default:
       return HJ_ERR_INVALID_ARG;
   }
@@ -61,8 +69,10 @@ hj_status hj_problem_create(hj_problem* out, int32_t family, int32_t d, const do
   if (p == nullptr) return HJ_ERR_OOM;
   p->family = family;
   p->d = d;
-  for (int i = 0; i < d; ++i)
+  for (int i = 0; i < d; ++i) {
     if (W[i] == 0.0) p->w_nonzero = false;
+    p->w2max = std::max(p->w2max, W[i] * W[i]);
+  }
   if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return HJ_ERR_CUDA; }
   std::vector<double> w2(d);
   for (int i = 0; i < d; ++i) w2[i] = W[i] * W[i];
@@ -71,6 +81,13 @@ hj_status hj_problem_create(hj_problem* out, int32_t family, int32_t d, const do
   if (r == HJ_OK) r = upload(&p->c, c, d);
   if (r == HJ_OK && family == HJ_FAMILY_QUADCOPTER) {
     for (int i = 0; i < 4; ++i) p->qc[i] = dyn[i];
+  }
+  if (r == HJ_OK && family == HJ_FAMILY_EIKONAL) {
+    for (int i = 0; i < 4; ++i) p->eik[i] = dyn[i];
+    std::vector<float> xf(d);
+    for (int i = 0; i < d; ++i) xf[i] = (float)dyn[4 + i];
+    r = upload(&p->xbd, dyn + 4, d);
+    if (r == HJ_OK) r = upload(&p->xbf, xf.data(), d);
   }
   if (r == HJ_OK && family == HJ_FAMILY_TANH_DRIFT) {
     const size_t n = (size_t)d * d;
@@ -115,7 +132,8 @@ hj_status hj_solve_batch(hj_problem prob, int64_t B, const double* xq, const dou
   const hj_solver_opts& o = *opts;
   const hj_status oc = check_opts(o);
   if (oc != HJ_OK) return oc;
-  if (check_formulation(prob, o) != HJ_OK) return HJ_ERR_INVALID_ARG;
+  const hj_status fc = check_formulation(prob, o);
+  if (fc != HJ_OK) return fc;
   if ((warm_x == nullptr) != (warm_p == nullptr)) return HJ_ERR_INVALID_ARG;
   if (o.point_offset + B > (int64_t(1) << 32)) return HJ_ERR_INVALID_ARG;
   if (B == 0) return HJ_OK;
@@ -139,6 +157,7 @@ hj_status hj_solve_grad(hj_problem prob, int64_t B, const double* t, int32_t N,
                         void* stream) {
   if (prob == nullptr || B < 0 || N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;
   if (precision != HJ_PREC_FP32 && precision != HJ_PREC_FP64) return HJ_ERR_INVALID_ARG;
+  if (prob->family == HJ_FAMILY_EIKONAL) return HJ_ERR_UNSUPPORTED;
   const int n_dyn = prob->family == HJ_FAMILY_QUADCOPTER ? 4
                     : prob->family == HJ_FAMILY_TANH_DRIFT ? prob->d * prob->d : 0;
   if (dW == nullptr || dc == nullptr || (n_dyn > 0 && ddyn == nullptr)) return HJ_ERR_INVALID_ARG;
@@ -265,7 +284,8 @@ hj_status hj_autotune(hj_problem prob, int64_t B, const double* xq, const double
   if (N < 1 || N > hj::kMaxN || repeats < 1) return HJ_ERR_INVALID_ARG;
   const hj_status oc = check_opts(*opts);
   if (oc != HJ_OK) return oc;
-  if (check_formulation(prob, *opts) != HJ_OK) return HJ_ERR_INVALID_ARG;
+  const hj_status fc = check_formulation(prob, *opts);
+  if (fc != HJ_OK) return fc;
   const bool f64 = opts->precision == HJ_PREC_FP64;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   double* V = nullptr;

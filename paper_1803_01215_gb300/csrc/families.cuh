@@ -113,6 +113,17 @@ __device__ __forceinline__ T tanh_t(T y) { return tanh(y); }
 template <>
 __device__ __forceinline__ float tanh_t<float>(float y) { return tanhf(y); }
 
+template <typename T>
+__device__ __forceinline__ T exp_t(T y) { return exp(y); }
+template <>
+__device__ __forceinline__ float exp_t<float>(float y) { return __expf(y); }
+
+template <typename T>
+__device__ __forceinline__ T sqrt_t(T y) { return sqrt(y); }
+template <>
+__device__ __forceinline__ float sqrt_t<float>(float y) { return sqrtf(y); }
+
+
 // ---------------------------------------------------------------- H = |p|^2/2
 template <typename T, int D>
 struct FamQuadratic {
@@ -396,6 +407,74 @@ struct FamTanhDrift {
       h += p[i] * tanh_t<T>(y) + T(0.5) * p[i] * p[i];
     }
     return h;
+  }
+};
+
+// ---------------------------------------------------------------- eikonal, small D
+// H = c(x) |p|_2 with c(x) = c0 + c1 exp(-c2 |x - x_b|^2) (Section 6.1).  The
+// dual step is the shrink_2 operator, p = v max(|v| - lam c, 0) / |v|, and
+// grad_x H = |p| grad c(x) = |p| (-2 c1 c2 e) (x - x_b), e = exp(-c2 |x - x_b|^2).
+template <typename T, int D>
+struct FamEikonal {
+  static constexpr bool kHasGradX = true;
+  struct Shared { T xb[D]; };
+  struct Ctx { T c, gf; };                 // c(x) and -2 c1 c2 e at x^k
+  struct PC { T lam; };
+  const T* xb;
+  const double* xb64;
+  T c0, c1, c2;
+  double c0d, c1d, c2d;
+  __device__ static void load_shared(const SolveArgs<T>& s, Shared& sh) {
+    for (int i = threadIdx.x; i < D; i += blockDim.x) sh.xb[i] = s.xb[i];
+  }
+  __device__ FamEikonal(const SolveArgs<T>& s, const Shared& sh)
+      : xb(sh.xb), xb64(s.xb64), c0(T(s.eik_c0)), c1(T(s.eik_c1)), c2(T(s.eik_c2)),
+        c0d(s.eik_c0), c1d(s.eik_c1), c2d(s.eik_c2) {}
+  __device__ __forceinline__ PC point(T lam) const { return PC{lam}; }
+  __device__ __forceinline__ void context(const T (&x)[D], Ctx& c) const {
+    T r2 = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) { const T y = x[k] - xb[k]; r2 += y * y; }
+    const T e = exp_t<T>(-c2 * r2);
+    c.c = c0 + c1 * e;
+    c.gf = T(-2) * c1 * c2 * e;
+  }
+  __device__ __forceinline__ void prox(const Ctx& c, const PC& pc, const T (&)[D],
+                                       T (&v)[D]) const {
+    T n2 = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) n2 += v[k] * v[k];
+    const T n = sqrt_t<T>(n2), th = pc.lam * c.c;
+    const T keep = (n > th) ? fdiv<T>(n - th, n) : T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] *= keep;
+  }
+  __device__ __forceinline__ void gradx(const Ctx& c, const T (&x)[D], const T (&p)[D],
+                                        T (&g)[D]) const {
+    T n2 = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) n2 += p[k] * p[k];
+    const T s = sqrt_t<T>(n2) * c.gf;
+#pragma unroll
+    for (int k = 0; k < D; ++k) g[k] = s * (x[k] - xb[k]);
+  }
+  __device__ __forceinline__ double H64(const T (&x)[D], const T (&p)[D]) const {
+    double r2 = 0.0, n2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double y = (double)x[k] - xb64[k];
+      r2 += y * y;
+      n2 += (double)p[k] * (double)p[k];
+    }
+    return (c0d + c1d * exp(-c2d * r2)) * sqrt(n2);
+  }
+  __device__ __forceinline__ T Ht(const T (&x)[D], const T (&p)[D]) const {
+    Ctx c;
+    context(x, c);
+    T n2 = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) n2 += p[k] * p[k];
+    return c.c * sqrt_t<T>(n2);
   }
 };
 

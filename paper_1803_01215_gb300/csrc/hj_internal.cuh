@@ -8,7 +8,8 @@
 namespace hj {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxD = 128;   // largest state dimension any kernel accepts
+constexpr int kMaxD = 128;   // largest state dimension of the families with d x d data
+constexpr int kMaxDEik = 4096;   // largest state dimension of the eikonal family
 constexpr int kMaxN = 256;   // largest number of time steps
 
 // Everything a solve kernel needs, passed by value.  Scalars that enter the
@@ -45,6 +46,13 @@ struct SolveArgs {
   const T* At;           // tanh drift: transpose of A in T
   const double* A64;     // tanh drift: [d][d] row-major in double (value epilogue)
   double qc_m, qc_ah, qc_gz, qc_eps;   // quadcopter parameters
+  double eik_c0, eik_c1, eik_c2;       // eikonal speed c(x) = c0 + c1 exp(-c2 |x - x_b|^2)
+  const double* xb64;                  // [d] eikonal bump centre x_b
+  const T* xb;                         // [d] the same in T
+  // +1, or -1 for the negative eikonal equation: the kernels solve the positive
+  // one with the initial data -g (x_0 prox and value with -W^2) and return
+  // V and p multiplied by cost_sign
+  double cost_sign;
   unsigned long long* counter;        // work counter (zeroed before launch)
   // Ragged batches: the launch processes items i = 0..B-1, point id idx[i]
   // (idx null: id = i).  Per-point N (Nv null: N), xq offset in doubles
@@ -211,11 +219,20 @@ template <typename T>
 hj_status launch_warp_quadcopter_hopf(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 template <typename T>
 hj_status launch_warp_tanh_hopf(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
+template <typename T>
+hj_status launch_warp_eikonal(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 // Default launch shape for (family, d, Nmax); {0, 0} when no warp kernel fits.
 WarpConfig default_warp_config(int family, int d, int Nmax, bool fp64);
 // Whether the warp kernel has an instantiation for (family, d, cfg, precision).
 bool warp_config_available(int family, int d, WarpConfig cfg, bool fp64);
 // Shared-memory CTA kernel: tanh drift (drift = true) or H = |p|^2/2 (drift = false).
+// Coordinate-parallel eikonal kernel (any d): one CTA per point, state in shared
+// memory when eik_cta_smem_bytes(d, N) != 0, else in a stream-ordered workspace.
+template <typename T>
+hj_status launch_eik_cta_solver(const SolveArgs<T>& a, cudaStream_t s);
+template <typename T>
+size_t eik_cta_smem_bytes(int d, int N);
+
 // Register-tiled FP32 tanh-drift kernel; HJ_ERR_UNSUPPORTED where it does not
 // apply (the shared-memory kernel then runs).  td_tile_group_warps: warps per
 // point for (d, N), 0 when the tiled kernel cannot hold the point.

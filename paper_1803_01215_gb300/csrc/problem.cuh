@@ -14,6 +14,10 @@ struct hj_problem_s {
   int family = 0, d = 0, device = 0;
   double qc[4] = {0, 0, 0, 0};        // m, a_h, g_z, eps
   bool w_nonzero = true;              // every W_i != 0 (g* finite: the Hopf form)
+  double w2max = 0.0;                 // max_i W_i^2 (the concave x_0 prox needs tau w2max < 1)
+  double eik[4] = {1, 0, 0, 0};       // eikonal: s, c0, c1, c2
+  double* xbd = nullptr;              // [d] eikonal bump centre
+  float* xbf = nullptr;
   double* W2 = nullptr;               // [d]  W_i^2
   double* W = nullptr;                // [d]  W_i as given (sign kept for dV/dW)
   double* c = nullptr;                // [d]
@@ -47,6 +51,7 @@ hj_status upload(T** dst, const T* src, size_t n) {
 inline void release(hj_problem_s* p) {
   cudaFree(p->W2); cudaFree(p->W); cudaFree(p->c);
   cudaFree(p->Af); cudaFree(p->Atf); cudaFree(p->Ad); cudaFree(p->Atd);
+  cudaFree(p->xbd); cudaFree(p->xbf);
   cudaFree(p->counter);
   delete p;
 }
@@ -71,6 +76,7 @@ hj_status dispatch(hj_problem_s* p, const hj::SolveArgs<T>& a, hj::WarpConfig cf
     if (r != HJ_ERR_UNSUPPORTED) return r;
   }
   if (p->family == HJ_FAMILY_TANH_DRIFT) return hj::launch_td_cta_solver<T>(a, true, s);
+  if (p->family == HJ_FAMILY_EIKONAL) return hj::launch_eik_cta_solver<T>(a, s);
   if (p->family == HJ_FAMILY_QUADRATIC) return hj::launch_td_cta_solver<T>(a, false, s);
   return HJ_ERR_UNSUPPORTED;
 }
@@ -86,7 +92,7 @@ inline void fill_args<float>(hj::SolveArgs<float>& a, const hj_problem_s* prob, 
                       const hj_solver_opts& o, const double* xq, const double* t, double* V,
                       int32_t* iters, int8_t* status, void* traj_x, void* traj_p,
                       const void* warm_x, const void* warm_p) {
-  a.A = prob->Af; a.At = prob->Atf;
+  a.A = prob->Af; a.At = prob->Atf; a.xb = prob->xbf;
   a.traj_x = static_cast<float*>(traj_x); a.traj_p = static_cast<float*>(traj_p);
   a.warm_x = static_cast<const float*>(warm_x); a.warm_p = static_cast<const float*>(warm_p);
   (void)B; (void)N; (void)o; (void)xq; (void)t; (void)V; (void)iters; (void)status;
@@ -97,7 +103,7 @@ inline void fill_args<double>(hj::SolveArgs<double>& a, const hj_problem_s* prob
                        const hj_solver_opts& o, const double* xq, const double* t, double* V,
                        int32_t* iters, int8_t* status, void* traj_x, void* traj_p,
                        const void* warm_x, const void* warm_p) {
-  a.A = prob->Ad; a.At = prob->Atd;
+  a.A = prob->Ad; a.At = prob->Atd; a.xb = prob->xbd;
   a.traj_x = static_cast<double*>(traj_x); a.traj_p = static_cast<double*>(traj_p);
   a.warm_x = static_cast<const double*>(warm_x); a.warm_p = static_cast<const double*>(warm_p);
   (void)B; (void)N; (void)o; (void)xq; (void)t; (void)V; (void)iters; (void)status;
@@ -120,6 +126,9 @@ hj::SolveArgs<T> make_args(const hj_problem_s* prob, int64_t B, int32_t N,
   a.xq = xq; a.t = t; a.V = V; a.iters = iters; a.status = status;
   a.W2 = prob->W2; a.c = prob->c; a.A64 = prob->Ad;
   a.qc_m = prob->qc[0]; a.qc_ah = prob->qc[1]; a.qc_gz = prob->qc[2]; a.qc_eps = prob->qc[3];
+  a.eik_c0 = prob->eik[1]; a.eik_c1 = prob->eik[2]; a.eik_c2 = prob->eik[3];
+  a.xb64 = prob->xbd;
+  a.cost_sign = (prob->family == HJ_FAMILY_EIKONAL && prob->eik[0] < 0) ? -1.0 : 1.0;
   a.counter = prob->counter;
   fill_args<T>(a, prob, B, N, o, xq, t, V, iters, status, traj_x, traj_p, warm_x, warm_p);
   return a;
@@ -139,9 +148,15 @@ inline hj_status check_opts(const hj_solver_opts& o) {
   return HJ_OK;
 }
 
-// The Hopf form needs g* finite: every W_i nonzero.
+// The Hopf form needs g* finite: every W_i nonzero; the eikonal family is
+// solved in the Lax form only, and its negative equation's concave x_0 prox
+// needs tau W_i^2 < 1.
 inline hj_status check_formulation(const hj_problem_s* p, const hj_solver_opts& o) {
-  return (o.formulation == HJ_FORM_HOPF && !p->w_nonzero) ? HJ_ERR_INVALID_ARG : HJ_OK;
+  if (o.formulation == HJ_FORM_HOPF && p->family == HJ_FAMILY_EIKONAL) return HJ_ERR_UNSUPPORTED;
+  if (o.formulation == HJ_FORM_HOPF && !p->w_nonzero) return HJ_ERR_INVALID_ARG;
+  if (p->family == HJ_FAMILY_EIKONAL && p->eik[0] < 0 && !(o.tau * p->w2max < 1.0))
+    return HJ_ERR_STEP_SIZE;
+  return HJ_OK;
 }
 
 template <typename T>

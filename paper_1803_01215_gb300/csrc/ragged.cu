@@ -125,7 +125,8 @@ hj_status hj_ragged_plan_create(hj_ragged_plan* out, int32_t n_prob, const hj_pr
   if (cudaGetDevice(&dev) != cudaSuccess) return HJ_ERR_CUDA;
   for (int i = 0; i < n_prob; ++i) {
     if (probs[i] == nullptr || probs[i]->device != dev) return HJ_ERR_INVALID_ARG;
-    if (check_formulation(probs[i], *opts) != HJ_OK) return HJ_ERR_INVALID_ARG;
+    const hj_status fc = check_formulation(probs[i], *opts);
+    if (fc != HJ_OK) return fc;
   }
   for (int64_t b = 0; b < B; ++b) {
     if (prob_of[b] < 0 || prob_of[b] >= n_prob) return HJ_ERR_INVALID_ARG;
@@ -177,7 +178,12 @@ hj_status hj_ragged_plan_create(hj_ragged_plan* out, int32_t n_prob, const hj_pr
       // shared-memory kernel: the bucket's largest N must fit its shared memory
       const bool drift = pr->family == HJ_FAMILY_TANH_DRIFT;
       if (pr->family == HJ_FAMILY_QUADCOPTER) r = HJ_ERR_UNSUPPORTED;
-      else if ((f64 ? hj::td_cta_smem_bytes<double>(pr->d, k.nmax, drift)
+      else if (pr->family == HJ_FAMILY_EIKONAL) {
+        // the captured graph holds no workspace: the state must fit shared memory
+        if ((f64 ? hj::eik_cta_smem_bytes<double>(pr->d, k.nmax)
+                 : hj::eik_cta_smem_bytes<float>(pr->d, k.nmax)) == 0)
+          r = HJ_ERR_UNSUPPORTED;
+      } else if ((f64 ? hj::td_cta_smem_bytes<double>(pr->d, k.nmax, drift)
                     : hj::td_cta_smem_bytes<float>(pr->d, k.nmax, drift)) == 0)
         r = HJ_ERR_UNSUPPORTED;
     }

@@ -199,10 +199,12 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         if (i == 0) v_sub<T, D>(dz, z[i], zl);
         else v_sub<T, D>(dz, z[i], z[i > 0 ? i - 1 : 0]);
         v_fma<T, D>(v, sig, dz, p[i]);                       // p + sigma (z_j - z_{j-1})
-        if (HOPF && i == 0 && gl == 0)                       // Hopf: node 1 also carries g*
-          fam.prox_first(ctx[i], pc, x[i], v, sh.hs, sh.hc);
-        else
+        if constexpr (HOPF) {                                // Hopf: node 1 also carries g*
+          if (i == 0 && gl == 0) fam.prox_first(ctx[i], pc, x[i], v, sh.hs, sh.hc);
+          else fam.prox(ctx[i], pc, x[i], v);
+        } else {
           fam.prox(ctx[i], pc, x[i], v);
+        }
         if constexpr (CHK) {
           T e[D];
           v_sub<T, D>(e, v, p[i]);
@@ -345,7 +347,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     for (int w = 0; w < G; ++w) acc += sh.vred[w];
   }
   if (gl == 0) {
-    a.V[pt.id] = acc;
+    a.V[pt.id] = a.cost_sign * acc;
     a.iters[pt.id] = k_it;
     a.status[pt.id] = st;
   }
@@ -364,7 +366,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     for (int i = 0; i < NPL; ++i)
       if (jbase + i <= N)
 #pragma unroll
-        for (int k = 0; k < D; ++k) o[(size_t)(jbase + i) * D + k] = p[i][k];
+        for (int k = 0; k < D; ++k) o[(size_t)(jbase + i) * D + k] = T(a.cost_sign) * p[i][k];
     if (own0) o[k0] = T(0);
   }
 }
@@ -375,7 +377,8 @@ lax_warp_kernel(const SolveArgs<T> a) {
   __shared__ WarpShared<T, F, D, G> sh;
   F::load_shared(a, sh.fam);
   for (int k = threadIdx.x; k < WarpShared<T, F, D, G>::DP; k += blockDim.x) {
-    const double w2 = k < D ? a.W2[k] : 0.0, c = k < D ? a.c[k] : 0.0;
+    // cost_sign = -1 (negative eikonal): the positive equation with initial data -g
+    const double w2 = k < D ? a.cost_sign * a.W2[k] : 0.0, c = k < D ? a.c[k] : 0.0;
     if (k < D) { sh.w2d[k] = w2; sh.cd[k] = c; }
     sh.g_off[k] = T(a.tau * w2 * c);
     sh.g_inv[k] = T(1.0 / (1.0 + a.tau * w2));

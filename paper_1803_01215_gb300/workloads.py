@@ -25,7 +25,7 @@ Every workload is a plain dict:
 """
 import numpy as np
 
-FAMILIES = {"quadratic": 0, "quadcopter": 1, "tanh_drift": 2}
+FAMILIES = {"quadratic": 0, "quadcopter": 1, "tanh_drift": 2, "eikonal": 3}
 
 # Quadcopter constants: unit mass, hover thrust gain equal to gravity so that
 # the level-attitude state is an equilibrium of the drift.
@@ -83,6 +83,40 @@ def tanh_drift(d, B=16384, seed=3, N=32):
 # point does not depend on them, only the iteration count does.
 QC_SIGMA = 1.4
 TD_SIGMA = 1.0
+
+
+EIK_DELTA = 0.02            # time step of Section 6.1's eikonal runs
+EIK_G_CONST = -0.5          # g(x) = -1/2 + 1/2 <A^-1 x, x>: the constant shifts V
+
+
+def eikonal(d=2, sign=1, t=0.2, B=None, grid_step=0.1, seed=8):
+    """Section 6.1's eikonal problems: phi_t + sign c(x)|grad phi| = 0 with
+    c(x) = 1 + 3 exp(-4 |x - (1, 1, 0, ..., 0)|^2) and
+    g(x) = -1/2 + 1/2 <A^-1 x, x>, A = diag(2.5^2, 1, 0.5^2, ..., 0.5^2)
+    (W = (1/2.5, 1, 2, ..., 2), c = 0; the constant -1/2 is EIK_G_CONST, added
+    to V by the caller).  Query points on the 2-D slice [-3, 3]^2 x {0}^(d-2):
+    the grid of mesh grid_step (B None) or B uniform draws.  delta = 0.02
+    (N = t / 0.02); sigma = 0.5 for sign +1 (the paper's choice away from the
+    bump) and 100 for sign -1, tau = 0.24 / sigma."""
+    r = _rng(seed)
+    if B is None:
+        ax = np.arange(-3.0, 3.0 + 1e-9, grid_step)
+        a, b = np.meshgrid(ax, ax, indexing="ij")
+        pts = np.stack([a.ravel(), b.ravel()], axis=1)
+    else:
+        pts = r.uniform(-3.0, 3.0, size=(B, 2))
+    xq = np.zeros((len(pts), d))
+    xq[:, :2] = pts
+    W = np.full(d, 2.0)
+    W[0], W[1] = 1.0 / 2.5, 1.0
+    xb = np.zeros(d)
+    xb[:2] = 1.0
+    N = int(round(t / EIK_DELTA))
+    sigma = 0.5 if sign > 0 else 100.0
+    return dict(family="eikonal", d=d, dyn=np.concatenate([[float(sign), 1.0, 3.0, 4.0], xb]),
+                W=W, c=np.zeros(d), xq=xq, t=np.full(len(pts), float(t)), N=N,
+                sigma=sigma, tau=0.24 / sigma, tol=1e-8, max_iter=20000, check_every=16,
+                seed=seed, init_radius=0.1, g_const=EIK_G_CONST)
 
 
 def subset(w, idx):
