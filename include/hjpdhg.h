@@ -62,7 +62,19 @@ enum {
    * with psi the s = +1 solution for the initial data -g (concave; its x_0
    * proximal map needs tau W_i^2 < 1, HJ_ERR_STEP_SIZE otherwise), and V and
    * the returned p are those of phi.  Lax form only.                        */
-  HJ_FAMILY_EIKONAL = 3
+  HJ_FAMILY_EIKONAL = 3,
+  /* Difference-of-norms differential game of Section 6.2 (Algorithm 3):
+   * state z = (x, y), x = z[0..d1) the minimising player, y = z[d1..d) the
+   * maximising one, costates (p, q) stored in that order; H(z, p, q) =
+   * c1(z)|p|_2 - c2(z)|q|_2 with c1(z) = c0 + a exp(-b |z - z_b|^2) and its mirror
+   * c2(z) = c1(-z).  dyn (host, 4 + d doubles): d1 (integer, 1..d-1), c0 > 0,
+   * a >= 0, b >= 0, z_b[d].  d = 2 or 7 (the paper's cases; other d are
+   * HJ_ERR_UNSUPPORTED at solve time).  V = g(z_0) + sum <p_j, dx_j>
+   * - sum <q_j, dy_j> - delta sum H; g is convex in both players, so the
+   * maximiser's y_0 step is the ascent prox of g (needs tau W_i^2 < 1 on the
+   * maximiser's coordinates, HJ_ERR_STEP_SIZE otherwise).  Lax form, one
+   * gradient step per primal block (inner_steps = 1), no gradient entry point. */
+  HJ_FAMILY_GAME_NORMS = 4
 };
 
 /* Iterate precision.  FP32 iterates keep the increment reductions and the

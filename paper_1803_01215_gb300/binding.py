@@ -173,7 +173,7 @@ def _ptr(t):
 
 
 def n_dyn(problem):
-    return {0: 0, 1: 4, 2: problem.d * problem.d, 3: 4 + problem.d}[problem.family]
+    return {0: 0, 1: 4, 2: problem.d * problem.d, 3: 4 + problem.d, 4: 4 + problem.d}[problem.family]
 
 
 def solve_grad(problem, t, N, precision, traj_x, traj_p, dL_dV, want_dxq=True, stream=None):

@@ -53,6 +53,12 @@ hj_status hj_problem_create(hj_problem* out, int32_t family, int32_t d, const do
     case HJ_FAMILY_TANH_DRIFT:
       if (n_dyn != (int64_t)d * d) return HJ_ERR_INVALID_ARG;
       break;
+    case HJ_FAMILY_GAME_NORMS:
+      if (n_dyn != 4 + (int64_t)d || d < 2) return HJ_ERR_INVALID_ARG;
+      if (!(dyn[0] >= 1.0 && dyn[0] <= d - 1.0 && dyn[0] == (double)(int)dyn[0]) ||
+          !(dyn[1] > 0.0) || !(dyn[2] >= 0.0) || !(dyn[3] >= 0.0))
+        return HJ_ERR_INVALID_ARG;
+      break;
     case HJ_FAMILY_EIKONAL:
       if (n_dyn != 4 + (int64_t)d) return HJ_ERR_INVALID_ARG;
       if (!(dyn[0] == 1.0 || dyn[0] == -1.0) || !(dyn[1] > 0.0) || !(dyn[2] >= 0.0) ||
@@ -82,7 +88,9 @@ hj_status hj_problem_create(hj_problem* out, int32_t family, int32_t d, const do
   if (r == HJ_OK && family == HJ_FAMILY_QUADCOPTER) {
     for (int i = 0; i < 4; ++i) p->qc[i] = dyn[i];
   }
-  if (r == HJ_OK && family == HJ_FAMILY_EIKONAL) {
+  if (family == HJ_FAMILY_GAME_NORMS)
+    for (int i = (int)dyn[0]; i < d; ++i) p->w2max_max = std::max(p->w2max_max, W[i] * W[i]);
+  if (r == HJ_OK && (family == HJ_FAMILY_EIKONAL || family == HJ_FAMILY_GAME_NORMS)) {
     for (int i = 0; i < 4; ++i) p->eik[i] = dyn[i];
     std::vector<float> xf(d);
     for (int i = 0; i < d; ++i) xf[i] = (float)dyn[4 + i];
@@ -157,7 +165,8 @@ hj_status hj_solve_grad(hj_problem prob, int64_t B, const double* t, int32_t N,
                         void* stream) {
   if (prob == nullptr || B < 0 || N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;
   if (precision != HJ_PREC_FP32 && precision != HJ_PREC_FP64) return HJ_ERR_INVALID_ARG;
-  if (prob->family == HJ_FAMILY_EIKONAL) return HJ_ERR_UNSUPPORTED;
+  if (prob->family == HJ_FAMILY_EIKONAL || prob->family == HJ_FAMILY_GAME_NORMS)
+    return HJ_ERR_UNSUPPORTED;
   const int n_dyn = prob->family == HJ_FAMILY_QUADCOPTER ? 4
                     : prob->family == HJ_FAMILY_TANH_DRIFT ? prob->d * prob->d : 0;
   if (dW == nullptr || dc == nullptr || (n_dyn > 0 && ddyn == nullptr)) return HJ_ERR_INVALID_ARG;

@@ -128,6 +128,7 @@ __device__ __forceinline__ float sqrt_t<float>(float y) { return sqrtf(y); }
 template <typename T, int D>
 struct FamQuadratic {
   static constexpr bool kHasGradX = false;
+  static constexpr bool kGame = false;
   struct Shared {};
   struct Ctx {};
   struct PC { T s, lam; };
@@ -173,6 +174,7 @@ template <typename T, int D>
 struct FamQuadcopter {
   static_assert(D == 12, "quadcopter state is 12-D");
   static constexpr bool kHasGradX = true;
+  static constexpr bool kGame = false;
   struct Shared {};
   struct Ctx { T a[3]; T J[9]; };
   T m_inv, ah, gz, eps;
@@ -340,6 +342,7 @@ struct FamQuadcopter {
 template <typename T, int D>
 struct FamTanhDrift {
   static constexpr bool kHasGradX = true;
+  static constexpr bool kGame = false;
   struct Shared { T A[D * D]; };
   struct Ctx { T a[D]; };
   const T* A;
@@ -417,6 +420,7 @@ struct FamTanhDrift {
 template <typename T, int D>
 struct FamEikonal {
   static constexpr bool kHasGradX = true;
+  static constexpr bool kGame = false;
   struct Shared { T xb[D]; };
   struct Ctx { T c, gf; };                 // c(x) and -2 c1 c2 e at x^k
   struct PC { T lam; };
@@ -475,6 +479,112 @@ struct FamEikonal {
 #pragma unroll
     for (int k = 0; k < D; ++k) n2 += p[k] * p[k];
     return c.c * sqrt_t<T>(n2);
+  }
+};
+
+// ---------------------------------------------------------------- difference-of-norms game
+// Section 6.2's differential game: state z = (x, y), x = z[0..d1) (the
+// minimising player), y = z[d1..D) (the maximising one); the costate array holds
+// (p, q).  H(z, p, q) = c1(z)|p| - c2(z)|q| with c1(z) = c0 + a exp(-b |z - z_b|^2)
+// and its mirror c2(z) = c1(-z).  Both dual steps are shrink_2 (thresholds
+// lam c1 and lam c2); the primal step is game_step: a descent step for x at z^k,
+// then an ascent step for y at (x^{k+1}, y^k) (Algorithm 3's order).
+template <typename T, int D>
+struct FamGame {
+  static constexpr bool kHasGradX = true;
+  static constexpr bool kGame = true;
+  struct Shared { T zb[D]; };
+  struct Ctx { T c1, c2, g1, g2; };        // speeds and gradient factors -2 a b e at z^k
+  struct PC { T lam; };
+  const T* zb;
+  const double* zb64;
+  int d1;
+  T c0, am, bw;
+  double c0d, amd, bwd;
+  __device__ static void load_shared(const SolveArgs<T>& s, Shared& sh) {
+    for (int i = threadIdx.x; i < D; i += blockDim.x) sh.zb[i] = s.xb[i];
+  }
+  __device__ FamGame(const SolveArgs<T>& s, const Shared& sh)
+      : zb(sh.zb), zb64(s.xb64), d1(s.game_d1), c0(T(s.eik_c0)), am(T(s.eik_c1)),
+        bw(T(s.eik_c2)), c0d(s.eik_c0), amd(s.eik_c1), bwd(s.eik_c2) {}
+  __device__ __forceinline__ PC point(T lam) const { return PC{lam}; }
+  __device__ __forceinline__ void context(const T (&z)[D], Ctx& c) const {
+    T r1 = T(0), r2 = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const T u = z[k] - zb[k], w = z[k] + zb[k];
+      r1 += u * u;
+      r2 += w * w;
+    }
+    const T e1 = exp_t<T>(-bw * r1), e2 = exp_t<T>(-bw * r2);
+    c.c1 = c0 + am * e1;
+    c.c2 = c0 + am * e2;
+    c.g1 = T(-2) * am * bw * e1;
+    c.g2 = T(-2) * am * bw * e2;
+  }
+  __device__ __forceinline__ void norms(const T (&P)[D], T& np, T& nq) const {
+    T sp = T(0), sq = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      if (k < d1) sp += P[k] * P[k];
+      else sq += P[k] * P[k];
+    }
+    np = sqrt_t<T>(sp);
+    nq = sqrt_t<T>(sq);
+  }
+  __device__ __forceinline__ void prox(const Ctx& c, const PC& pc, const T (&)[D],
+                                       T (&v)[D]) const {
+    T np, nq;
+    norms(v, np, nq);
+    const T tp = pc.lam * c.c1, tq = pc.lam * c.c2;
+    const T kp = (np > tp) ? fdiv<T>(np - tp, np) : T(0);
+    const T kq = (nq > tq) ? fdiv<T>(nq - tq, nq) : T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] *= (k < d1) ? kp : kq;
+  }
+  // xn holds z - tau (P - P_next) on entry
+  __device__ __forceinline__ void game_step(const Ctx& c, const T (&z)[D], const T (&P)[D],
+                                            T taud, T (&xn)[D]) const {
+    T np, nq;
+    norms(P, np, nq);
+    const T f1 = np * c.g1, f2 = nq * c.g2;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k < d1) xn[k] += taud * (f1 * (z[k] - zb[k]) - f2 * (z[k] + zb[k]));
+    T zm[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) zm[k] = (k < d1) ? xn[k] : z[k];
+    Ctx cm;
+    context(zm, cm);
+    const T h1 = np * cm.g1, h2 = nq * cm.g2;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k >= d1) xn[k] -= taud * (h1 * (zm[k] - zb[k]) - h2 * (zm[k] + zb[k]));
+  }
+  __device__ __forceinline__ void gradx(const Ctx&, const T (&)[D], const T (&)[D],
+                                        T (&g)[D]) const {
+#pragma unroll
+    for (int k = 0; k < D; ++k) g[k] = T(0);      // the primal step is game_step
+  }
+  __device__ __forceinline__ double H64(const T (&z)[D], const T (&P)[D]) const {
+    double r1 = 0.0, r2 = 0.0, sp = 0.0, sq = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double u = (double)z[k] - zb64[k], w = (double)z[k] + zb64[k];
+      r1 += u * u;
+      r2 += w * w;
+      const double pk = (double)P[k];
+      if (k < d1) sp += pk * pk;
+      else sq += pk * pk;
+    }
+    return (c0d + amd * exp(-bwd * r1)) * sqrt(sp) - (c0d + amd * exp(-bwd * r2)) * sqrt(sq);
+  }
+  __device__ __forceinline__ T Ht(const T (&z)[D], const T (&P)[D]) const {
+    Ctx c;
+    context(z, c);
+    T np, nq;
+    norms(P, np, nq);
+    return c.c1 * np - c.c2 * nq;
   }
 };
 

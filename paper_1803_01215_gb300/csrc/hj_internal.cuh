@@ -53,6 +53,8 @@ struct SolveArgs {
   // one with the initial data -g (x_0 prox and value with -W^2) and return
   // V and p multiplied by cost_sign
   double cost_sign;
+  int32_t game_d1;                     // difference-of-norms game: coordinates of the
+                                       // minimising player (d for every other family)
   unsigned long long* counter;        // work counter (zeroed before launch)
   // Ragged batches: the launch processes items i = 0..B-1, point id idx[i]
   // (idx null: id = i).  Per-point N (Nv null: N), xq offset in doubles
@@ -221,6 +223,8 @@ template <typename T>
 hj_status launch_warp_tanh_hopf(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 template <typename T>
 hj_status launch_warp_eikonal(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
+template <typename T>
+hj_status launch_warp_game(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 // Default launch shape for (family, d, Nmax); {0, 0} when no warp kernel fits.
 WarpConfig default_warp_config(int family, int d, int Nmax, bool fp64);
 // Whether the warp kernel has an instantiation for (family, d, cfg, precision).

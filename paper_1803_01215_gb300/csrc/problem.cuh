@@ -15,7 +15,8 @@ struct hj_problem_s {
   double qc[4] = {0, 0, 0, 0};        // m, a_h, g_z, eps
   bool w_nonzero = true;              // every W_i != 0 (g* finite: the Hopf form)
   double w2max = 0.0;                 // max_i W_i^2 (the concave x_0 prox needs tau w2max < 1)
-  double eik[4] = {1, 0, 0, 0};       // eikonal: s, c0, c1, c2
+  double eik[4] = {1, 0, 0, 0};       // eikonal: s, c0, c1, c2; game: d1, c0, a, b
+  double w2max_max = 0.0;             // game: max W_i^2 over the maximiser's coordinates
   double* xbd = nullptr;              // [d] eikonal bump centre
   float* xbf = nullptr;
   double* W2 = nullptr;               // [d]  W_i^2
@@ -77,6 +78,7 @@ hj_status dispatch(hj_problem_s* p, const hj::SolveArgs<T>& a, hj::WarpConfig cf
   }
   if (p->family == HJ_FAMILY_TANH_DRIFT) return hj::launch_td_cta_solver<T>(a, true, s);
   if (p->family == HJ_FAMILY_EIKONAL) return hj::launch_eik_cta_solver<T>(a, s);
+  if (p->family == HJ_FAMILY_GAME_NORMS) return HJ_ERR_UNSUPPORTED;   // register kernel only
   if (p->family == HJ_FAMILY_QUADRATIC) return hj::launch_td_cta_solver<T>(a, false, s);
   return HJ_ERR_UNSUPPORTED;
 }
@@ -129,6 +131,7 @@ hj::SolveArgs<T> make_args(const hj_problem_s* prob, int64_t B, int32_t N,
   a.eik_c0 = prob->eik[1]; a.eik_c1 = prob->eik[2]; a.eik_c2 = prob->eik[3];
   a.xb64 = prob->xbd;
   a.cost_sign = (prob->family == HJ_FAMILY_EIKONAL && prob->eik[0] < 0) ? -1.0 : 1.0;
+  a.game_d1 = (prob->family == HJ_FAMILY_GAME_NORMS) ? (int32_t)prob->eik[0] : prob->d;
   a.counter = prob->counter;
   fill_args<T>(a, prob, B, N, o, xq, t, V, iters, status, traj_x, traj_p, warm_x, warm_p);
   return a;
@@ -156,6 +159,10 @@ inline hj_status check_formulation(const hj_problem_s* p, const hj_solver_opts& 
   if (o.formulation == HJ_FORM_HOPF && !p->w_nonzero) return HJ_ERR_INVALID_ARG;
   if (p->family == HJ_FAMILY_EIKONAL && p->eik[0] < 0 && !(o.tau * p->w2max < 1.0))
     return HJ_ERR_STEP_SIZE;
+  if (p->family == HJ_FAMILY_GAME_NORMS) {
+    if (o.formulation != HJ_FORM_LAX || o.inner_steps != 1) return HJ_ERR_UNSUPPORTED;
+    if (!(o.tau * p->w2max_max < 1.0)) return HJ_ERR_STEP_SIZE;
+  }
   return HJ_OK;
 }
 

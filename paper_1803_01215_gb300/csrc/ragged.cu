@@ -177,7 +177,8 @@ hj_status hj_ragged_plan_create(hj_ragged_plan* out, int32_t n_prob, const hj_pr
     if (k.cfg.G == 0) {
       // shared-memory kernel: the bucket's largest N must fit its shared memory
       const bool drift = pr->family == HJ_FAMILY_TANH_DRIFT;
-      if (pr->family == HJ_FAMILY_QUADCOPTER) r = HJ_ERR_UNSUPPORTED;
+      if (pr->family == HJ_FAMILY_QUADCOPTER || pr->family == HJ_FAMILY_GAME_NORMS)
+        r = HJ_ERR_UNSUPPORTED;
       else if (pr->family == HJ_FAMILY_EIKONAL) {
         // the captured graph holds no workspace: the state must fit shared memory
         if ((f64 ? hj::eik_cta_smem_bytes<double>(pr->d, k.nmax)

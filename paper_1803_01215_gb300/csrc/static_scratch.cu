@@ -89,6 +89,7 @@ hj_status hj_solve_batch_static(int32_t family, int32_t d, const double* dyn, in
       break;
     case HJ_FAMILY_TANH_DRIFT: if (n_dyn != (int64_t)d * d) return HJ_ERR_INVALID_ARG; break;
     case HJ_FAMILY_EIKONAL: return HJ_ERR_UNSUPPORTED;   // no bump-centre slot in the array
+    case HJ_FAMILY_GAME_NORMS: return HJ_ERR_UNSUPPORTED;
     default: return HJ_ERR_INVALID_ARG;
   }
   if (!all_finite(W, d) || !all_finite(c, d) || (n_dyn > 0 && !all_finite(dyn, n_dyn)))

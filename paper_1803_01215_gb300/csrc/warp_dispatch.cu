@@ -10,6 +10,7 @@ bool warp_family_has(int family, int d) {
     case HJ_FAMILY_QUADCOPTER: return d == 12;
     case HJ_FAMILY_TANH_DRIFT: return d == 2 || d == 4;
     case HJ_FAMILY_EIKONAL: return d == 2 || d == 10;
+    case HJ_FAMILY_GAME_NORMS: return d == 2 || d == 7;
     default: return false;
   }
 }
@@ -48,6 +49,8 @@ hj_status launch_warp_solver(int family, const SolveArgs<T>& a, WarpConfig cfg, 
       return hopf ? launch_warp_tanh_hopf<T>(a, cfg, s) : launch_warp_tanh<T>(a, cfg, s);
     case HJ_FAMILY_EIKONAL:
       return hopf ? HJ_ERR_UNSUPPORTED : launch_warp_eikonal<T>(a, cfg, s);
+    case HJ_FAMILY_GAME_NORMS:
+      return hopf ? HJ_ERR_UNSUPPORTED : launch_warp_game<T>(a, cfg, s);
     default: return HJ_ERR_UNSUPPORTED;
   }
 }

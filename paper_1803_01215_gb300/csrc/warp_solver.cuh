@@ -239,7 +239,9 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         if (i == NPL - 1) v_sub<T, D>(dp, p[i], pr);
         else v_sub<T, D>(dp, p[i], p[i + 1 < NPL ? i + 1 : i]);
         v_fma<T, D>(xn, -tau, dp, x[i]);                     // x - tau (p_j - p_{j+1})
-        if (F::kHasGradX) {
+        if constexpr (F::kGame) {
+          fam.game_step(ctx[i], x[i], p[i], taud, xn);      // descent in x, ascent in y
+        } else if (F::kHasGradX) {
           T g[D];
           fam.gradx(ctx[i], x[i], p[i], g);
           T base[D];
@@ -315,14 +317,20 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
           // in FP32, the sum over nodes in FP64
           T s = T(0);
 #pragma unroll
-          for (int k = 0; k < D; ++k) s += p[i][k] * (x[i][k] - ((i == 0) ? xl[k] : x[i - 1][k]));
+          for (int k = 0; k < D; ++k) {
+            const T term = p[i][k] * (x[i][k] - ((i == 0) ? xl[k] : x[i - 1][k]));
+            if constexpr (F::kGame) s += (k < fam.d1) ? term : -term;   // <p, dx> - <q, dy>
+            else s += term;
+          }
           acc += (double)(s - delta_t * fam.Ht(x[i], p[i]));
         } else {
           double s = 0.0;
 #pragma unroll
           for (int k = 0; k < D; ++k) {
             const double xm = (double)((i == 0) ? xl[k] : x[i - 1][k]);
-            s += (double)p[i][k] * ((double)x[i][k] - xm);
+            const double term = (double)p[i][k] * ((double)x[i][k] - xm);
+            if constexpr (F::kGame) s += (k < fam.d1) ? term : -term;
+            else s += term;
           }
           acc += s - delta * fam.H64(x[i], p[i]);
         }
@@ -380,8 +388,11 @@ lax_warp_kernel(const SolveArgs<T> a) {
     // cost_sign = -1 (negative eikonal): the positive equation with initial data -g
     const double w2 = k < D ? a.cost_sign * a.W2[k] : 0.0, c = k < D ? a.c[k] : 0.0;
     if (k < D) { sh.w2d[k] = w2; sh.cd[k] = c; }
-    sh.g_off[k] = T(a.tau * w2 * c);
-    sh.g_inv[k] = T(1.0 / (1.0 + a.tau * w2));
+    // a game's maximising coordinates take the ascent prox of g at y_0: the
+    // same formula with -W^2 (the stretch, tau W^2 < 1)
+    const double w2p = (F::kGame && k >= a.game_d1) ? -w2 : w2;
+    sh.g_off[k] = T(a.tau * w2p * c);
+    sh.g_inv[k] = T(1.0 / (1.0 + a.tau * w2p));
     sh.hs[k] = (HOPF && k < D) ? T(a.sigma / w2) : T(0);
     sh.hc[k] = T(a.sigma * c);
   }

@@ -25,7 +25,7 @@ Every workload is a plain dict:
 """
 import numpy as np
 
-FAMILIES = {"quadratic": 0, "quadcopter": 1, "tanh_drift": 2, "eikonal": 3}
+FAMILIES = {"quadratic": 0, "quadcopter": 1, "tanh_drift": 2, "eikonal": 3, "game_norms": 4}
 
 # Quadcopter constants: unit mass, hover thrust gain equal to gravity so that
 # the level-attitude state is an equilibrium of the drift.
@@ -117,6 +117,34 @@ def eikonal(d=2, sign=1, t=0.2, B=None, grid_step=0.1, seed=8):
                 W=W, c=np.zeros(d), xq=xq, t=np.full(len(pts), float(t)), N=N,
                 sigma=sigma, tau=0.24 / sigma, tol=1e-8, max_iter=20000, check_every=16,
                 seed=seed, init_radius=0.1, g_const=EIK_G_CONST)
+
+
+def game_norms(d=2, t=0.1, B=None, grid_step=1.0 / 12.0, seed=9):
+    """Section 6.2's difference-of-norms game: z = (x, y) with x = z[0] (d1 = 1)
+    and y = z[1..d), H = c1(z)|p| - c2(z)|q|, c1(z) = 1 + 3 exp(-4 |z - (1, 1, 0, ...)|^2),
+    c2(z) = c1(-z), and the eikonal example's data g(z) = -1/2 + 1/2 <A^-1 z, z>
+    (W = (1/2.5, 1, 2, ..., 2), c = 0; the -1/2 is EIK_G_CONST).  Query points on
+    the 2-D slice [-3, 3]^2 x {0}^(d-2): the grid of mesh grid_step (1/12, the
+    paper's; B None) or B uniform draws.  delta = 0.02, sigma = 50, tau = 0.24 / sigma."""
+    r = _rng(seed)
+    if B is None:
+        ax = np.linspace(-3.0, 3.0, int(round(6.0 / grid_step)) + 1)
+        a, b = np.meshgrid(ax, ax, indexing="ij")
+        pts = np.stack([a.ravel(), b.ravel()], axis=1)
+    else:
+        pts = r.uniform(-3.0, 3.0, size=(B, 2))
+    zq = np.zeros((len(pts), d))
+    zq[:, :2] = pts
+    W = np.full(d, 2.0)
+    W[0], W[1] = 1.0 / 2.5, 1.0
+    zb = np.zeros(d)
+    zb[:2] = 1.0
+    sigma = 50.0
+    return dict(family="game_norms", d=d, dyn=np.concatenate([[1.0, 1.0, 3.0, 4.0], zb]),
+                W=W, c=np.zeros(d), xq=zq, t=np.full(len(pts), float(t)),
+                N=int(round(t / EIK_DELTA)), sigma=sigma, tau=0.24 / sigma, tol=1e-8,
+                max_iter=20000, check_every=16, seed=seed, init_radius=0.1,
+                g_const=EIK_G_CONST)
 
 
 def subset(w, idx):
