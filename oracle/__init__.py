@@ -20,13 +20,17 @@ Contents
   hopf_pdhg    Algorithm 2 (Hopf formula, backward Euler, Eq. dischopf) as the
                appendix's Hopf tutorial algorithm: the joint prox of g* and
                delta H at j = 1, x_0 eliminated through the conjugate of g.
+  lax_schemes  the Lax saddle problem with forward Euler (Eq. disclaxFE) and
+               the trapezoid average of the two Euler forms, costates indexed
+               by interval as in Eq. disclaxFE, same PDHG steps as lax_pdhg.
   game_pdhg    Algorithm 3 (Lax form for differential games, Eq.
                discgenlaxhopfdg) for Section 6.2's difference-of-norms game:
                shrink_2 dual steps for both players, a descent step for the
                minimiser and an ascent step for the maximiser.
 
 Pins: see tests/test_oracle_pins.py, tests/test_oracle_hopf_pins.py,
-tests/test_oracle_eikonal_pins.py and tests/test_oracle_game_pins.py.  Closed form (quadratic H), discrete
+tests/test_oracle_eikonal_pins.py, tests/test_oracle_game_pins.py and
+tests/test_oracle_schemes_pins.py.  Closed form (quadratic H), discrete
 Riccati (linear drift), direct collocation (tanh drift), the discrete
 characteristic (KKT) equations with complex-step derivatives of an H written
 independently from the quadcopter dynamics, the primal/dual value identity, and

@@ -9,6 +9,9 @@ control-affine dynamics f = f0(x) + B(x) u, so H = <p, f0> + |B^T p|^2 / 2.
 Every array argument has the coordinate axis last: x, p have shape [..., d].
 prox_p(x, v, lam) returns argmin_p { lam * H(x, p) + |p - v|^2 / 2 }, the
 dual proximal map of Algorithm 1 with lam = sigma * delta.
+prox_p_mix(xl, xr, wl, wr, v, lam) returns
+argmin_p { lam (wl H(xl, p) + wr H(xr, p)) + |p - v|^2 / 2 }, the dual map of
+the forward-Euler (wl = 1, wr = 0) and trapezoid (wl = wr = 1/2) forms.
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 """
@@ -33,6 +36,10 @@ class Quadratic:
     def prox_p(self, x, v, lam):
         # lam * p + (p - v) = 0
         return v / (1.0 + lam[..., None])
+
+    def prox_p_mix(self, xl, xr, wl, wr, v, lam):
+        # lam (wl + wr) p + (p - v) = 0
+        return v / (1.0 + (wl + wr) * lam[..., None])
 
 
 class TanhDrift:
@@ -71,6 +78,13 @@ class TanhDrift:
         a, _ = self._act(x)
         lam = lam[..., None]
         return (v - lam * a) / (1.0 + lam)
+
+    def prox_p_mix(self, xl, xr, wl, wr, v, lam):
+        # lam (wl (a(xl) + p) + wr (a(xr) + p)) + (p - v) = 0
+        al, _ = self._act(xl)
+        ar, _ = self._act(xr)
+        lam = lam[..., None]
+        return (v - lam * (wl * al + wr * ar)) / (1.0 + (wl + wr) * lam)
 
 
 class Quadcopter:
@@ -170,6 +184,17 @@ class Quadcopter:
         rhs = v - lam * self.f0(x)
         return np.linalg.solve(M, rhs[..., None])[..., 0]
 
+    def prox_p_mix(self, xl, xr, wl, wr, v, lam):
+        # lam (wl grad_p H(xl, p) + wr grad_p H(xr, p)) + (p - v) = 0, a linear system
+        # with matrix (1 + lam eps (wl + wr)) I + lam (wl B_l B_l^T + wr B_r B_r^T)
+        Bl, Br = self.Bmat(xl), self.Bmat(xr)
+        lam = lam[..., None]
+        BB = wl * np.einsum("...ik,...jk->...ij", Bl, Bl) \
+            + wr * np.einsum("...ik,...jk->...ij", Br, Br)
+        M = (1.0 + lam[..., None] * self.eps * (wl + wr)) * np.eye(12) + lam[..., None] * BB
+        rhs = v - lam * (wl * self.f0(xl) + wr * self.f0(xr))
+        return np.linalg.solve(M, rhs[..., None])[..., 0]
+
 
 class Eikonal:
     """H(x, p) = c(x) |p|_2 with the speed of Section 6.1,
@@ -209,6 +234,14 @@ class Eikonal:
         c, _ = self.speed(x)
         n = np.sqrt(np.sum(v * v, axis=-1))
         keep = np.maximum(n - lam * c, 0.0) / np.where(n > 0, n, 1.0)
+        return keep[..., None] * v
+
+    def prox_p_mix(self, xl, xr, wl, wr, v, lam):
+        # (wl c(xl) + wr c(xr)) |p|: shrink_2 with the weighted speed
+        cl, _ = self.speed(xl)
+        cr, _ = self.speed(xr)
+        n = np.sqrt(np.sum(v * v, axis=-1))
+        keep = np.maximum(n - lam * (wl * cl + wr * cr), 0.0) / np.where(n > 0, n, 1.0)
         return keep[..., None] * v
 
 
