@@ -155,14 +155,16 @@ def measure_other_configs(dev, flush, stream, peak):
     from paper_1803_01215_gb300 import binding
     out = {}
 
-    def run_uniform(w, precision, tag, npts=None, formulation="lax", tune=False):
+    def run_uniform(w, precision, tag, npts=None, formulation="lax", tune=False, scheme="be",
+                    tol=None):
         if npts is not None:
             w = W.subset(w, np.arange(npts))
         prob = binding.Problem.from_workload(w)
-        opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], tol=w["tol"],
+        opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"],
+                                 tol=w["tol"] if tol is None else tol,
                                  max_iter=w["max_iter"], check_every=w["check_every"],
                                  seed=w["seed"], init_radius=w["init_radius"], precision=precision,
-                                 formulation=formulation)
+                                 formulation=formulation, scheme=scheme)
         xq = torch.as_tensor(w["xq"], device=dev)
         t = torch.as_tensor(w["t"], device=dev)
         if tune:
@@ -211,6 +213,35 @@ def measure_other_configs(dev, flush, stream, peak):
         "fp64": {"solves_per_s": conv64 / (ms64 * 1e-3), "ms_per_step": ms64, "converged": conv64},
         "fp32_over_fp64": (n_ok / ms) / (conv64 / ms64) if conv64 else None,
         "note": "trajectories written (the headline step writes V and status only)"}
+
+    # The forward-Euler (Eq. disclaxFE) and trapezoid schemes on the 12-D workload:
+    # throughput (FP32, a solve counts when converged and within 1e-4 of the FP64
+    # value of the same scheme), and the discretisation error of each scheme on
+    # a 256-point slice (FP64, tight stop) against the Richardson extrapolation
+    # (4 V_trap(128) - V_trap(64)) / 3 of the second-order trapezoid values.
+    sch = {}
+    wq = W.quadcopter()
+    for scheme in ("fe", "trap"):
+        ms, conv, iters, r32 = run_uniform(wq, "fp32", f"timed_{scheme}_qc", scheme=scheme)
+        ms64, conv64, _, r64 = run_uniform(wq, "fp64", f"timed_{scheme}_qc_fp64", scheme=scheme)
+        ok = ((r32["status"] == 0) & (r64["status"] == 0)
+              & ((r32["V"] - r64["V"]).abs() <= 1e-4 * r64["V"].abs().clamp_min(1.0)))
+        n_ok = int(ok.sum().item())
+        sch[scheme] = {"fp32": {"solves_per_s": n_ok / (ms * 1e-3), "ms_per_step": ms,
+                                "converged_accurate": n_ok, "mean_iters": iters / len(wq["xq"])},
+                       "fp64": {"solves_per_s": conv64 / (ms64 * 1e-3), "ms_per_step": ms64,
+                                "converged": conv64}}
+    acc = {}
+    for scheme, N in (("be", 64), ("fe", 64), ("trap", 32), ("trap", 64), ("trap", 128)):
+        wa = dict(W.subset(wq, np.arange(256)), N=N, max_iter=400000)
+        _, conv, _, ra = run_uniform(wa, "fp64", f"acc_{scheme}_{N}", scheme=scheme, tol=1e-18)
+        acc[(scheme, N)] = ra["V"].double().cpu().numpy()
+    vref = (4.0 * acc[("trap", 128)] - acc[("trap", 64)]) / 3.0
+    sch["discretisation_error_256_points_fp64"] = {
+        f"{k[0]}_N{k[1]}": {"median_abs": float(np.median(np.abs(v - vref))),
+                            "max_abs": float(np.max(np.abs(v - vref)))}
+        for k, v in acc.items() if k != ("trap", 128)}
+    out["schemes_quadcopter12d_B4096_N64"] = sch
 
     # Section 6.1's dimensional scaling: the negative eikonal equation at t = 0.2
     # (delta = 0.02, N = 10, sigma = 100) on the 2-D slice grid [-3, 3]^2 (mesh

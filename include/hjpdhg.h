@@ -91,6 +91,29 @@ enum { HJ_PREC_FP32 = 0, HJ_PREC_FP64 = 1 };
  *                 the same saddle value.                                        */
 enum { HJ_FORM_LAX = 0, HJ_FORM_HOPF = 1 };
 
+/* Time discretisation of the Lax form (hj_solver_opts.scheme).  With the
+ * costate of interval [s_{j-1}, s_j] stored at node j (traj_p[b][j], j = 1..N),
+ * every scheme solves
+ *   max_p min_x g(x_0) + sum_{j=1}^N <p_j, x_j - x_{j-1}>
+ *               - delta sum_{j=1}^N (wR H(x_j, p_j) + wL H(x_{j-1}, p_j))
+ * with weights on the two ends of each interval:
+ *   HJ_SCHEME_BE    (wR, wL) = (1, 0): backward Euler, Eq. (disclaxBE).
+ *   HJ_SCHEME_FE    (0, 1): forward Euler, Eq. (disclaxFE); its costate p_{j-1}
+ *                   (the paper's index) is stored at node j.
+ *   HJ_SCHEME_TRAP  (1/2, 1/2): the average of the two Euler forms, which the
+ *                   paper proposes for higher accuracy (end of Section 5 and
+ *                   Section 7); second order in delta where both are first.
+ * The PDHG steps are Algorithm 1's with H at x^k: the dual step is the prox of
+ * sigma delta (wR H(x_j, .) + wL H(x_{j-1}, .)); x_j (1 <= j < N) takes one
+ * gradient step on -delta (wR H(x_j, p_j) + wL H(x_j, p_{j+1})); x_0, on which
+ * both g and (for wL > 0) H act, takes one gradient step on -delta wL H(x_0, p_1)
+ * followed by the exact prox of g.  FE and TRAP run in the register-resident
+ * kernel only (quadcopter, tanh drift d in {2, 4}, eikonal d in {2, 10}; N <= 128
+ * in FP64) with the Lax form and inner_steps = 1; the quadratic family, whose H
+ * does not depend on x, has the same problem under every scheme.  Other cases
+ * return HJ_ERR_UNSUPPORTED.                                                  */
+enum { HJ_SCHEME_BE = 0, HJ_SCHEME_FE = 1, HJ_SCHEME_TRAP = 2 };
+
 /* Per-point outcome written to status[].  HJ_POINT_INVALID marks a point whose
  * own N was outside the range of the kernel it was routed to (ragged batches:
  * N[b] outside 1..256); such a point is not iterated.                        */
@@ -135,7 +158,9 @@ hj_status hj_problem_destroy(hj_problem prob);
  *                point b depends on (seed, point_offset + b) only, so a batch
  *                split into slices reproduces the unsplit run.
  *   formulation  HJ_FORM_LAX (0, the default of a zeroed struct) or HJ_FORM_HOPF;
- *                Hopf needs every W_i nonzero (HJ_ERR_INVALID_ARG otherwise).  */
+ *                Hopf needs every W_i nonzero (HJ_ERR_INVALID_ARG otherwise).
+ *   scheme       HJ_SCHEME_BE (0, the default), HJ_SCHEME_FE or HJ_SCHEME_TRAP
+ *                (Lax form only).                                              */
 typedef struct {
   double sigma, tau, theta, tol;
   int32_t max_iter, check_every, inner_steps, precision;
@@ -143,6 +168,7 @@ typedef struct {
   double init_radius;
   int64_t point_offset;
   int32_t formulation;
+  int32_t scheme;
 } hj_solver_opts;
 
 /* Solve B independent points with a common N (Algorithm 1, Eq. (disclaxBE); with
@@ -156,7 +182,8 @@ typedef struct {
  *   status   (device) [B] int8 out: HJ_POINT_*.
  *   traj_x   (device, may be NULL) [B][N+1][d] out: x_0..x_N (Hopf: x_0 is the
  *            minimiser grad g*(p_1) = c + p_1 / W^2 of g(x_0) - <p_1, x_0>).
- *   traj_p   (device, may be NULL) [B][N+1][d] out: p_0 (= 0), p_1..p_N.
+ *   traj_p   (device, may be NULL) [B][N+1][d] out: p_0 (= 0), p_1..p_N
+ *            (p_j: the costate of interval [s_{j-1}, s_j], see HJ_SCHEME_*).
  *   warm_x, warm_p (device, may both be NULL) [B][N+1][d] in: initial iterate
  *            instead of the random guess (resume); warm_x[b][N] is ignored
  *            (x_N = x) and warm_p[b][0] is ignored (p_0 = 0); Hopf also
@@ -174,7 +201,8 @@ hj_status hj_solve_batch(hj_problem prob, int64_t B,
                          void* stream);
 
 /* Gradient of L = sum_b w_b V_b at solved points (the adjoint of the value).
- * At a saddle of Eq. (disclaxBE) every total derivative of V equals the partial
+ * At a saddle of Eq. (disclaxBE) (trajectories of HJ_SCHEME_BE, Lax or Hopf
+ * form) every total derivative of V equals the partial
  * derivative of its Lagrangian (envelope theorem), so from the trajectories of
  * a converged hj_solve_batch call (same problem, t, N, precision):
  *   dV/dW_i = W_i (x_0i - c_i)^2,   dV/dc_i = -W_i^2 (x_0i - c_i),
@@ -217,7 +245,8 @@ hj_status hj_solve_grad(hj_problem prob, int64_t B, const double* t, int32_t N,
  *   dL_dV, dW, dc, ddyn, dxq  as hj_solve_grad (dxq required).
  * Families: quadcopter (ddyn: m, a_h, g_z, eps) and quadratic with d <= 4;
  * N <= 256, and N <= 128 for the quadcopter in FP64; opts->inner_steps == 1
- * and opts->formulation == HJ_FORM_LAX (HJ_ERR_UNSUPPORTED otherwise).
+ * opts->formulation == HJ_FORM_LAX and opts->scheme == HJ_SCHEME_BE
+ * (HJ_ERR_UNSUPPORTED otherwise).
  * Allocates a workspace of about 3 (N+1) d (max_iters/checkpoint_every + 1)
  * values per CTA of a grid of 4 CTAs per SM, and synchronises `stream`.
  * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_STEP_SIZE, HJ_ERR_UNSUPPORTED, HJ_ERR_OOM,

@@ -30,7 +30,8 @@ class SolverOpts(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("inner_steps", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("init_radius", ctypes.c_double),
-                ("point_offset", ctypes.c_int64), ("formulation", ctypes.c_int32)]
+                ("point_offset", ctypes.c_int64), ("formulation", ctypes.c_int32),
+                ("scheme", ctypes.c_int32)]
 
 
 _LIB = None
@@ -224,14 +225,15 @@ def solve_grad_unrolled(problem, xq, t, N, opts, iters, dL_dV, checkpoint_every=
 
 
 FORM = {"lax": 0, "hopf": 1}
+SCHEME = {"be": 0, "fe": 1, "trap": 2}
 
 
 def make_opts(*, sigma, tau, theta=1.0, tol=1e-8, max_iter=20000, check_every=16,
               inner_steps=1, precision="fp32", seed=0, init_radius=0.1, point_offset=0,
-              formulation="lax"):
+              formulation="lax", scheme="be"):
     return SolverOpts(float(sigma), float(tau), float(theta), float(tol), int(max_iter),
                       int(check_every), int(inner_steps), PREC[precision], int(seed),
-                      float(init_radius), int(point_offset), FORM[formulation])
+                      float(init_radius), int(point_offset), FORM[formulation], SCHEME[scheme])
 
 
 def solve_batch(problem, xq, t, N, opts, *, return_traj=False, warm_x=None, warm_p=None,

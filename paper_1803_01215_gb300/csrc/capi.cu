@@ -32,7 +32,7 @@ const char* hj_status_str(hj_status s) {
   return "unknown status";
 }
 
-int32_t hj_version(void) { return 100; }
+int32_t hj_version(void) { return 101; }
 
 hj_status hj_problem_create(hj_problem* out, int32_t family, int32_t d, const double* dyn,
                             int64_t n_dyn, const double* W, const double* c) {
@@ -208,7 +208,8 @@ hj_status hj_solve_grad_unrolled(hj_problem prob, int64_t B, const double* xq, c
   if (oc != HJ_OK) return oc;
   if (max_iters < 0 || checkpoint_every < 1) return HJ_ERR_INVALID_ARG;
   if (opts->inner_steps != 1) return HJ_ERR_UNSUPPORTED;   // one gradient step per x-update
-  if (opts->formulation != HJ_FORM_LAX) return HJ_ERR_UNSUPPORTED;   // the Lax iteration only
+  if (opts->formulation != HJ_FORM_LAX || opts->scheme != HJ_SCHEME_BE)
+    return HJ_ERR_UNSUPPORTED;                   // the backward-Euler Lax iteration only
   const bool qc = prob->family == HJ_FAMILY_QUADCOPTER;
   if (!(qc || (prob->family == HJ_FAMILY_QUADRATIC && prob->d <= 4))) return HJ_ERR_UNSUPPORTED;
   if (dW == nullptr || dc == nullptr || dxq == nullptr || (qc && ddyn == nullptr))

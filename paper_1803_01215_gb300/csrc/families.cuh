@@ -13,6 +13,10 @@
 //   prox_first(ctx, pc, x, v, hs, hc)
 //                           the Hopf form's node-1 dual step: the prox of
 //                           sigma g* + lam H, hs = sigma / W^2, hc = sigma c
+//   prox_mix(cr, cl, pc, wr, wl, xr, xl, v)
+//                           v <- argmin_p lam (wr H(xr, p) + wl H(xl, p)) + |p - v|^2/2
+//                           for weights wr + wl = 1 (forward-Euler and trapezoid
+//                           schemes; cr, cl the contexts at xr, xl)
 // All families have L = |u|^2/2, so H = <p, f0(x)> + |B(x)^T p|^2/2 (Section 2).
 #pragma once
 #include "hj_internal.cuh"
@@ -261,6 +265,40 @@ struct FamQuadcopter {
     v[8] = (w2 - f * b2) * ial;
   }
 
+  // Mixed schemes: (al I + lam (wr B_r B_r^T + wl B_l B_l^T)) p = v - lam (wr f0(xr) + wl f0(xl)),
+  // al = 1 + lam eps (wr + wl = 1).  Rows 0-5 and 9-11 decouple as above; rows
+  // 6-8 carry two rank-1 terms, u = a_r/m and s = a_l/m with alpha = lam wr and
+  // beta = lam wl.  With y = (w - alpha U u - beta S s) / al, U = u.y and S = s.y
+  // solve the 2x2 system
+  //   [al + alpha u.u, beta u.s; alpha u.s, al + beta s.s] [U; S] = [u.w; s.w].
+  __device__ __forceinline__ void prox_mix(const Ctx& cr, const Ctx& cl, const PC& pc, T wr, T wl,
+                                           const T (&xr)[D], const T (&xl)[D], T (&v)[D]) const {
+    const T lam = pc.lam, ial = pc.ial;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = (v[k] - lam * (wr * xr[6 + k] + wl * xl[6 + k])) * ial;
+#pragma unroll
+    for (int k = 9; k < 12; ++k) v[k] *= pc.irate;
+    T w[3], u[3], sv[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      w[r] = v[6 + r] - (pc.lam_ah * (wr * cr.a[r] + wl * cl.a[r]) - (r == 2 ? pc.lam_gz : T(0)));
+      u[r] = cr.a[r] * m_inv;
+      sv[r] = cl.a[r] * m_inv;
+    }
+    const T al = pc.al, alpha = lam * wr, beta = lam * wl;
+    const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const T ss = sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2];
+    const T us = u[0] * sv[0] + u[1] * sv[1] + u[2] * sv[2];
+    const T uw = u[0] * w[0] + u[1] * w[1] + u[2] * w[2];
+    const T sw = sv[0] * w[0] + sv[1] * w[1] + sv[2] * w[2];
+    const T m11 = al + alpha * uu, m22 = al + beta * ss;
+    const T idet = fdiv<T>(T(1), m11 * m22 - alpha * beta * us * us);
+    const T U = (m22 * uw - beta * us * sw) * idet;
+    const T S = (m11 * sw - alpha * us * uw) * idet;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) v[6 + r] = (w[r] - alpha * U * u[r] - beta * S * sv[r]) * ial;
+  }
+
   // Hopf form, node 1: the prox above with sigma g*(p) added, g*(p) = <p, c> +
   // 1/2 sum p_k^2 / W_k^2 (hs = sigma / W^2, hc = sigma c):
   //   (diag(1 + lam eps + hs) + lam B B^T) p = v - hc - lam f0.
@@ -367,6 +405,12 @@ struct FamTanhDrift {
 #pragma unroll
     for (int k = 0; k < D; ++k) v[k] = (v[k] - pc.lam * c.a[k]) * pc.s;
   }
+  // the drift averaged with the weights: (1 + lam) p = v - lam (wr a(xr) + wl a(xl))
+  __device__ __forceinline__ void prox_mix(const Ctx& cr, const Ctx& cl, const PC& pc, T wr, T wl,
+                                           const T (&)[D], const T (&)[D], T (&v)[D]) const {
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = (v[k] - pc.lam * (wr * cr.a[k] + wl * cl.a[k])) * pc.s;
+  }
   // Hopf form, node 1 (hs = sigma / W^2, hc = sigma c):
   //   (1 + lam + hs_k) p_k = v_k - hc_k - lam a_k.
   __device__ __forceinline__ void prox_first(const Ctx& c, const PC& pc, const T (&)[D],
@@ -449,6 +493,17 @@ struct FamEikonal {
 #pragma unroll
     for (int k = 0; k < D; ++k) n2 += v[k] * v[k];
     const T n = sqrt_t<T>(n2), th = pc.lam * c.c;
+    const T keep = (n > th) ? fdiv<T>(n - th, n) : T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] *= keep;
+  }
+  // shrink_2 with the weighted speed wr c(xr) + wl c(xl)
+  __device__ __forceinline__ void prox_mix(const Ctx& cr, const Ctx& cl, const PC& pc, T wr, T wl,
+                                           const T (&)[D], const T (&)[D], T (&v)[D]) const {
+    T n2 = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) n2 += v[k] * v[k];
+    const T n = sqrt_t<T>(n2), th = pc.lam * (wr * cr.c + wl * cl.c);
     const T keep = (n > th) ? fdiv<T>(n - th, n) : T(0);
 #pragma unroll
     for (int k = 0; k < D; ++k) v[k] *= keep;

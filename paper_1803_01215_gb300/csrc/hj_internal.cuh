@@ -28,6 +28,11 @@ struct SolveArgs {
   T tol_t;
   int32_t max_iter, check_every, inner_steps;
   int32_t formulation;   // HJ_FORM_LAX or HJ_FORM_HOPF
+  // HJ_SCHEME_*: H on interval j weighted wR at x_j and wL at x_{j-1}
+  // (backward Euler 1, 0; forward Euler 0, 1; trapezoid 1/2, 1/2)
+  int32_t scheme;
+  T mix_wr_t, mix_wl_t;
+  double mix_wr, mix_wl;
   uint64_t seed;
   double radius;
   int64_t point_offset;
@@ -223,6 +228,13 @@ template <typename T>
 hj_status launch_warp_tanh_hopf(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 template <typename T>
 hj_status launch_warp_eikonal(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
+// forward-Euler and trapezoid schemes (SolveArgs::scheme != HJ_SCHEME_BE)
+template <typename T>
+hj_status launch_warp_quadcopter_mix(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
+template <typename T>
+hj_status launch_warp_tanh_mix(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
+template <typename T>
+hj_status launch_warp_eikonal_mix(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 template <typename T>
 hj_status launch_warp_game(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 // Default launch shape for (family, d, Nmax); {0, 0} when no warp kernel fits.

@@ -76,6 +76,7 @@ hj_status dispatch(hj_problem_s* p, const hj::SolveArgs<T>& a, hj::WarpConfig cf
     const hj_status r = hj::launch_warp_solver<T>(p->family, a, cfg, s);
     if (r != HJ_ERR_UNSUPPORTED) return r;
   }
+  if (a.scheme != HJ_SCHEME_BE) return HJ_ERR_UNSUPPORTED;   // register kernel only
   if (p->family == HJ_FAMILY_TANH_DRIFT) return hj::launch_td_cta_solver<T>(a, true, s);
   if (p->family == HJ_FAMILY_EIKONAL) return hj::launch_eik_cta_solver<T>(a, s);
   if (p->family == HJ_FAMILY_GAME_NORMS) return HJ_ERR_UNSUPPORTED;   // register kernel only
@@ -125,6 +126,12 @@ hj::SolveArgs<T> make_args(const hj_problem_s* prob, int64_t B, int32_t N,
   a.max_iter = o.max_iter; a.check_every = o.check_every; a.inner_steps = o.inner_steps;
   a.seed = o.seed; a.radius = o.init_radius; a.point_offset = o.point_offset;
   a.formulation = o.formulation;
+  // H independent of x (quadratic family): both ends of an interval give the
+  // same H, so every scheme is the backward-Euler problem and runs as such
+  a.scheme = prob->family == HJ_FAMILY_QUADRATIC ? HJ_SCHEME_BE : o.scheme;
+  a.mix_wr = a.scheme == HJ_SCHEME_BE ? 1.0 : (a.scheme == HJ_SCHEME_FE ? 0.0 : 0.5);
+  a.mix_wl = 1.0 - a.mix_wr;
+  a.mix_wr_t = T(a.mix_wr); a.mix_wl_t = T(a.mix_wl);
   a.xq = xq; a.t = t; a.V = V; a.iters = iters; a.status = status;
   a.W2 = prob->W2; a.c = prob->c; a.A64 = prob->Ad;
   a.qc_m = prob->qc[0]; a.qc_ah = prob->qc[1]; a.qc_gz = prob->qc[2]; a.qc_eps = prob->qc[3];
@@ -145,6 +152,8 @@ inline hj_status check_opts(const hj_solver_opts& o) {
   if (o.max_iter < 1 || o.check_every < 1 || o.inner_steps < 1) return HJ_ERR_INVALID_ARG;
   if (o.precision != HJ_PREC_FP32 && o.precision != HJ_PREC_FP64) return HJ_ERR_INVALID_ARG;
   if (o.formulation != HJ_FORM_LAX && o.formulation != HJ_FORM_HOPF) return HJ_ERR_INVALID_ARG;
+  if (o.scheme != HJ_SCHEME_BE && o.scheme != HJ_SCHEME_FE && o.scheme != HJ_SCHEME_TRAP)
+    return HJ_ERR_INVALID_ARG;
   if (!(std::isfinite(o.init_radius) && o.init_radius >= 0.0) || o.point_offset < 0)
     return HJ_ERR_INVALID_ARG;
   if (4.0 * o.sigma * o.tau >= 1.0) return HJ_ERR_STEP_SIZE;
@@ -155,6 +164,10 @@ inline hj_status check_opts(const hj_solver_opts& o) {
 // solved in the Lax form only, and its negative equation's concave x_0 prox
 // needs tau W_i^2 < 1.
 inline hj_status check_formulation(const hj_problem_s* p, const hj_solver_opts& o) {
+  // the forward-Euler and trapezoid forms: Lax form, one gradient step, no game
+  if (o.scheme != HJ_SCHEME_BE && p->family != HJ_FAMILY_QUADRATIC &&
+      (o.formulation != HJ_FORM_LAX || o.inner_steps != 1 || p->family == HJ_FAMILY_GAME_NORMS))
+    return HJ_ERR_UNSUPPORTED;
   if (o.formulation == HJ_FORM_HOPF && p->family == HJ_FAMILY_EIKONAL) return HJ_ERR_UNSUPPORTED;
   if (o.formulation == HJ_FORM_HOPF && !p->w_nonzero) return HJ_ERR_INVALID_ARG;
   if (p->family == HJ_FAMILY_EIKONAL && p->eik[0] < 0 && !(o.tau * p->w2max < 1.0))

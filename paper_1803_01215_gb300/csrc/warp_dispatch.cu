@@ -40,6 +40,15 @@ hj_status launch_warp_solver(int family, const SolveArgs<T>& a, WarpConfig cfg, 
   if (!warp_config_available(family, a.d, cfg, sizeof(T) == 8)) return HJ_ERR_UNSUPPORTED;
   if (a.N > 32 * cfg.G * cfg.NPL) return HJ_ERR_UNSUPPORTED;
   const bool hopf = a.formulation == HJ_FORM_HOPF;
+  if (a.scheme != HJ_SCHEME_BE) {                 // forward Euler, trapezoid (Lax form)
+    if (hopf) return HJ_ERR_UNSUPPORTED;
+    switch (family) {
+      case HJ_FAMILY_QUADCOPTER: return launch_warp_quadcopter_mix<T>(a, cfg, s);
+      case HJ_FAMILY_TANH_DRIFT: return launch_warp_tanh_mix<T>(a, cfg, s);
+      case HJ_FAMILY_EIKONAL: return launch_warp_eikonal_mix<T>(a, cfg, s);
+      default: return HJ_ERR_UNSUPPORTED;
+    }
+  }
   switch (family) {
     case HJ_FAMILY_QUADRATIC:
       return hopf ? launch_warp_quadratic_hopf<T>(a, cfg, s) : launch_warp_quadratic<T>(a, cfg, s);

@@ -1,0 +1,18 @@
+// Instantiations of the register-resident solver for the Quadcopter family,
+// forward-Euler and trapezoid schemes.
+#include "warp_solver.cuh"
+
+namespace hj {
+
+template <typename T>
+hj_status launch_warp_quadcopter_mix(const SolveArgs<T>& a, WarpConfig c, cudaStream_t s) {
+  switch (a.d) {
+    case 12: return launch_warp_shape<T, FamQuadcopter, 12, false, true>(a, c, s);
+    default: return HJ_ERR_UNSUPPORTED;
+  }
+}
+
+template hj_status launch_warp_quadcopter_mix<float>(const SolveArgs<float>&, WarpConfig, cudaStream_t);
+template hj_status launch_warp_quadcopter_mix<double>(const SolveArgs<double>&, WarpConfig, cudaStream_t);
+
+}  // namespace hj

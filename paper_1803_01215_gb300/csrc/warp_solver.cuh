@@ -19,6 +19,12 @@
 //   x_j  <- x_j - tau (p_j - p_{j+1}) + tau delta grad_x H(x_j^k, p_j)      j = 1..N-1
 //   z_j  <- x_j^{k+1} + theta (x_j^{k+1} - x_j^k)
 // and, on test iterations, the squared increments summed in FP64 over the group.
+//
+// MIX = true runs the forward-Euler and trapezoid schemes (HJ_SCHEME_FE/TRAP):
+// H on interval j is wR H(x_j, .) + wL H(x_{j-1}, .), so the dual step also
+// needs x_{j-1}^k (one more exchange slot per lane, and x_0^k as a whole vector),
+// x_j's gradient step adds wL grad_x H(x_j, p_{j+1}), and the x_0 step adds
+// wL grad_x H(x_0, p_1) before the prox of g.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -42,7 +48,7 @@ constexpr int padded_dim() { return ((D * (int)sizeof(T) + 15) / 16) * 16 / (int
 // (x_0 <- (v + tau W^2 c) / (1 + tau W^2) as offset and reciprocal), the
 // per-lane exchange slots of the CTA's groups, and for G > 1 the reduction
 // scratch of the CTA's one group.
-template <typename T, class F, int D, int G>
+template <typename T, class F, int D, int G, bool MIX = false>
 struct WarpShared {
   static constexpr int kGroups = (G == 1) ? kWarpsPerCtaG1 : 1;
   static constexpr int DP = padded_dim<T, D>();
@@ -55,6 +61,9 @@ struct WarpShared {
   alignas(16) T zs[kGroups][32 * G][DP];   // z (in the epilogue x) of each lane's last node
   alignas(16) T ps[kGroups][32 * G][DP];   // p of each lane's first node
   alignas(16) T x0s[kGroups][DP];          // z_0 (in the epilogue x_0), one coordinate per lane
+  // MIX only: x^k of each lane's last node, and x_0^k
+  alignas(16) T xs[MIX ? kGroups : 1][MIX ? 32 * G : 1][MIX ? DP : 1];
+  alignas(16) T x0x[MIX ? kGroups : 1][MIX ? DP : 1];
   T red[G][2];
   double vred[G];
   unsigned long long item;
@@ -113,9 +122,10 @@ __device__ __forceinline__ T relax(T xn, T xo, T th) {
   else return xn + th * (xn - xo);
 }
 
-template <typename T, class F, int D, int NPL, int G, bool TH1, bool HOPF>
+template <typename T, class F, int D, int NPL, int G, bool TH1, bool HOPF, bool MIX>
 __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam, int64_t item,
-                                            int lane, int wg, WarpShared<T, F, D, G>& sh) {
+                                            int lane, int wg, WarpShared<T, F, D, G, MIX>& sh) {
+  static_assert(!(MIX && (HOPF || F::kGame)), "the mixed schemes are Lax-form control problems");
   const PointRef<T> pt = point_ref(a, item);
   const int N = pt.N;
   const int gl = wg * 32 + lane;
@@ -127,6 +137,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   const T sig = a.sigma_t, tau = a.tau_t, th = a.theta_t;
   const T delta_t = T(a.t[pt.id]) / T(N);
   const T lam = sig * delta_t, taud = tau * delta_t;
+  const T wr = a.mix_wr_t, wl = a.mix_wl_t;      // MIX: weights of H at x_j and x_{j-1}
   const typename F::PC pc = fam.point(lam);
   const uint64_t gid = (uint64_t)(a.point_offset + pt.id);
 
@@ -178,7 +189,10 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   T* pslot = &sh.ps[grp][0][0];
   T* x0slot = &sh.x0s[grp][0];
   if (own0) x0slot[k0] = z0;                  // read by lane 0 after the first barrier
-  constexpr int DP = WarpShared<T, F, D, G>::DP;
+  T* xslot = &sh.xs[grp][0][0];
+  T* x0xslot = &sh.x0x[grp][0];
+  if constexpr (MIX) { if (own0) x0xslot[k0] = x0; }
+  constexpr int DP = WarpShared<T, F, D, G, MIX>::DP;
   constexpr int kLanes = 32 * G;
 
   // One iteration; CHK adds the squared increments (test iterations only, so
@@ -188,9 +202,19 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     typename F::Ctx ctx[NPL];
     // ---- z_{j-1} of the first owned node: the left lane's slot (z^k of its last node)
     slot_store<T, D>(zslot + gl * DP, z[NPL - 1]);
+    if constexpr (MIX) slot_store<T, D>(xslot + gl * DP, x[NPL - 1]);
     group_sync<G>();
     T zl[D];
     slot_load<T, D>(gl > 0 ? zslot + (gl - 1) * DP : x0slot, zl);
+    // MIX: x_{j-1}^k of the first owned node and its H quantities; x_0^k whole
+    // (read here, before the next barrier, since the x_0 step rewrites its slot)
+    T xlv[MIX ? D : 1], x0v[MIX ? D : 1];
+    typename F::Ctx ctxl;
+    if constexpr (MIX) {
+      slot_load<T, D>(gl > 0 ? xslot + (gl - 1) * DP : x0xslot, xlv);
+      if (own0) slot_load<T, D>(x0xslot, x0v);
+      fam.context(xlv, ctxl);
+    }
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
       if (jbase + i <= N) {
@@ -202,6 +226,9 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         if constexpr (HOPF) {                                // Hopf: node 1 also carries g*
           if (i == 0 && gl == 0) fam.prox_first(ctx[i], pc, x[i], v, sh.hs, sh.hc);
           else fam.prox(ctx[i], pc, x[i], v);
+        } else if constexpr (MIX) {                          // prox of lam (wR H(x_j) + wL H(x_{j-1}))
+          if (i == 0) fam.prox_mix(ctx[i], ctxl, pc, wr, wl, x[i], xlv, v);
+          else fam.prox_mix(ctx[i], ctx[i > 0 ? i - 1 : 0], pc, wr, wl, x[i], x[i > 0 ? i - 1 : 0], v);
         } else {
           fam.prox(ctx[i], pc, x[i], v);
         }
@@ -226,11 +253,25 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     }
     if (own0 && !HOPF) {
       // x_0 <- prox_{tau g}(x_0 + tau p_1), coordinate k0; p_1 is lane 0's slot
-      const T xn = (x0 + tau * pslot[k0] + goff) * ginv;      // (D^T p)_0 = -p_1
+      T v0 = x0 + tau * pslot[k0];                            // (D^T p)_0 = -p_1
+      if constexpr (MIX) {
+        // + tau delta wL grad_x H(x_0^k, p_1): the whole gradient, coordinate k0 kept
+        T p1[D], g0[D];
+        slot_load<T, D>(pslot, p1);
+        typename F::Ctx c0;
+        fam.context(x0v, c0);
+        fam.gradx(c0, x0v, p1, g0);
+        T gk = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) gk = (k == k0) ? g0[k] : gk;
+        v0 += taud * wl * gk;
+      }
+      const T xn = (v0 + goff) * ginv;
       if constexpr (CHK) { const T e = xn - x0; rx += e * e; }
       z0 = relax<T, TH1>(xn, x0, th);
       x0 = xn;
       x0slot[k0] = z0;
+      if constexpr (MIX) x0xslot[k0] = xn;
     }
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
@@ -241,6 +282,18 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         v_fma<T, D>(xn, -tau, dp, x[i]);                     // x - tau (p_j - p_{j+1})
         if constexpr (F::kGame) {
           fam.game_step(ctx[i], x[i], p[i], taud, xn);      // descent in x, ascent in y
+        } else if constexpr (MIX) {
+          // + tau delta (wR grad_x H(x_j, p_j) + wL grad_x H(x_j, p_{j+1}))
+          T g[D], g2[D];
+          fam.gradx(ctx[i], x[i], p[i], g);
+          if (i == NPL - 1) fam.gradx(ctx[i], x[i], pr, g2);
+          else fam.gradx(ctx[i], x[i], p[i + 1 < NPL ? i + 1 : i], g2);
+#pragma unroll
+          for (int k = 0; k < D; ++k) g[k] = wr * g[k] + wl * g2[k];
+          T base[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) base[k] = xn[k];
+          v_fma<T, D>(xn, taud, g, base);
         } else if (F::kHasGradX) {
           T g[D];
           fam.gradx(ctx[i], x[i], p[i], g);
@@ -322,7 +375,12 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
             if constexpr (F::kGame) s += (k < fam.d1) ? term : -term;   // <p, dx> - <q, dy>
             else s += term;
           }
-          acc += (double)(s - delta_t * fam.Ht(x[i], p[i]));
+          if constexpr (MIX) {
+            const T hl = (i == 0) ? fam.Ht(xl, p[i]) : fam.Ht(x[i > 0 ? i - 1 : 0], p[i]);
+            acc += (double)(s - delta_t * (wr * fam.Ht(x[i], p[i]) + wl * hl));
+          } else {
+            acc += (double)(s - delta_t * fam.Ht(x[i], p[i]));
+          }
         } else {
           double s = 0.0;
 #pragma unroll
@@ -332,7 +390,12 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
             if constexpr (F::kGame) s += (k < fam.d1) ? term : -term;
             else s += term;
           }
-          acc += s - delta * fam.H64(x[i], p[i]);
+          if constexpr (MIX) {
+            const double hl = (i == 0) ? fam.H64(xl, p[i]) : fam.H64(x[i > 0 ? i - 1 : 0], p[i]);
+            acc += s - delta * (a.mix_wr * fam.H64(x[i], p[i]) + a.mix_wl * hl);
+          } else {
+            acc += s - delta * fam.H64(x[i], p[i]);
+          }
         }
       }
     }
@@ -379,12 +442,12 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   }
 }
 
-template <typename T, class F, int D, int NPL, int G, bool TH1, bool HOPF>
+template <typename T, class F, int D, int NPL, int G, bool TH1, bool HOPF, bool MIX>
 __global__ void __launch_bounds__(warp_block_threads<G>())
 lax_warp_kernel(const SolveArgs<T> a) {
-  __shared__ WarpShared<T, F, D, G> sh;
+  __shared__ WarpShared<T, F, D, G, MIX> sh;
   F::load_shared(a, sh.fam);
-  for (int k = threadIdx.x; k < WarpShared<T, F, D, G>::DP; k += blockDim.x) {
+  for (int k = threadIdx.x; k < WarpShared<T, F, D, G, MIX>::DP; k += blockDim.x) {
     // cost_sign = -1 (negative eikonal): the positive equation with initial data -g
     const double w2 = k < D ? a.cost_sign * a.W2[k] : 0.0, c = k < D ? a.c[k] : 0.0;
     if (k < D) { sh.w2d[k] = w2; sh.cd[k] = c; }
@@ -413,15 +476,15 @@ lax_warp_kernel(const SolveArgs<T> a) {
       item = (int64_t)sh.item;
     }
     if (item >= a.B) break;
-    solve_point<T, F, D, NPL, G, TH1, HOPF>(a, fam, item, lane, wg, sh);
+    solve_point<T, F, D, NPL, G, TH1, HOPF, MIX>(a, fam, item, lane, wg, sh);
   }
 }
 
-template <typename T, class F, int D, int NPL, int G, bool TH1, bool HOPF>
+template <typename T, class F, int D, int NPL, int G, bool TH1, bool HOPF, bool MIX>
 hj_status launch_warp_cfg_th(const SolveArgs<T>& a, cudaStream_t s) {
   static int blocks_per_sm = -1;
   static int num_sms = 0;
-  auto kern = lax_warp_kernel<T, F, D, NPL, G, TH1, HOPF>;
+  auto kern = lax_warp_kernel<T, F, D, NPL, G, TH1, HOPF, MIX>;
   constexpr int threads = warp_block_threads<G>();
   if (blocks_per_sm < 0) {
     int dev = 0;
@@ -442,34 +505,43 @@ hj_status launch_warp_cfg_th(const SolveArgs<T>& a, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? HJ_OK : HJ_ERR_CUDA;
 }
 
-// theta = 1 (the paper's choice) gets its own kernel
-template <typename T, class F, int D, int NPL, int G, bool HOPF>
+// theta = 1 (the paper's choice) gets its own kernel; the mixed schemes run
+// the general relaxation z = x + theta (x - x^k) for every theta
+template <typename T, class F, int D, int NPL, int G, bool HOPF, bool MIX>
 hj_status launch_warp_cfg(const SolveArgs<T>& a, cudaStream_t s) {
-  return a.theta == 1.0 ? launch_warp_cfg_th<T, F, D, NPL, G, true, HOPF>(a, s)
-                        : launch_warp_cfg_th<T, F, D, NPL, G, false, HOPF>(a, s);
+  if constexpr (MIX) {
+    return launch_warp_cfg_th<T, F, D, NPL, G, false, HOPF, MIX>(a, s);
+  } else {
+    return a.theta == 1.0 ? launch_warp_cfg_th<T, F, D, NPL, G, true, HOPF, MIX>(a, s)
+                          : launch_warp_cfg_th<T, F, D, NPL, G, false, HOPF, MIX>(a, s);
+  }
 }
 
 // Every (G, NPL) the library instantiates: FP32 G in {1,2,4,8} x NPL in {1,2};
-// FP64 G in {1,2,4,8} x NPL = 1.
-template <typename T, template <typename, int> class F, int D, bool HOPF>
+// FP64 G in {1,2,4,8} x NPL = 1; the mixed schemes in FP64 stop at G = 4 (their
+// second exchange slot would bring the static shared memory of the FP64 G = 8
+// group to about 75 KB; that instantiation is not built).
+template <typename T, template <typename, int> class F, int D, bool HOPF, bool MIX = false>
 hj_status launch_warp_shape(const SolveArgs<T>& a, WarpConfig c, cudaStream_t s) {
   constexpr bool f64 = sizeof(T) == 8;
   if (c.NPL == 1) {
     switch (c.G) {
-      case 1: return launch_warp_cfg<T, F<T, D>, D, 1, 1, HOPF>(a, s);
-      case 2: return launch_warp_cfg<T, F<T, D>, D, 1, 2, HOPF>(a, s);
-      case 4: return launch_warp_cfg<T, F<T, D>, D, 1, 4, HOPF>(a, s);
-      case 8: return launch_warp_cfg<T, F<T, D>, D, 1, 8, HOPF>(a, s);
+      case 1: return launch_warp_cfg<T, F<T, D>, D, 1, 1, HOPF, MIX>(a, s);
+      case 2: return launch_warp_cfg<T, F<T, D>, D, 1, 2, HOPF, MIX>(a, s);
+      case 4: return launch_warp_cfg<T, F<T, D>, D, 1, 4, HOPF, MIX>(a, s);
+      case 8:
+        if constexpr (f64 && MIX) return HJ_ERR_UNSUPPORTED;
+        else return launch_warp_cfg<T, F<T, D>, D, 1, 8, HOPF, MIX>(a, s);
       default: return HJ_ERR_UNSUPPORTED;
     }
   }
   if constexpr (!f64) {
     if (c.NPL == 2) {
       switch (c.G) {
-        case 1: return launch_warp_cfg<T, F<T, D>, D, 2, 1, HOPF>(a, s);
-        case 2: return launch_warp_cfg<T, F<T, D>, D, 2, 2, HOPF>(a, s);
-        case 4: return launch_warp_cfg<T, F<T, D>, D, 2, 4, HOPF>(a, s);
-        case 8: return launch_warp_cfg<T, F<T, D>, D, 2, 8, HOPF>(a, s);
+        case 1: return launch_warp_cfg<T, F<T, D>, D, 2, 1, HOPF, MIX>(a, s);
+        case 2: return launch_warp_cfg<T, F<T, D>, D, 2, 2, HOPF, MIX>(a, s);
+        case 4: return launch_warp_cfg<T, F<T, D>, D, 2, 4, HOPF, MIX>(a, s);
+        case 8: return launch_warp_cfg<T, F<T, D>, D, 2, 8, HOPF, MIX>(a, s);
         default: return HJ_ERR_UNSUPPORTED;
       }
     }
