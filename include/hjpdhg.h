@@ -185,7 +185,9 @@ typedef struct {
  *   traj_p   (device, may be NULL) [B][N+1][d] out: p_0 (= 0), p_1..p_N
  *            (p_j: the costate of interval [s_{j-1}, s_j], see HJ_SCHEME_*).
  *   warm_x, warm_p (device, may both be NULL) [B][N+1][d] in: initial iterate
- *            instead of the random guess (resume); warm_x[b][N] is ignored
+ *            instead of the random guess (resume from traj_x, traj_p as written,
+ *            so for the negative eikonal equation warm_p is the costate of phi,
+ *            like traj_p); warm_x[b][N] is ignored
  *            (x_N = x) and warm_p[b][0] is ignored (p_0 = 0); Hopf also
  *            ignores warm_x[b][0].
  *   The trajectory and warm-start arrays have the element type of `precision`.

@@ -82,8 +82,9 @@ def make_game(w):
 
 
 def solve_game(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter=None,
-               check_every=None, seed=None, init_radius=None):
-    """Run Algorithm 3 on every query point (x, y) of workload `w` (uniform N).
+               check_every=None, seed=None, init_radius=None, x_init=None, p_init=None):
+    """Run Algorithm 3 on every query point (x, y) of workload `w` (uniform N),
+    from the random initial guess or from (x_init, p_init) as returned.
 
     Returns dict(V, iters, status, x [B, N+1, d] (z = (x, y)), p [B, N+1, d]
     ((p, q); index 0 is 0), rx, rp) like lax_pdhg.solve.
@@ -106,7 +107,13 @@ def solve_game(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter
     B, d = zq.shape
     pidx = w.get("point_index", np.arange(B))
     delta_all = np.asarray(w["t"], dtype=np.float64) / N
-    z_all, P_all = initial_guess(zq, N, seed, radius, pidx)
+    if x_init is None:
+        z_all, P_all = initial_guess(zq, N, seed, radius, pidx)
+    else:                                     # resume from returned iterates
+        z_all = np.array(x_init, dtype=np.float64)
+        P_all = np.array(p_init, dtype=np.float64)
+        z_all[:, N, :] = zq
+        P_all[:, 0, :] = 0.0
     zb_all = z_all.copy()
     iters = np.zeros(B, dtype=np.int64)
     status = np.full(B, MAX_ITER, dtype=np.int64)

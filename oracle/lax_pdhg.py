@@ -97,7 +97,7 @@ def solve(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter=None
         x_all, p_all = initial_guess(xq, N, seed, radius, pidx)
     else:
         x_all = np.array(x_init, dtype=np.float64)
-        p_all = np.array(p_init, dtype=np.float64)
+        p_all = sign * np.array(p_init, dtype=np.float64)    # p_init as returned (phi's costate)
         x_all[:, N, :] = xq
         p_all[:, 0, :] = 0.0
     z_all = x_all.copy()

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(512) lax_eik_kernel(const SolveArgs<T> a, T* w
             if (j >= 1) pv = ig.p(a.seed, pt, j, k);
           } else {
             xv = (j < N) ? a.warm_x[ref.traj + (size_t)j * d + k] : T(xq);
-            if (j >= 1) pv = a.warm_p[ref.traj + (size_t)j * d + k];
+            if (j >= 1) pv = T(a.cost_sign) * a.warm_p[ref.traj + (size_t)j * d + k];
           }
           X[(size_t)j * d + k] = xv;
           P[(size_t)j * d + k] = pv;

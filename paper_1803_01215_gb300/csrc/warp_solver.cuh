@@ -176,7 +176,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
           T xv = T(0), pv = T(0);
           if (j < N) xv = wx[(size_t)j * D + k];
           else if (j == N) xv = T(pt.xq[k]);
-          if (j <= N) pv = wp[(size_t)j * D + k];
+          if (j <= N) pv = T(a.cost_sign) * wp[(size_t)j * D + k];   // traj_p convention
           x[i][k] = xv; p[i][k] = pv; z[i][k] = xv;
         }
       }
