@@ -350,6 +350,41 @@ hj_status hj_ragged_autotune(hj_ragged_plan plan, const double* xq, const double
 /* Destroy a plan (NULL accepted); synchronises its device first.            */
 hj_status hj_ragged_plan_destroy(hj_ragged_plan plan);
 
+/* ---------------------------------------------------------------- retry rounds
+ * The paper's handling of points that reach the iteration cap: Section 6.2
+ * raises sigma by 20 and sets tau = 0.25 / sigma (here: step_product / sigma)
+ * for such game points; Section 6.1 reruns such eikonal points.
+ *   rounds        extra rounds, 0..127 (0: the plain hj_solve_batch).
+ *   sigma_step    round r runs sigma_r = opts->sigma + r * sigma_step.
+ *   step_product  tau_r = step_product / sigma_r; 0 keeps opts->sigma * opts->tau.
+ *   warm          0: round r reruns the point from a fresh random guess drawn
+ *                 with seed + r; 1: it continues from the point's last iterate
+ *                 (z restarts at x).                                          */
+typedef struct {
+  int32_t rounds;
+  double sigma_step;
+  double step_product;
+  int32_t warm;
+} hj_retry_policy;
+
+/* hj_solve_batch, then up to policy->rounds more rounds, each over the points
+ * whose status is still HJ_POINT_MAX_ITER, with that round's sigma, tau and
+ * seed (opts->max_iter iterations per round).  A retried point's outputs are
+ * those of its last round; iters[] is its total over all rounds; rounds[]
+ * (device, may be NULL) [B] int8 out: the last round the point ran in.
+ * traj_x, traj_p may be NULL (with warm = 1 the library then keeps them in a
+ * workspace).  Every round's options must pass the checks of hj_solve_batch
+ * (sigma_r > 0, 4 sigma_r tau_r < 1, ...) or nothing runs.  Allocates a
+ * stream-ordered workspace of 2B int32 (+ 2 or 4 trajectory arrays with
+ * warm = 1) and synchronises `stream` once per extra round (to read how many
+ * points it retries).  The paper's other remedy, switching to a stopping test
+ * on the value after a maximum count, is not provided.
+ * Errors: those of hj_solve_batch, HJ_ERR_OOM.                               */
+hj_status hj_solve_batch_retry(hj_problem prob, int64_t B, const double* xq, const double* t,
+                               int32_t N, const hj_solver_opts* opts, const hj_retry_policy* policy,
+                               double* V, int32_t* iters, int8_t* status, int8_t* rounds,
+                               void* traj_x, void* traj_p, void* stream);
+
 /* ---------------------------------------------------------------- no device allocation
  * hj_solve_batch for callers that cannot allocate device memory: code running
  * under a device-memory budget fixed before it starts (an allocator owned by a

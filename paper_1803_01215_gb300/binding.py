@@ -40,7 +40,7 @@ EXPORTED = ("hj_problem_create", "hj_problem_destroy", "hj_solve_batch",
             "hj_ragged_plan_create", "hj_ragged_plan_layout", "hj_ragged_plan_bucket",
             "hj_ragged_solve", "hj_ragged_autotune", "hj_ragged_plan_destroy",
             "hj_solve_grad", "hj_solve_grad_unrolled", "hj_solve_batch_static",
-            "hj_static_scratch_bytes", "hj_probe_fp32_fma",
+            "hj_static_scratch_bytes", "hj_probe_fp32_fma", "hj_solve_batch_retry",
             "hj_status_str", "hj_version")
 
 
@@ -80,6 +80,9 @@ def _lib():
         lib.hj_solve_grad_unrolled.argtypes = [P, I64, P, P, I32, ctypes.POINTER(SolverOpts), P,
                                                I32, I32, P, P, P, P, P, P]
         lib.hj_solve_grad_unrolled.restype = ctypes.c_int
+        lib.hj_solve_batch_retry.argtypes = [P, I64, P, P, I32, ctypes.POINTER(SolverOpts),
+                                             ctypes.POINTER(RetryPolicy), P, P, P, P, P, P, P]
+        lib.hj_solve_batch_retry.restype = ctypes.c_int
         lib.hj_probe_fp32_fma.argtypes = [I64, I32, ctypes.POINTER(ctypes.c_double), P]
         lib.hj_probe_fp32_fma.restype = ctypes.c_int
         lib.hj_status_str.restype = ctypes.c_char_p
@@ -268,6 +271,40 @@ def solve_batch(problem, xq, t, N, opts, *, return_traj=False, warm_x=None, warm
                               _ptr(warm_x), _ptr(warm_p), ctypes.c_void_p(s.cuda_stream))
     if r != HJ_OK:
         raise HJError(r, "hj_solve_batch")
+    return out
+
+
+class RetryPolicy(ctypes.Structure):
+    """hj_retry_policy: extra rounds for points that reach the iteration cap."""
+    _fields_ = [("rounds", ctypes.c_int32), ("sigma_step", ctypes.c_double),
+                ("step_product", ctypes.c_double), ("warm", ctypes.c_int32)]
+
+
+def solve_batch_retry(problem, xq, t, N, opts, policy, *, return_traj=False, stream=None):
+    """hj_solve_batch_retry on device tensors (as solve_batch); the result also
+    holds `rounds` [B] int8, the last round each point ran in."""
+    if not (xq.is_cuda and t.is_cuda) or xq.dtype != torch.float64 or t.dtype != torch.float64:
+        raise ValueError("xq and t must be float64 CUDA tensors")
+    xq = xq.contiguous()
+    t = t.contiguous()
+    B, d = xq.shape
+    dev = xq.device
+    it_dtype = torch.float32 if opts.precision == 0 else torch.float64
+    out = dict(V=torch.empty(B, dtype=torch.float64, device=dev),
+               iters=torch.empty(B, dtype=torch.int32, device=dev),
+               status=torch.empty(B, dtype=torch.int8, device=dev),
+               rounds=torch.empty(B, dtype=torch.int8, device=dev))
+    if return_traj:
+        out["traj_x"] = torch.empty(B, N + 1, d, dtype=it_dtype, device=dev)
+        out["traj_p"] = torch.empty(B, N + 1, d, dtype=it_dtype, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    r = _lib().hj_solve_batch_retry(problem.handle, B, _ptr(xq), _ptr(t), int(N),
+                                    ctypes.byref(opts), ctypes.byref(policy), _ptr(out["V"]),
+                                    _ptr(out["iters"]), _ptr(out["status"]), _ptr(out["rounds"]),
+                                    _ptr(out.get("traj_x")), _ptr(out.get("traj_p")),
+                                    ctypes.c_void_p(s.cuda_stream))
+    if r != HJ_OK:
+        raise HJError(r, "hj_solve_batch_retry")
     return out
 
 
