@@ -23,6 +23,10 @@ Contents
   lax_schemes  the Lax saddle problem with forward Euler (Eq. disclaxFE) and
                the trapezoid average of the two Euler forms, costates indexed
                by interval as in Eq. disclaxFE, same PDHG steps as lax_pdhg.
+  game_schemes Algorithm 3 with the forward-Euler and trapezoid forms (the
+               averaging Section 7 proposes for the Lax discretisations).
+  retry        rounds for the points that reach the iteration cap (the
+               paper's sigma raise and reruns, Sections 6.1 and 6.2).
   game_pdhg    Algorithm 3 (Lax form for differential games, Eq.
                discgenlaxhopfdg) for Section 6.2's difference-of-norms game:
                shrink_2 dual steps for both players, a descent step for the
@@ -30,7 +34,8 @@ Contents
 
 Pins: see tests/test_oracle_pins.py, tests/test_oracle_hopf_pins.py,
 tests/test_oracle_eikonal_pins.py, tests/test_oracle_game_pins.py and
-tests/test_oracle_schemes_pins.py.  Closed form (quadratic H), discrete
+tests/test_oracle_schemes_pins.py, tests/test_oracle_game_schemes_pins.py
+and tests/test_oracle_retry_pins.py.  Closed form (quadratic H), discrete
 Riccati (linear drift), direct collocation (tanh drift), the discrete
 characteristic (KKT) equations with complex-step derivatives of an H written
 independently from the quadcopter dynamics, the primal/dual value identity, and
