@@ -107,11 +107,13 @@ enum { HJ_FORM_LAX = 0, HJ_FORM_HOPF = 1 };
  * sigma delta (wR H(x_j, .) + wL H(x_{j-1}, .)); x_j (1 <= j < N) takes one
  * gradient step on -delta (wR H(x_j, p_j) + wL H(x_j, p_{j+1})); x_0, on which
  * both g and (for wL > 0) H act, takes one gradient step on -delta wL H(x_0, p_1)
- * followed by the exact prox of g.  FE and TRAP run in the register-resident
- * kernel only (quadcopter, tanh drift d in {2, 4}, eikonal d in {2, 10}; N <= 128
- * in FP64) with the Lax form and inner_steps = 1; the quadratic family, whose H
- * does not depend on x, has the same problem under every scheme.  Other cases
- * return HJ_ERR_UNSUPPORTED.                                                  */
+ * followed by the exact prox of g.  For the game (HJ_FAMILY_GAME_NORMS) the
+ * same weights apply to both players in Algorithm 3's order: the y-block's H
+ * terms, y_0's included, are taken at (x^{k+1}, y^k).  FE and TRAP run in the
+ * register-resident kernel only (quadcopter, tanh drift d in {2, 4}, eikonal
+ * d in {2, 10}, the game d in {2, 7}; N <= 128 in FP64) with the Lax form and
+ * inner_steps = 1; the quadratic family, whose H does not depend on x, has the
+ * same problem under every scheme.  Other cases return HJ_ERR_UNSUPPORTED.   */
 enum { HJ_SCHEME_BE = 0, HJ_SCHEME_FE = 1, HJ_SCHEME_TRAP = 2 };
 
 /* Per-point outcome written to status[].  HJ_POINT_INVALID marks a point whose

@@ -597,11 +597,29 @@ struct FamGame {
 #pragma unroll
     for (int k = 0; k < D; ++k) v[k] *= (k < d1) ? kp : kq;
   }
+  // shrink_2 of both players with the weighted speeds (forward-Euler and
+  // trapezoid schemes): thresholds lam (wr c_i(zr) + wl c_i(zl))
+  __device__ __forceinline__ void prox_mix(const Ctx& cr, const Ctx& cl, const PC& pc, T wr, T wl,
+                                           const T (&)[D], const T (&)[D], T (&v)[D]) const {
+    T np, nq;
+    norms(v, np, nq);
+    const T tp = pc.lam * (wr * cr.c1 + wl * cl.c1), tq = pc.lam * (wr * cr.c2 + wl * cl.c2);
+    const T kp = (np > tp) ? fdiv<T>(np - tp, np) : T(0);
+    const T kq = (nq > tq) ? fdiv<T>(nq - tq, nq) : T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] *= (k < d1) ? kp : kq;
+  }
   // xn holds z - tau (P - P_next) on entry
   __device__ __forceinline__ void game_step(const Ctx& c, const T (&z)[D], const T (&P)[D],
                                             T taud, T (&xn)[D]) const {
     T np, nq;
     norms(P, np, nq);
+    game_step_norms(c, z, np, nq, taud, xn);
+  }
+  // grad_z H(z, P) = |p| grad c1(z) - |q| grad c2(z) is linear in the two norms,
+  // so a weighted sum of gradients over costates is this step with weighted norms
+  __device__ __forceinline__ void game_step_norms(const Ctx& c, const T (&z)[D], T np, T nq,
+                                                  T taud, T (&xn)[D]) const {
     const T f1 = np * c.g1, f2 = nq * c.g2;
 #pragma unroll
     for (int k = 0; k < D; ++k)
@@ -620,6 +638,32 @@ struct FamGame {
                                         T (&g)[D]) const {
 #pragma unroll
     for (int k = 0; k < D; ++k) g[k] = T(0);      // the primal step is game_step
+  }
+  // Node 0 under the mixed schemes, all coordinates: x_0 <- prox of g_x at
+  // x_0 + tau p_1 + tau delta wl d_x H(z_0, P_1), then, at m_0 = (x_0^{k+1}, y_0),
+  // y_0 <- ascent prox of g_y at y_0 + tau q_1 - tau delta wl d_y H(m_0, P_1)
+  // (the prox as offset and reciprocal per coordinate, the maximiser's with -W^2).
+  __device__ __forceinline__ void node0_step_mix(const T (&z0)[D], const T (&P1)[D], T tau,
+                                                 T taudw, const T* goff, const T* ginv,
+                                                 T (&zn)[D]) const {
+    T np, nq;
+    norms(P1, np, nq);
+    Ctx c;
+    context(z0, c);
+    const T f1 = np * c.g1, f2 = nq * c.g2;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const T gx = f1 * (z0[k] - zb[k]) - f2 * (z0[k] + zb[k]);
+      zn[k] = (k < d1) ? (z0[k] + tau * P1[k] + taudw * gx + goff[k]) * ginv[k] : z0[k];
+    }
+    Ctx cm;
+    context(zn, cm);
+    const T h1 = np * cm.g1, h2 = nq * cm.g2;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const T gy = h1 * (zn[k] - zb[k]) - h2 * (zn[k] + zb[k]);
+      if (k >= d1) zn[k] = (z0[k] + tau * P1[k] - taudw * gy + goff[k]) * ginv[k];
+    }
   }
   __device__ __forceinline__ double H64(const T (&z)[D], const T (&P)[D]) const {
     double r1 = 0.0, r2 = 0.0, sp = 0.0, sq = 0.0;

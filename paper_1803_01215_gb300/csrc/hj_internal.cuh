@@ -236,6 +236,8 @@ hj_status launch_warp_tanh_mix(const SolveArgs<T>& a, WarpConfig cfg, cudaStream
 template <typename T>
 hj_status launch_warp_eikonal_mix(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 template <typename T>
+hj_status launch_warp_game_mix(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
+template <typename T>
 hj_status launch_warp_game(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 // Default launch shape for (family, d, Nmax); {0, 0} when no warp kernel fits.
 WarpConfig default_warp_config(int family, int d, int Nmax, bool fp64);

@@ -164,9 +164,9 @@ inline hj_status check_opts(const hj_solver_opts& o) {
 // solved in the Lax form only, and its negative equation's concave x_0 prox
 // needs tau W_i^2 < 1.
 inline hj_status check_formulation(const hj_problem_s* p, const hj_solver_opts& o) {
-  // the forward-Euler and trapezoid forms: Lax form, one gradient step, no game
+  // the forward-Euler and trapezoid forms: Lax form, one gradient step
   if (o.scheme != HJ_SCHEME_BE && p->family != HJ_FAMILY_QUADRATIC &&
-      (o.formulation != HJ_FORM_LAX || o.inner_steps != 1 || p->family == HJ_FAMILY_GAME_NORMS))
+      (o.formulation != HJ_FORM_LAX || o.inner_steps != 1))
     return HJ_ERR_UNSUPPORTED;
   if (o.formulation == HJ_FORM_HOPF && p->family == HJ_FAMILY_EIKONAL) return HJ_ERR_UNSUPPORTED;
   if (o.formulation == HJ_FORM_HOPF && !p->w_nonzero) return HJ_ERR_INVALID_ARG;

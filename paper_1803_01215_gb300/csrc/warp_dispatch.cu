@@ -46,6 +46,7 @@ hj_status launch_warp_solver(int family, const SolveArgs<T>& a, WarpConfig cfg, 
       case HJ_FAMILY_QUADCOPTER: return launch_warp_quadcopter_mix<T>(a, cfg, s);
       case HJ_FAMILY_TANH_DRIFT: return launch_warp_tanh_mix<T>(a, cfg, s);
       case HJ_FAMILY_EIKONAL: return launch_warp_eikonal_mix<T>(a, cfg, s);
+      case HJ_FAMILY_GAME_NORMS: return launch_warp_game_mix<T>(a, cfg, s);
       default: return HJ_ERR_UNSUPPORTED;
     }
   }

@@ -125,7 +125,7 @@ __device__ __forceinline__ T relax(T xn, T xo, T th) {
 template <typename T, class F, int D, int NPL, int G, bool TH1, bool HOPF, bool MIX>
 __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam, int64_t item,
                                             int lane, int wg, WarpShared<T, F, D, G, MIX>& sh) {
-  static_assert(!(MIX && (HOPF || F::kGame)), "the mixed schemes are Lax-form control problems");
+  static_assert(!(MIX && HOPF), "the mixed schemes are Lax-form problems");
   const PointRef<T> pt = point_ref(a, item);
   const int N = pt.N;
   const int gl = wg * 32 + lane;
@@ -253,20 +253,31 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     }
     if (own0 && !HOPF) {
       // x_0 <- prox_{tau g}(x_0 + tau p_1), coordinate k0; p_1 is lane 0's slot
-      T v0 = x0 + tau * pslot[k0];                            // (D^T p)_0 = -p_1
-      if constexpr (MIX) {
-        // + tau delta wL grad_x H(x_0^k, p_1): the whole gradient, coordinate k0 kept
-        T p1[D], g0[D];
+      T xn;
+      if constexpr (MIX && F::kGame) {
+        // the whole node-0 step in every x_0 lane (the y-block needs all of x_0^{k+1})
+        T p1[D], zn0[D];
         slot_load<T, D>(pslot, p1);
-        typename F::Ctx c0;
-        fam.context(x0v, c0);
-        fam.gradx(c0, x0v, p1, g0);
-        T gk = T(0);
+        fam.node0_step_mix(x0v, p1, tau, taud * wl, sh.g_off, sh.g_inv, zn0);
+        xn = T(0);
 #pragma unroll
-        for (int k = 0; k < D; ++k) gk = (k == k0) ? g0[k] : gk;
-        v0 += taud * wl * gk;
+        for (int k = 0; k < D; ++k) xn = (k == k0) ? zn0[k] : xn;
+      } else {
+        T v0 = x0 + tau * pslot[k0];                          // (D^T p)_0 = -p_1
+        if constexpr (MIX) {
+          // + tau delta wL grad_x H(x_0^k, p_1): the whole gradient, coordinate k0 kept
+          T p1[D], g0[D];
+          slot_load<T, D>(pslot, p1);
+          typename F::Ctx c0;
+          fam.context(x0v, c0);
+          fam.gradx(c0, x0v, p1, g0);
+          T gk = T(0);
+#pragma unroll
+          for (int k = 0; k < D; ++k) gk = (k == k0) ? g0[k] : gk;
+          v0 += taud * wl * gk;
+        }
+        xn = (v0 + goff) * ginv;
       }
-      const T xn = (v0 + goff) * ginv;
       if constexpr (CHK) { const T e = xn - x0; rx += e * e; }
       z0 = relax<T, TH1>(xn, x0, th);
       x0 = xn;
@@ -280,7 +291,14 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         if (i == NPL - 1) v_sub<T, D>(dp, p[i], pr);
         else v_sub<T, D>(dp, p[i], p[i + 1 < NPL ? i + 1 : i]);
         v_fma<T, D>(xn, -tau, dp, x[i]);                     // x - tau (p_j - p_{j+1})
-        if constexpr (F::kGame) {
+        if constexpr (F::kGame && MIX) {
+          // norms of the two costates weighted: wR at P_j, wL at P_{j+1}
+          T np1, nq1, np2, nq2;
+          fam.norms(p[i], np1, nq1);
+          if (i == NPL - 1) fam.norms(pr, np2, nq2);
+          else fam.norms(p[i + 1 < NPL ? i + 1 : i], np2, nq2);
+          fam.game_step_norms(ctx[i], x[i], wr * np1 + wl * np2, wr * nq1 + wl * nq2, taud, xn);
+        } else if constexpr (F::kGame) {
           fam.game_step(ctx[i], x[i], p[i], taud, xn);      // descent in x, ascent in y
         } else if constexpr (MIX) {
           // + tau delta (wR grad_x H(x_j, p_j) + wL grad_x H(x_j, p_{j+1}))

@@ -15,6 +15,7 @@ import pytest
 
 from gpu_common import CONVERGED_TOL, gpu, value_err
 from oracle import lax_pdhg as O
+from oracle import game_schemes as GS
 from oracle import lax_schemes as S
 from paper_1803_01215_gb300 import workloads as W
 from test_parity_gpu import _custom
@@ -31,15 +32,21 @@ def _eik(d, sign, N, B, seed=71):
 
 
 # every launch shape the mixed kernels have: FP32 NPL 1/2 with G 1/2 (N = 23,
-# 64, 100), FP64 G 1/2/4 (N = 23, 64, 100, 128), ragged tails; the three families
+# 64, 100), FP64 G 1/2/4 (N = 23, 64, 100, 128), ragged tails; the four families
 CASES = [
     ("quadcopter", 12, 23), ("quadcopter", 12, 64), ("quadcopter", 12, 100),
     ("tanh_drift", 4, 50), ("tanh_drift", 2, 128),
     ("eikonal+", 2, 5), ("eikonal+", 10, 30), ("eikonal-", 2, 10),
+    ("game", 2, 5), ("game", 2, 23), ("game", 7, 10),
 ]
 
 
 def _case(family, d, N, B, seed=21):
+    if family == "game":
+        w = W.game_norms(d=d, B=B, seed=seed)
+        w["N"] = N
+        w["t"] = np.full(B, N * W.EIK_DELTA)
+        return w
     if family.startswith("eikonal"):
         return _eik(d, 1 if family.endswith("+") else -1, N, B, seed=seed)
     return _custom(family, d, N, B, seed=seed)
@@ -59,7 +66,8 @@ def test_scheme_fixed_iterations_elementwise(family, d, N, scheme, precision):
     w = _case(family, d, N, B=37)
     K = 150
     g = gpu(w, precision, tol=0.0, max_iter=K, check_every=K, scheme=scheme)
-    o = S.solve_scheme(w, scheme, tol=0.0, max_iter=K, check_every=K)
+    solve = GS.solve_game_scheme if family == "game" else S.solve_scheme
+    o = solve(w, scheme, tol=0.0, max_iter=K, check_every=K)
     assert np.all(g["iters"] == K) and np.all(g["status"] == O.MAX_ITER)
     ex, ep, ev = _cmp(g, o)
     print(f"{scheme} {family} d={d} N={N} {precision}: |dx| {ex:.2e} |dp| {ep:.2e} V {ev:.2e}")
@@ -87,6 +95,19 @@ def test_scheme_fp64_same_stop_and_fp32_value(family, d, N, B, scheme):
     ok = (oc["status"] == O.CONVERGED) & (g32["status"] == O.CONVERGED)
     assert np.mean(ok) >= 0.9
     assert value_err(g32["V"][ok], oc["V"][ok]).max() <= 1e-4
+
+
+@pytest.mark.parametrize("d", [2, 7])
+@pytest.mark.parametrize("scheme", ["fe", "trap"])
+def test_game_scheme_fp64_same_stop(d, scheme):
+    w = _case("game", d, 5, 24, seed=62)
+    o = GS.solve_game_scheme(w, scheme)
+    g = gpu(w, "fp64", scheme=scheme)
+    conv = o["status"] == O.CONVERGED
+    assert np.mean(conv) >= 0.8
+    same = (g["iters"] == o["iters"]) & conv
+    assert np.mean(same) >= 0.7
+    assert value_err(g["V"][same], o["V"][same]).max() <= 1e-9
 
 
 def test_quadratic_family_is_scheme_independent():
@@ -180,18 +201,12 @@ def test_scheme_argument_errors():
     with pytest.raises(binding.HJError) as e:
         binding.solve_batch(prob, xq, t, 8, bad)
     assert e.value.code == 1                                       # HJ_ERR_INVALID_ARG
-    # no mixed kernel for the shared-memory tanh drift sizes or the game
+    # no mixed kernel for the shared-memory tanh drift sizes
     wt = _custom("tanh_drift", 8, 8, B=3)
     pt = binding.Problem.from_workload(wt)
     xt = torch.as_tensor(wt["xq"], device="cuda")
     with pytest.raises(binding.HJError) as e:
         binding.solve_batch(pt, xt, t, 8, binding.make_opts(sigma=1.0, tau=0.24, scheme="trap"))
-    assert e.value.code == 2
-    wg = W.game_norms(d=2, B=3)
-    pg = binding.Problem.from_workload(wg)
-    xg = torch.as_tensor(wg["xq"], device="cuda")
-    with pytest.raises(binding.HJError) as e:
-        binding.solve_batch(pg, xg, t, 5, binding.make_opts(sigma=50.0, tau=0.0048, scheme="fe"))
     assert e.value.code == 2
     # the reverse sweep differentiates the backward-Euler iteration only
     fe = binding.make_opts(sigma=1.0, tau=0.24, scheme="fe", precision="fp64")
