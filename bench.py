@@ -146,14 +146,18 @@ def _events_time(fn, steps, warmup, flush, stream, tag):
     return tot / steps
 
 
-def measure_other_configs(dev, flush, stream, peak):
+def measure_other_configs(dev, flush, stream, peak, only=None):
     """The remaining workloads of the hot path, each timed like the headline:
     the d = 2 closed-form batch (FP64), the tanh-drift scaling batches (FP32, and
-    FP64 on a 2048-point slice), the 100 000-point ragged batch (one graph
-    launch) and the adjoint of the 12-D batch."""
+    FP64 on a 2048-point slice), the Hopf form and the forward-Euler / trapezoid
+    schemes of the 12-D batch, the eikonal scaling study, the game grids, the
+    100 000-point ragged batch (one graph launch) and the adjoint of the 12-D
+    batch.  `only`: a comma list of row names to run instead of all."""
     import torch
     from paper_1803_01215_gb300 import binding
     out = {}
+    rows = None if not only else set(only.split(","))
+    want = lambda name: rows is None or name in rows      # noqa: E731
 
     def run_uniform(w, precision, tag, npts=None, formulation="lax", tune=False, scheme="be",
                     tol=None):
@@ -176,177 +180,185 @@ def measure_other_configs(dev, flush, stream, peak):
         iters = int(res["iters"].to(torch.int64).sum().item())
         return ms, conv, iters, res
 
-    w1 = W.quadratic_closed_form()
-    ms, conv, _, res = run_uniform(w1, "fp64", "timed_quadratic_d2")
-    exact = torch.as_tensor((w1["xq"] ** 2).sum(1) / (2 * (1 + w1["t"])), device=dev)
-    out["quadratic_d2_B64_N20_fp64"] = {
-        "solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
-        "max_abs_err_vs_closed_form": float((res["V"] - exact).abs().max().item())}
+    if want("quadratic"):
+        w1 = W.quadratic_closed_form()
+        ms, conv, _, res = run_uniform(w1, "fp64", "timed_quadratic_d2")
+        exact = torch.as_tensor((w1["xq"] ** 2).sum(1) / (2 * (1 + w1["t"])), device=dev)
+        out["quadratic_d2_B64_N20_fp64"] = {
+            "solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
+            "max_abs_err_vs_closed_form": float((res["V"] - exact).abs().max().item())}
 
-    for d, seed in ((32, 3), (64, 4), (100, 5)):
-        w = W.tanh_drift(d, seed=seed)
-        ms, conv, iters, _ = run_uniform(w, "fp32", f"timed_tanh_d{d}")
-        flops = iters * 32 * (4 * d * d + 14 * d)
-        ms64, conv64, _, _ = run_uniform(w, "fp64", f"timed_tanh_d{d}_fp64", npts=2048)
-        out[f"tanh_drift_d{d}_B16384_N32"] = {
-            "fp32": {"solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
-                     "tflops": flops / (ms * 1e-3) / 1e12,
-                     "frac_of_fp32_peak": flops / (ms * 1e-3) / 1e12 / peak},
-            "fp64_2048_points": {"solves_per_s": conv64 / (ms64 * 1e-3), "ms_per_step": ms64,
-                                 "converged": conv64},
-            "fp32_over_fp64": (conv / ms) / (conv64 / ms64) if conv64 else None}
+    if want("tanh"):
+        for d, seed in ((32, 3), (64, 4), (100, 5)):
+            w = W.tanh_drift(d, seed=seed)
+            ms, conv, iters, _ = run_uniform(w, "fp32", f"timed_tanh_d{d}")
+            flops = iters * 32 * (4 * d * d + 14 * d)
+            ms64, conv64, _, _ = run_uniform(w, "fp64", f"timed_tanh_d{d}_fp64", npts=2048)
+            out[f"tanh_drift_d{d}_B16384_N32"] = {
+                "fp32": {"solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
+                         "tflops": flops / (ms * 1e-3) / 1e12,
+                         "frac_of_fp32_peak": flops / (ms * 1e-3) / 1e12 / peak},
+                "fp64_2048_points": {"solves_per_s": conv64 / (ms64 * 1e-3), "ms_per_step": ms64,
+                                     "converged": conv64},
+                "fp32_over_fp64": (conv / ms) / (conv64 / ms64) if conv64 else None}
 
-    # the Hopf form (Algorithm 2) on the 12-D workload, autotuned launch shape;
-    # a solve counts when converged and within 1e-4 of the FP64 Hopf value
-    wqh = W.quadcopter()
-    ms, conv, iters, r32 = run_uniform(wqh, "fp32", "timed_hopf_qc", formulation="hopf", tune=True)
-    ms64, conv64, _, r64 = run_uniform(wqh, "fp64", "timed_hopf_qc_fp64", formulation="hopf",
-                                       tune=True)
-    ok = ((r32["status"] == 0) & (r64["status"] == 0)
-          & ((r32["V"] - r64["V"]).abs() <= 1e-4 * r64["V"].abs().clamp_min(1.0)))
-    n_ok = int(ok.sum().item())
-    flops = iters * 64 * QC_FLOPS_PER_NODE_ITER
-    out["hopf_quadcopter12d_B4096_N64"] = {
-        "fp32": {"solves_per_s": n_ok / (ms * 1e-3), "ms_per_step": ms, "converged_accurate": n_ok,
-                 "tflops": flops / (ms * 1e-3) / 1e12,
-                 "frac_of_fp32_peak": flops / (ms * 1e-3) / 1e12 / peak},
-        "fp64": {"solves_per_s": conv64 / (ms64 * 1e-3), "ms_per_step": ms64, "converged": conv64},
-        "fp32_over_fp64": (n_ok / ms) / (conv64 / ms64) if conv64 else None,
-        "note": "trajectories written (the headline step writes V and status only)"}
-
-    # The forward-Euler (Eq. disclaxFE) and trapezoid schemes on the 12-D workload:
-    # throughput (FP32, a solve counts when converged and within 1e-4 of the FP64
-    # value of the same scheme), and the discretisation error of each scheme on
-    # a 256-point slice (FP64, tight stop) against the Richardson extrapolation
-    # (4 V_trap(128) - V_trap(64)) / 3 of the second-order trapezoid values.
-    sch = {}
-    wq = W.quadcopter()
-    for scheme in ("fe", "trap"):
-        ms, conv, iters, r32 = run_uniform(wq, "fp32", f"timed_{scheme}_qc", scheme=scheme)
-        ms64, conv64, _, r64 = run_uniform(wq, "fp64", f"timed_{scheme}_qc_fp64", scheme=scheme)
+    if want("hopf"):
+        # the Hopf form (Algorithm 2) on the 12-D workload, autotuned launch shape;
+        # a solve counts when converged and within 1e-4 of the FP64 Hopf value
+        wqh = W.quadcopter()
+        ms, conv, iters, r32 = run_uniform(wqh, "fp32", "timed_hopf_qc", formulation="hopf", tune=True)
+        ms64, conv64, _, r64 = run_uniform(wqh, "fp64", "timed_hopf_qc_fp64", formulation="hopf",
+                                           tune=True)
         ok = ((r32["status"] == 0) & (r64["status"] == 0)
               & ((r32["V"] - r64["V"]).abs() <= 1e-4 * r64["V"].abs().clamp_min(1.0)))
         n_ok = int(ok.sum().item())
-        sch[scheme] = {"fp32": {"solves_per_s": n_ok / (ms * 1e-3), "ms_per_step": ms,
-                                "converged_accurate": n_ok, "mean_iters": iters / len(wq["xq"])},
-                       "fp64": {"solves_per_s": conv64 / (ms64 * 1e-3), "ms_per_step": ms64,
-                                "converged": conv64}}
-    acc = {}
-    for scheme, N in (("be", 64), ("fe", 64), ("trap", 32), ("trap", 64), ("trap", 128)):
-        wa = dict(W.subset(wq, np.arange(256)), N=N, max_iter=400000)
-        _, conv, _, ra = run_uniform(wa, "fp64", f"acc_{scheme}_{N}", scheme=scheme, tol=1e-18)
-        acc[(scheme, N)] = ra["V"].double().cpu().numpy()
-    vref = (4.0 * acc[("trap", 128)] - acc[("trap", 64)]) / 3.0
-    sch["discretisation_error_256_points_fp64"] = {
-        f"{k[0]}_N{k[1]}": {"median_abs": float(np.median(np.abs(v - vref))),
-                            "max_abs": float(np.max(np.abs(v - vref)))}
-        for k, v in acc.items() if k != ("trap", 128)}
-    out["schemes_quadcopter12d_B4096_N64"] = sch
+        flops = iters * 64 * QC_FLOPS_PER_NODE_ITER
+        out["hopf_quadcopter12d_B4096_N64"] = {
+            "fp32": {"solves_per_s": n_ok / (ms * 1e-3), "ms_per_step": ms, "converged_accurate": n_ok,
+                     "tflops": flops / (ms * 1e-3) / 1e12,
+                     "frac_of_fp32_peak": flops / (ms * 1e-3) / 1e12 / peak},
+            "fp64": {"solves_per_s": conv64 / (ms64 * 1e-3), "ms_per_step": ms64, "converged": conv64},
+            "fp32_over_fp64": (n_ok / ms) / (conv64 / ms64) if conv64 else None,
+            "note": "trajectories written (the headline step writes V and status only)"}
 
-    # Section 6.1's dimensional scaling: the negative eikonal equation at t = 0.2
-    # (delta = 0.02, N = 10, sigma = 100) on the 2-D slice grid [-3, 3]^2 (mesh
-    # 0.1, 3721 points) embedded in d dimensions, FP32.  Algorithmic flops per
-    # (node, coordinate, iteration): 20 (the two node sums 8, dual step 4, x-step 6,
-    # relaxation 2); the paper's own fit of its single-core C++ time per point,
-    # 1.14e-4 d + 0.0021 s, is context only.
-    eik = {}
-    for d in (10, 100, 1000, 2000):
-        we = W.eikonal(d=d, sign=-1, t=0.2)
-        ms, conv, iters, _ = run_uniform(we, "fp32", f"timed_eikonal_d{d}")
-        flops = iters * 10 * d * 20
-        eik[f"d{d}"] = {"solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
-                        "points": len(we["xq"]), "mean_iters": iters / len(we["xq"]),
-                        "tflops": flops / (ms * 1e-3) / 1e12,
-                        "paper_cpu_fit_s_per_point": 1.14e-4 * d + 0.0021}
-    out["eikonal_negative_t0.2_slice3721_fp32"] = eik
+    if want("schemes"):
+        # The forward-Euler (Eq. disclaxFE) and trapezoid schemes on the 12-D workload:
+        # throughput (FP32, a solve counts when converged and within 1e-4 of the FP64
+        # value of the same scheme), and the discretisation error of each scheme on
+        # a 256-point slice (FP64, tight stop) against the Richardson extrapolation
+        # (4 V_trap(128) - V_trap(64)) / 3 of the second-order trapezoid values.
+        sch = {}
+        wq = W.quadcopter()
+        for scheme in ("fe", "trap"):
+            ms, conv, iters, r32 = run_uniform(wq, "fp32", f"timed_{scheme}_qc", scheme=scheme)
+            ms64, conv64, _, r64 = run_uniform(wq, "fp64", f"timed_{scheme}_qc_fp64", scheme=scheme)
+            ok = ((r32["status"] == 0) & (r64["status"] == 0)
+                  & ((r32["V"] - r64["V"]).abs() <= 1e-4 * r64["V"].abs().clamp_min(1.0)))
+            n_ok = int(ok.sum().item())
+            sch[scheme] = {"fp32": {"solves_per_s": n_ok / (ms * 1e-3), "ms_per_step": ms,
+                                    "converged_accurate": n_ok, "mean_iters": iters / len(wq["xq"])},
+                           "fp64": {"solves_per_s": conv64 / (ms64 * 1e-3), "ms_per_step": ms64,
+                                    "converged": conv64}}
+        acc = {}
+        for scheme, N in (("be", 64), ("fe", 64), ("trap", 32), ("trap", 64), ("trap", 128)):
+            wa = dict(W.subset(wq, np.arange(256)), N=N, max_iter=400000)
+            _, conv, _, ra = run_uniform(wa, "fp64", f"acc_{scheme}_{N}", scheme=scheme, tol=1e-18)
+            acc[(scheme, N)] = ra["V"].double().cpu().numpy()
+        vref = (4.0 * acc[("trap", 128)] - acc[("trap", 64)]) / 3.0
+        sch["discretisation_error_256_points_fp64"] = {
+            f"{k[0]}_N{k[1]}": {"median_abs": float(np.median(np.abs(v - vref))),
+                                "max_abs": float(np.max(np.abs(v - vref)))}
+            for k, v in acc.items() if k != ("trap", 128)}
+        out["schemes_quadcopter12d_B4096_N64"] = sch
 
-    # Section 6.2's difference-of-norms game, 2-D and its 7-D slice, on the
-    # paper's grid [-3, 3]^2 (mesh 1/12, 5329 points), sigma = 50, FP32.  The
-    # paper raises sigma for points that reach the iteration cap; here they are
-    # counted, not retried.  Its per-point C++ times (0.0135 s in 2-D, 0.0159 s
-    # in 7-D, averaged over t) are context only.
-    game = {}
-    for d in (2, 7):
-        for t_g in (0.1, 0.2, 0.3):
-            wg = W.game_norms(d=d, t=t_g)
-            ms, conv, iters, _ = run_uniform(wg, "fp32", f"timed_game_d{d}_t{t_g}")
-            game[f"d{d}_t{t_g}"] = {"solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms,
-                                    "converged": conv, "points": len(wg["xq"]),
-                                    "mean_iters": iters / len(wg["xq"]),
-                                    "paper_cpu_s_per_point": 0.0135 if d == 2 else 0.01587}
-    # the paper's remedy for the points that reach the cap (raise sigma by 20,
-    # tau = 0.24 / sigma, rerun; up to three raises), timed over all rounds
-    for d in (2, 7):
-        wg = W.game_norms(d=d, t=0.3)
-        prob = binding.Problem.from_workload(wg)
-        gopts = binding.make_opts(sigma=wg["sigma"], tau=wg["tau"], tol=wg["tol"],
-                                  max_iter=wg["max_iter"], check_every=wg["check_every"],
-                                  seed=wg["seed"], init_radius=wg["init_radius"])
-        pol = binding.RetryPolicy(3, 20.0, 0.24, 0)
-        xq = torch.as_tensor(wg["xq"], device=dev)
-        t = torch.as_tensor(wg["t"], device=dev)
-        res = binding.solve_batch_retry(prob, xq, t, int(wg["N"]), gopts, pol)
-        ms = _events_time(lambda: binding.solve_batch_retry(prob, xq, t, int(wg["N"]), gopts, pol,
-                                                            stream=stream),
-                          2, 1, flush, stream, f"timed_game_retry_d{d}")
+    if want("eikonal"):
+        # Section 6.1's dimensional scaling: the negative eikonal equation at t = 0.2
+        # (delta = 0.02, N = 10, sigma = 100) on the 2-D slice grid [-3, 3]^2 (mesh
+        # 0.1, 3721 points) embedded in d dimensions, FP32.  Algorithmic flops per
+        # (node, coordinate, iteration): 20 (the two node sums 8, dual step 4, x-step 6,
+        # relaxation 2); the paper's own fit of its single-core C++ time per point,
+        # 1.14e-4 d + 0.0021 s, is context only.
+        eik = {}
+        for d in (10, 100, 1000, 2000):
+            we = W.eikonal(d=d, sign=-1, t=0.2)
+            ms, conv, iters, _ = run_uniform(we, "fp32", f"timed_eikonal_d{d}")
+            flops = iters * 10 * d * 20
+            eik[f"d{d}"] = {"solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
+                            "points": len(we["xq"]), "mean_iters": iters / len(we["xq"]),
+                            "tflops": flops / (ms * 1e-3) / 1e12,
+                            "paper_cpu_fit_s_per_point": 1.14e-4 * d + 0.0021}
+        out["eikonal_negative_t0.2_slice3721_fp32"] = eik
+
+    if want("game"):
+        # Section 6.2's difference-of-norms game, 2-D and its 7-D slice, on the
+        # paper's grid [-3, 3]^2 (mesh 1/12, 5329 points), sigma = 50, FP32.  The
+        # paper raises sigma for points that reach the iteration cap; here they are
+        # counted, not retried.  Its per-point C++ times (0.0135 s in 2-D, 0.0159 s
+        # in 7-D, averaged over t) are context only.
+        game = {}
+        for d in (2, 7):
+            for t_g in (0.1, 0.2, 0.3):
+                wg = W.game_norms(d=d, t=t_g)
+                ms, conv, iters, _ = run_uniform(wg, "fp32", f"timed_game_d{d}_t{t_g}")
+                game[f"d{d}_t{t_g}"] = {"solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms,
+                                        "converged": conv, "points": len(wg["xq"]),
+                                        "mean_iters": iters / len(wg["xq"]),
+                                        "paper_cpu_s_per_point": 0.0135 if d == 2 else 0.01587}
+        # the paper's remedy for the points that reach the cap (raise sigma by 20,
+        # tau = 0.24 / sigma, rerun; up to three raises), timed over all rounds
+        for d in (2, 7):
+            wg = W.game_norms(d=d, t=0.3)
+            prob = binding.Problem.from_workload(wg)
+            gopts = binding.make_opts(sigma=wg["sigma"], tau=wg["tau"], tol=wg["tol"],
+                                      max_iter=wg["max_iter"], check_every=wg["check_every"],
+                                      seed=wg["seed"], init_radius=wg["init_radius"])
+            pol = binding.RetryPolicy(3, 20.0, 0.24, 0)
+            xq = torch.as_tensor(wg["xq"], device=dev)
+            t = torch.as_tensor(wg["t"], device=dev)
+            res = binding.solve_batch_retry(prob, xq, t, int(wg["N"]), gopts, pol)
+            ms = _events_time(lambda: binding.solve_batch_retry(prob, xq, t, int(wg["N"]), gopts, pol,
+                                                                stream=stream),
+                              2, 1, flush, stream, f"timed_game_retry_d{d}")
+            conv = int((res["status"] == 0).sum().item())
+            game[f"d{d}_t0.3_sigma_raise"] = {
+                "solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
+                "points": len(wg["xq"]),
+                "retried": int((res["rounds"] > 0).sum().item()),
+                "policy": "up to 3 rounds, sigma + 20 per round, tau = 0.24 / sigma, fresh guess"}
+        out["game_norms_slice5329_fp32"] = game
+
+    if want("ragged"):
+        rw = W.ragged_mix()
+        probs = [binding.Problem.from_workload(p) for p in rw["problems"]]
+        ropts = binding.make_opts(sigma=rw["sigma"], tau=rw["tau"], tol=rw["tol"],
+                                  max_iter=rw["max_iter"], check_every=rw["check_every"], seed=rw["seed"])
+        plan = binding.RaggedPlan(probs, rw["prob_of"], rw["N_of"], ropts)
+        xq = torch.as_tensor(plan.pack_xq(rw["xq"]), device=dev)
+        t = torch.as_tensor(rw["t"], device=dev)
+        plan.autotune(xq, t, repeats=1)
+        res = plan.solve(xq, t, return_traj=True)
+        ms = _events_time(lambda: plan.solve(xq, t, out=res, stream=stream), 2, 1, flush, stream,
+                          "timed_ragged")
         conv = int((res["status"] == 0).sum().item())
-        game[f"d{d}_t0.3_sigma_raise"] = {
+        out["ragged_B100000_d4_12_32_N16_256"] = {
             "solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
-            "points": len(wg["xq"]),
-            "retried": int((res["rounds"] > 0).sum().item()),
-            "policy": "up to 3 rounds, sigma + 20 per round, tau = 0.24 / sigma, fresh guess"}
-    out["game_norms_slice5329_fp32"] = game
+            "graph_launches_per_step": 1, "buckets": len(plan.buckets())}
 
-    rw = W.ragged_mix()
-    probs = [binding.Problem.from_workload(p) for p in rw["problems"]]
-    ropts = binding.make_opts(sigma=rw["sigma"], tau=rw["tau"], tol=rw["tol"],
-                              max_iter=rw["max_iter"], check_every=rw["check_every"], seed=rw["seed"])
-    plan = binding.RaggedPlan(probs, rw["prob_of"], rw["N_of"], ropts)
-    xq = torch.as_tensor(plan.pack_xq(rw["xq"]), device=dev)
-    t = torch.as_tensor(rw["t"], device=dev)
-    plan.autotune(xq, t, repeats=1)
-    res = plan.solve(xq, t, return_traj=True)
-    ms = _events_time(lambda: plan.solve(xq, t, out=res, stream=stream), 2, 1, flush, stream,
-                      "timed_ragged")
-    conv = int((res["status"] == 0).sum().item())
-    out["ragged_B100000_d4_12_32_N16_256"] = {
-        "solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms, "converged": conv,
-        "graph_launches_per_step": 1, "buckets": len(plan.buckets())}
-
-    wq = W.quadcopter()
-    prob = binding.Problem.from_workload(wq)
-    opts = binding.make_opts(sigma=wq["sigma"], tau=wq["tau"], tol=wq["tol"],
-                             max_iter=wq["max_iter"], check_every=wq["check_every"], seed=wq["seed"])
-    xq = torch.as_tensor(wq["xq"], device=dev)
-    t = torch.as_tensor(wq["t"], device=dev)
-    B = len(wq["xq"])
-    wts = torch.full((B,), 1.0 / B, dtype=torch.float64, device=dev)
-    res = binding.solve_batch(prob, xq, t, 64, opts, return_traj=True)
-    g_ms = _events_time(lambda: binding.solve_grad(prob, t, 64, "fp32", res["traj_x"], res["traj_p"],
-                                                   wts, stream=stream), 3, 1, flush, stream,
-                        "timed_grad")
-    both = _events_time(lambda: (binding.solve_batch(prob, xq, t, 64, opts, out=res, stream=stream),
-                                 binding.solve_grad(prob, t, 64, "fp32", res["traj_x"], res["traj_p"],
-                                                    wts, stream=stream)), 2, 1, flush, stream,
-                        "timed_solve_grad")
-    traj_bytes = 2 * B * 65 * 12 * 4
-    # the reverse sweep through the iterations each point ran, checkpoints every 32
-    binding.solve_batch(prob, xq, t, 64, opts, out=res, stream=stream)
-    kmax = int(res["iters"].max().item())
-    ge = binding.solve_grad(prob, t, 64, "fp32", res["traj_x"], res["traj_p"], wts, stream=stream)
-    gu = binding.solve_grad_unrolled(prob, xq, t, 64, opts, res["iters"], wts, checkpoint_every=32,
-                                     max_iters=kmax, stream=stream)
-    agree = max(float((gu[k] - ge[k]).abs().max() / ge[k].abs().max().clamp_min(1.0))
-                for k in ("dW", "ddyn", "dxq"))
-    u_ms = _events_time(lambda: binding.solve_grad_unrolled(prob, xq, t, 64, opts, res["iters"], wts,
-                                                            checkpoint_every=32, max_iters=kmax,
-                                                            stream=stream),
-                        2, 1, flush, stream, "timed_grad_unrolled")
-    out["adjoint_quadcopter_B4096_N64"] = {
-        "value_and_grad_per_s": B / (both * 1e-3), "ms_solve_plus_grad": both,
-        "ms_grad_kernel": g_ms, "grad_kernel_gbs": traj_bytes / (g_ms * 1e-3) / 1e9,
-        "ms_grad_unrolled_ckpt32": u_ms, "grad_unrolled_per_s": B / (u_ms * 1e-3),
-        "unrolled_vs_envelope_max_rel": agree, "max_iters": kmax}
+    if want("adjoint"):
+        wq = W.quadcopter()
+        prob = binding.Problem.from_workload(wq)
+        opts = binding.make_opts(sigma=wq["sigma"], tau=wq["tau"], tol=wq["tol"],
+                                 max_iter=wq["max_iter"], check_every=wq["check_every"], seed=wq["seed"])
+        xq = torch.as_tensor(wq["xq"], device=dev)
+        t = torch.as_tensor(wq["t"], device=dev)
+        B = len(wq["xq"])
+        wts = torch.full((B,), 1.0 / B, dtype=torch.float64, device=dev)
+        res = binding.solve_batch(prob, xq, t, 64, opts, return_traj=True)
+        g_ms = _events_time(lambda: binding.solve_grad(prob, t, 64, "fp32", res["traj_x"], res["traj_p"],
+                                                       wts, stream=stream), 3, 1, flush, stream,
+                            "timed_grad")
+        both = _events_time(lambda: (binding.solve_batch(prob, xq, t, 64, opts, out=res, stream=stream),
+                                     binding.solve_grad(prob, t, 64, "fp32", res["traj_x"], res["traj_p"],
+                                                        wts, stream=stream)), 2, 1, flush, stream,
+                            "timed_solve_grad")
+        traj_bytes = 2 * B * 65 * 12 * 4
+        # the reverse sweep through the iterations each point ran, checkpoints every 32
+        binding.solve_batch(prob, xq, t, 64, opts, out=res, stream=stream)
+        kmax = int(res["iters"].max().item())
+        ge = binding.solve_grad(prob, t, 64, "fp32", res["traj_x"], res["traj_p"], wts, stream=stream)
+        gu = binding.solve_grad_unrolled(prob, xq, t, 64, opts, res["iters"], wts, checkpoint_every=32,
+                                         max_iters=kmax, stream=stream)
+        agree = max(float((gu[k] - ge[k]).abs().max() / ge[k].abs().max().clamp_min(1.0))
+                    for k in ("dW", "ddyn", "dxq"))
+        u_ms = _events_time(lambda: binding.solve_grad_unrolled(prob, xq, t, 64, opts, res["iters"], wts,
+                                                                checkpoint_every=32, max_iters=kmax,
+                                                                stream=stream),
+                            2, 1, flush, stream, "timed_grad_unrolled")
+        out["adjoint_quadcopter_B4096_N64"] = {
+            "value_and_grad_per_s": B / (both * 1e-3), "ms_solve_plus_grad": both,
+            "ms_grad_kernel": g_ms, "grad_kernel_gbs": traj_bytes / (g_ms * 1e-3) / 1e9,
+            "ms_grad_unrolled_ckpt32": u_ms, "grad_unrolled_per_s": B / (u_ms * 1e-3),
+            "unrolled_vs_envelope_max_rel": agree, "max_iters": kmax}
     return out
 
 
@@ -391,6 +403,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-other-configs", action="store_true")
+    ap.add_argument("--only", default=None,
+                    help="comma list of the other rows to run (quadratic, tanh, hopf, schemes, "
+                         "eikonal, game, ragged, adjoint); default all")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -553,7 +568,7 @@ def main():
         "clocks": clocks,
     }
     if not args.no_other_configs:
-        line["configs"] = measure_other_configs(dev, flush, stream, peak)
+        line["configs"] = measure_other_configs(dev, flush, stream, peak, args.only)
     if not args.no_cpu_baseline:
         v1, n1, t1 = run_cpu_oracle(w, 16, budget_s=8.0)
         v, n, wall, procs, cpu_s = run_cpu_oracle_all_cores(w)

@@ -31,8 +31,9 @@ def _eik(d, sign, N, B, seed=71):
     return w
 
 
-# every launch shape the mixed kernels have: FP32 NPL 1/2 with G 1/2 (N = 23,
-# 64, 100), FP64 G 1/2/4 (N = 23, 64, 100, 128), ragged tails; the four families
+# the default launch shapes (one node per lane, G = 1, 2, 4 for N = 23, 64, 100,
+# 128) with ragged tails, the four families; every other shape is checked by
+# test_scheme_every_launch_shape_gives_the_same_iterates
 CASES = [
     ("quadcopter", 12, 23), ("quadcopter", 12, 64), ("quadcopter", 12, 100),
     ("tanh_drift", 4, 50), ("tanh_drift", 2, 128),
@@ -108,6 +109,43 @@ def test_game_scheme_fp64_same_stop(d, scheme):
     same = (g["iters"] == o["iters"]) & conv
     assert np.mean(same) >= 0.7
     assert value_err(g["V"][same], o["V"][same]).max() <= 1e-9
+
+
+@pytest.mark.parametrize("family,d,N", [("quadcopter", 12, 64), ("eikonal+", 2, 64),
+                                        ("game", 2, 40), ("tanh_drift", 4, 64)])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_scheme_every_launch_shape_gives_the_same_iterates(family, d, N, precision):
+    """Every (warps per point, nodes per lane) instantiation of the mixed kernel
+    computes the same node formulas: the first shape against the oracle, the
+    others against the first to the rounding level."""
+    from paper_1803_01215_gb300 import binding
+    w = _case(family, d, N, B=21)
+    prob = binding.Problem.from_workload(w)
+    xq = torch.as_tensor(w["xq"], device="cuda")
+    t = torch.as_tensor(w["t"], device="cuda")
+    opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], tol=0.0, max_iter=60, check_every=60,
+                             precision=precision, seed=w["seed"], scheme="trap")
+    outs = []
+    for G in (1, 2, 4, 8):
+        for npl in ((1, 2) if precision == "fp32" else (1,)):
+            if N > 32 * G * npl or (precision == "fp64" and G == 8):
+                continue
+            binding.set_launch_shape(prob, precision, N, G, npl)
+            o = binding.solve_batch(prob, xq, t, N, opts, return_traj=True)
+            outs.append(((G, npl), {k: v.cpu().numpy() for k, v in o.items()}))
+    assert len(outs) >= 2
+    ref = outs[0][1]
+    solve = GS.solve_game_scheme if family == "game" else S.solve_scheme
+    o = solve(w, "trap", tol=0.0, max_iter=60, check_every=60)
+    ex, ep, _ = _cmp(ref, o)
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    assert ex <= tol and ep <= (tol * max(1.0, w["sigma"] / 25.0) if precision == "fp32" else tol)
+    rt = 1e-13 if precision == "fp64" else 1e-5
+    rp = rt * (max(1.0, w["sigma"] / 25.0) if precision == "fp32" else 1.0)
+    for shape, out in outs[1:]:
+        np.testing.assert_allclose(out["traj_x"], ref["traj_x"], rtol=rt, atol=rt, err_msg=str(shape))
+        np.testing.assert_allclose(out["traj_p"], ref["traj_p"], rtol=rp, atol=rp, err_msg=str(shape))
+        assert np.max(value_err(out["V"], ref["V"])) <= (1e-12 if precision == "fp64" else 1e-6)
 
 
 def test_quadratic_family_is_scheme_independent():
