@@ -261,9 +261,14 @@ hj_status hj_solve_grad_unrolled(hj_problem prob, int64_t B, const double* xq, c
                                  double* dW, double* dc, double* ddyn, double* dxq, void* stream);
 
 /* Launch shape of the register-resident kernel (quadratic d <= 4, quadcopter,
- * tanh drift d in {2, 4}): a group of `warps_per_point` warps (1, 2, 4, 8)
- * solves one point, each lane holding `nodes_per_lane` time nodes (1 or 2; 1
- * for FP64), so N <= 32 * warps_per_point * nodes_per_lane.  The shape does not
+ * tanh drift d in {2, 4}, eikonal d in {2, 10}, the game d in {2, 7}): a group
+ * of `warps_per_point` warps (1, 2, 4, 8) solves one point, each lane holding
+ * `nodes_per_lane` time nodes (1 or 2; 1 for FP64), so
+ * N <= 32 * warps_per_point * nodes_per_lane; warps_per_point = 0 selects half
+ * a warp (16 lanes, nodes_per_lane = 1, N <= 16): two points per warp.  The
+ * default is one node per lane over as few warps as N needs (two nodes per lane
+ * for H = |p|^2/2, half a warp for N <= 16); hj_autotune times every
+ * instantiated shape.  The shape does not
  * change any result, only the speed (the nodes a lane owns and the exchange
  * between lanes are the same arithmetic).  The shape is stored on the handle for
  * (precision, N) and used by later solves with that N.

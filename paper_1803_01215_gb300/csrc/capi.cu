@@ -266,10 +266,11 @@ hj_status hj_set_launch_shape(hj_problem prob, int32_t precision, int32_t N,
                               int32_t warps_per_point, int32_t nodes_per_lane) {
   if (prob == nullptr || N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;
   if (precision != HJ_PREC_FP32 && precision != HJ_PREC_FP64) return HJ_ERR_INVALID_ARG;
-  const hj::WarpConfig c{warps_per_point, nodes_per_lane};
+  hj::WarpConfig c{warps_per_point, nodes_per_lane};
+  if (warps_per_point == 0) c = hj::WarpConfig{1, nodes_per_lane, 1};   // half a warp
   if (!hj::warp_config_available(prob->family, prob->d, c, precision == HJ_PREC_FP64))
     return HJ_ERR_UNSUPPORTED;
-  if (N > 32 * c.G * c.NPL) return HJ_ERR_UNSUPPORTED;
+  if (N > hj::warp_config_lanes(c) * c.NPL) return HJ_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> g(prob->mu);
   prob->shapes[{precision, N}] = c;
   return HJ_OK;
@@ -281,7 +282,7 @@ hj_status hj_get_launch_shape(hj_problem prob, int32_t precision, int32_t N,
     return HJ_ERR_INVALID_ARG;
   if (N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;
   const hj::WarpConfig c = shape_for(prob, precision, N);
-  *warps_per_point = c.G;
+  *warps_per_point = c.half ? 0 : c.G;
   *nodes_per_lane = c.NPL;
   return HJ_OK;
 }
@@ -311,11 +312,12 @@ hj_status hj_autotune(hj_problem prob, int64_t B, const double* xq, const double
     r = HJ_ERR_CUDA;
   float best = -1.0f;
   hj::WarpConfig best_c{0, 0};
-  const int Gs[4] = {1, 2, 4, 8};
+  const int Gs[5] = {0, 1, 2, 4, 8};             // 0: half a warp
   for (int npl = 1; npl <= 2 && r == HJ_OK; ++npl) {
-    for (int gi = 0; gi < 4 && r == HJ_OK; ++gi) {
-      const hj::WarpConfig c{Gs[gi], npl};
-      if (!hj::warp_config_available(prob->family, prob->d, c, f64) || N > 32 * c.G * c.NPL)
+    for (int gi = 0; gi < 5 && r == HJ_OK; ++gi) {
+      const hj::WarpConfig c = Gs[gi] == 0 ? hj::WarpConfig{1, npl, 1} : hj::WarpConfig{Gs[gi], npl};
+      if (!hj::warp_config_available(prob->family, prob->d, c, f64) ||
+          N > hj::warp_config_lanes(c) * c.NPL)
         continue;
       float tot = 0.0f;
       for (int rep = 0; rep <= repeats && r == HJ_OK; ++rep) {   // rep 0 warms up
@@ -348,7 +350,7 @@ hj_status hj_autotune(hj_problem prob, int64_t B, const double* xq, const double
     std::lock_guard<std::mutex> g(prob->mu);
     prob->shapes[{opts->precision, N}] = best_c;
   }
-  if (warps_per_point) *warps_per_point = best_c.G;
+  if (warps_per_point) *warps_per_point = best_c.half ? 0 : best_c.G;
   if (nodes_per_lane) *nodes_per_lane = best_c.NPL;
   if (best_ms) *best_ms = best;
   return HJ_OK;

@@ -90,10 +90,13 @@ __device__ __forceinline__ PointRef<T> point_ref(const SolveArgs<T>& a, int64_t 
 }
 
 // Launch shape of the register-resident kernel: G warps per point, NPL time
-// nodes per lane; a point needs N <= 32 * G * NPL.
+// nodes per lane; a point needs N <= 32 * G * NPL.  half = 1 (with G = 1,
+// NPL = 1): half a warp per point, two points per warp, N <= 16.
 struct WarpConfig {
   int G, NPL;
+  int half = 0;
 };
+inline int warp_config_lanes(const WarpConfig& c) { return c.half ? 16 : 32 * c.G; }
 
 // splitmix64 (Vigna 2015) evaluated at a counter: z = seed + (c + 1) * golden,
 // followed by the generator's xor-shift-multiply finaliser.  Used for the

@@ -240,7 +240,7 @@ hj_status hj_ragged_plan_bucket(hj_ragged_plan plan, int32_t i, int32_t* problem
   if (problem) *problem = b.prob;
   if (n_max) *n_max = b.nmax;
   if (n_points) *n_points = (int64_t)b.ids.size();
-  if (warps_per_point) *warps_per_point = b.cfg.G;
+  if (warps_per_point) *warps_per_point = b.cfg.half ? 0 : b.cfg.G;
   if (nodes_per_lane) *nodes_per_lane = b.cfg.NPL;
   if (inner_steps) *inner_steps = b.inner_steps > 0 ? b.inner_steps : plan->opts.inner_steps;
   return HJ_OK;
@@ -307,7 +307,7 @@ hj_status hj_ragged_autotune(hj_ragged_plan plan, const double* xq, const double
     r = HJ_ERR_OOM;
   if (r == HJ_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
     r = HJ_ERR_CUDA;
-  const int Gs[4] = {1, 2, 4, 8};
+  const int Gs[5] = {0, 1, 2, 4, 8};             // 0: half a warp
   for (size_t bi = 0; bi < plan->buckets.size() && r == HJ_OK; ++bi) {
     Bucket& b = plan->buckets[bi];
     const hj_problem_s* pr = plan->probs[b.prob];
@@ -323,9 +323,10 @@ hj_status hj_ragged_autotune(hj_ragged_plan plan, const double* xq, const double
                          ? 1 : plan->opts.inner_steps;
     for (int inner = inner_lo; inner <= inner_hi && r == HJ_OK; ++inner)
     for (int npl = 1; npl <= 2 && r == HJ_OK; ++npl) {
-      for (int gi = 0; gi < 4 && r == HJ_OK; ++gi) {
-        const hj::WarpConfig c{Gs[gi], npl};
-        if (!hj::warp_config_available(pr->family, pr->d, c, f64) || b.nmax > 32 * c.G * c.NPL)
+      for (int gi = 0; gi < 5 && r == HJ_OK; ++gi) {
+        const hj::WarpConfig c = Gs[gi] == 0 ? hj::WarpConfig{1, npl, 1} : hj::WarpConfig{Gs[gi], npl};
+        if (!hj::warp_config_available(pr->family, pr->d, c, f64) ||
+            b.nmax > hj::warp_config_lanes(c) * c.NPL)
           continue;
         b.inner_steps = inner;
         float tot = 0.0f;

@@ -37,8 +37,14 @@ namespace hj {
 
 constexpr int kWarpsPerCtaG1 = 4;   // independent single-warp groups per CTA when G = 1
 
+// G = 0 stands for half a warp: two independent 16-lane groups per warp, for
+// N <= 16, where a whole warp per point would leave half its lanes without a node.
 template <int G>
-constexpr int warp_block_threads() { return (G == 1 ? kWarpsPerCtaG1 : G) * 32; }
+constexpr int warp_block_threads() { return (G <= 1 ? kWarpsPerCtaG1 : G) * 32; }
+template <int G>
+constexpr int group_lanes() { return G == 0 ? 16 : 32 * G; }
+template <int G>
+constexpr int groups_per_cta() { return G == 0 ? 2 * kWarpsPerCtaG1 : (G == 1 ? kWarpsPerCtaG1 : 1); }
 
 // Coordinates padded to a whole number of 16-byte vectors.
 template <typename T, int D>
@@ -50,7 +56,8 @@ constexpr int padded_dim() { return ((D * (int)sizeof(T) + 15) / 16) * 16 / (int
 // scratch of the CTA's one group.
 template <typename T, class F, int D, int G, bool MIX = false>
 struct WarpShared {
-  static constexpr int kGroups = (G == 1) ? kWarpsPerCtaG1 : 1;
+  static constexpr int kGroups = groups_per_cta<G>();
+  static constexpr int kL = group_lanes<G>();
   static constexpr int DP = padded_dim<T, D>();
   typename F::Shared fam;
   alignas(16) T g_off[DP];
@@ -58,21 +65,38 @@ struct WarpShared {
   alignas(16) T hs[DP];                    // Hopf form: sigma / W^2 and sigma c (node-1 prox)
   alignas(16) T hc[DP];
   double w2d[D], cd[D];
-  alignas(16) T zs[kGroups][32 * G][DP];   // z (in the epilogue x) of each lane's last node
-  alignas(16) T ps[kGroups][32 * G][DP];   // p of each lane's first node
+  alignas(16) T zs[kGroups][kL][DP];       // z (in the epilogue x) of each lane's last node
+  alignas(16) T ps[kGroups][kL][DP];       // p of each lane's first node
   alignas(16) T x0s[kGroups][DP];          // z_0 (in the epilogue x_0), one coordinate per lane
   // MIX only: x^k of each lane's last node, and x_0^k
-  alignas(16) T xs[MIX ? kGroups : 1][MIX ? 32 * G : 1][MIX ? DP : 1];
+  alignas(16) T xs[MIX ? kGroups : 1][MIX ? kL : 1][MIX ? DP : 1];
   alignas(16) T x0x[MIX ? kGroups : 1][MIX ? DP : 1];
-  T red[G][2];
-  double vred[G];
+  T red[G > 0 ? G : 1][2];
+  double vred[G > 0 ? G : 1];
   unsigned long long item;
 };
+
+// lanes of this thread's 16-lane half
+__device__ __forceinline__ unsigned half_mask() { return 0xFFFFu << (threadIdx.x & 16); }
 
 template <int G>
 __device__ __forceinline__ void group_sync() {
   if constexpr (G > 1) __syncthreads();
-  else __syncwarp();
+  else if constexpr (G == 1) __syncwarp();
+  else __syncwarp(half_mask());
+}
+
+// sum over the lanes of a warp, or of a half warp for G = 0
+template <int G, typename U>
+__device__ __forceinline__ U lanes_sum(U v) {
+  if constexpr (G == 0) {
+    const unsigned m = half_mask();
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o);
+    return v;
+  } else {
+    return warp_sum<U>(v);
+  }
 }
 
 // 16-byte vector copies between a D-array in registers and a padded slot.
@@ -128,8 +152,8 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   static_assert(!(MIX && HOPF), "the mixed schemes are Lax-form problems");
   const PointRef<T> pt = point_ref(a, item);
   const int N = pt.N;
-  const int gl = wg * 32 + lane;
-  if (N < 1 || N > 32 * G * NPL) {          // the host never routes such a point here
+  const int gl = wg * 32 + lane;              // lane: 0..15 for G = 0
+  if (N < 1 || N > group_lanes<G>() * NPL) {  // the host never routes such a point here
     if (gl == 0) { a.status[pt.id] = HJ_POINT_INVALID; a.iters[pt.id] = 0; a.V[pt.id] = 0.0; }
     return;
   }
@@ -184,7 +208,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     }
     z0 = x0;
   }
-  const int grp = (G == 1) ? (int)(threadIdx.x >> 5) : 0;
+  const int grp = (G == 1) ? (int)(threadIdx.x >> 5) : (G == 0 ? (int)(threadIdx.x >> 4) : 0);
   T* zslot = &sh.zs[grp][0][0];
   T* pslot = &sh.ps[grp][0][0];
   T* x0slot = &sh.x0s[grp][0];
@@ -193,7 +217,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   T* x0xslot = &sh.x0x[grp][0];
   if constexpr (MIX) { if (own0) x0xslot[k0] = x0; }
   constexpr int DP = WarpShared<T, F, D, G, MIX>::DP;
-  constexpr int kLanes = 32 * G;
+  constexpr int kLanes = group_lanes<G>();
 
   // One iteration; CHK adds the squared increments (test iterations only, so
   // the plain iterations carry no residual code at all).
@@ -358,7 +382,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     // lane partials summed across the warp (and the group's warps) in the
     // iterate type; the test against tol_t is then exactly the FP64 test of
     // that sum, so the loop needs no FP64 instruction
-    T sx = warp_sum<T>(rx), sp = warp_sum<T>(rp);
+    T sx = lanes_sum<G, T>(rx), sp = lanes_sum<G, T>(rp);
     if constexpr (G > 1) {
       if (lane == 0) { sh.red[wg][0] = sx; sh.red[wg][1] = sp; }
       __syncthreads();
@@ -427,7 +451,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
       }
     }
   }
-  acc = warp_sum<double>(acc);
+  acc = lanes_sum<G, double>(acc);
   if constexpr (G > 1) {
     if (lane == 0) sh.vred[wg] = acc;
     __syncthreads();
@@ -479,14 +503,18 @@ lax_warp_kernel(const SolveArgs<T> a) {
   }
   __syncthreads();
   const F fam(a, sh.fam);
-  const int lane = threadIdx.x & 31;
-  const int wg = (G == 1) ? 0 : (int)(threadIdx.x >> 5);
+  const int lane = (G == 0) ? (int)(threadIdx.x & 15) : (int)(threadIdx.x & 31);
+  const int wg = (G <= 1) ? 0 : (int)(threadIdx.x >> 5);
   for (;;) {
     int64_t item;
     if constexpr (G == 1) {
       unsigned long long bb = 0;
       if (lane == 0) bb = atomicAdd(a.counter, 1ull);
       item = (int64_t)__shfl_sync(kFull, bb, 0);
+    } else if constexpr (G == 0) {           // each half draws its own points
+      unsigned long long bb = 0;
+      if (lane == 0) bb = atomicAdd(a.counter, 1ull);
+      item = (int64_t)__shfl_sync(half_mask(), bb, (int)(threadIdx.x & 16));
     } else {
       __syncthreads();                       // the previous point is finished by every warp
       if (threadIdx.x == 0) sh.item = atomicAdd(a.counter, 1ull);
@@ -514,7 +542,7 @@ hj_status launch_warp_cfg_th(const SolveArgs<T>& a, cudaStream_t s) {
       return HJ_ERR_CUDA;
     blocks_per_sm = bps > 0 ? bps : 1;
   }
-  constexpr int points_per_cta = (G == 1) ? kWarpsPerCtaG1 : 1;
+  constexpr int points_per_cta = groups_per_cta<G>();
   const int64_t need = (a.B + points_per_cta - 1) / points_per_cta;
   const int64_t cap = (int64_t)blocks_per_sm * num_sms;
   const int grid = (int)(need < cap ? need : cap);
@@ -536,12 +564,18 @@ hj_status launch_warp_cfg(const SolveArgs<T>& a, cudaStream_t s) {
 }
 
 // Every (G, NPL) the library instantiates: FP32 G in {1,2,4,8} x NPL in {1,2};
-// FP64 G in {1,2,4,8} x NPL = 1; the mixed schemes in FP64 stop at G = 4 (their
+// FP64 G in {1,2,4,8} x NPL = 1; and half-warp groups (G = 0, NPL = 1, N <= 16); the mixed schemes in FP64 stop at G = 4 (their
 // second exchange slot would bring the static shared memory of the FP64 G = 8
 // group to about 75 KB; that instantiation is not built).
 template <typename T, template <typename, int> class F, int D, bool HOPF, bool MIX = false>
 hj_status launch_warp_shape(const SolveArgs<T>& a, WarpConfig c, cudaStream_t s) {
   constexpr bool f64 = sizeof(T) == 8;
+  if (c.half) {                                  // two 16-lane groups per warp
+    if constexpr (D <= 16) {
+      if (c.NPL == 1) return launch_warp_cfg<T, F<T, D>, D, 1, 0, HOPF, MIX>(a, s);
+    }
+    return HJ_ERR_UNSUPPORTED;
+  }
   if (c.NPL == 1) {
     switch (c.G) {
       case 1: return launch_warp_cfg<T, F<T, D>, D, 1, 1, HOPF, MIX>(a, s);

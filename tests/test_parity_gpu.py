@@ -320,3 +320,43 @@ def test_shared_memory_kernel_large_batches(d, B, precision):
     assert np.mean(same) >= 0.8
     bar = 1e-9 if precision == "fp64" else 1e-4
     assert np.max(value_err(g["V"][idx][same], o["V"][same])) <= bar
+
+
+@pytest.mark.parametrize("family,d,N", [("quadcopter", 12, 16), ("tanh_drift", 4, 9),
+                                        ("quadratic", 2, 16), ("eikonal", 10, 10),
+                                        ("game_norms", 7, 13)])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_half_warp_groups_match_the_oracle(family, d, N, precision):
+    """Half a warp per point (two points per warp, N <= 16): element-wise
+    against the oracle after K iterations, for a batch whose size is not a
+    multiple of the points per CTA."""
+    from oracle import game_pdhg as GO
+    from paper_1803_01215_gb300 import binding
+    if family == "eikonal":
+        w = dict(W.eikonal(d=d, sign=1, B=21, seed=81), N=N)
+        w["t"] = np.full(21, N * W.EIK_DELTA)
+    elif family == "game_norms":
+        w = dict(W.game_norms(d=d, B=21, seed=82), N=N)
+        w["t"] = np.full(21, N * W.EIK_DELTA)
+    else:
+        w = _custom(family, d, N, B=21)
+    prob = binding.Problem.from_workload(w)
+    binding.set_launch_shape(prob, precision, N, 0, 1)
+    assert binding.get_launch_shape(prob, precision, N) == (0, 1)
+    xq = torch.as_tensor(w["xq"], device="cuda")
+    t = torch.as_tensor(w["t"], device="cuda")
+    K = 90
+    opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], tol=0.0, max_iter=K, check_every=K,
+                             precision=precision, seed=w["seed"])
+    g = {k: v.cpu().numpy() for k, v in
+         binding.solve_batch(prob, xq, t, N, opts, return_traj=True).items()}
+    solve = GO.solve_game if family == "game_norms" else oracle_same_stop
+    o = solve(w, tol=0.0, max_iter=K, check_every=K)
+    assert np.all(g["iters"] == K)
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    tol_p = tol * max(1.0, w["sigma"] / 25.0) if precision == "fp32" else tol
+    assert np.max(np.abs(g["traj_x"] - o["x"])) <= tol
+    assert np.max(np.abs(g["traj_p"] - o["p"])) <= tol_p
+    assert np.max(value_err(g["V"], o["V"])) <= (1e-9 if precision == "fp64" else 1e-4)
+    with pytest.raises(binding.HJError):
+        binding.set_launch_shape(prob, precision, 17, 0, 1)        # 16 lanes hold N <= 16
