@@ -30,7 +30,7 @@ Arrays hold z = (x, y) and (p, q) stacked on the coordinate axis.
 import numpy as np
 
 from .families import QuadCost
-from .lax_pdhg import CONVERGED, MAX_ITER, NONFINITE, initial_guess
+from .lax_pdhg import CONVERGED, MAX_ITER, NONFINITE, VALUE_STOP, initial_guess
 
 
 class NormsGame:
@@ -82,9 +82,11 @@ def make_game(w):
 
 
 def solve_game(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter=None,
-               check_every=None, seed=None, init_radius=None, x_init=None, p_init=None):
+               check_every=None, seed=None, init_radius=None, x_init=None, p_init=None,
+               value_tol=0.0):
     """Run Algorithm 3 on every query point (x, y) of workload `w` (uniform N),
     from the random initial guess or from (x_init, p_init) as returned.
+    value_tol > 0: the value test of lax_pdhg.solve (status VALUE_STOP).
 
     Returns dict(V, iters, status, x [B, N+1, d] (z = (x, y)), p [B, N+1, d]
     ((p, q); index 0 is 0), rx, rp) like lax_pdhg.solve.
@@ -124,6 +126,7 @@ def solve_game(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter
 
     act = np.arange(B)
     z, P, zb, delta = z_all[act], P_all[act], zb_all[act], delta_all[act]
+    vprev = np.full(B, np.nan)
     k = 0
     while act.size and k < max_iter:
         dl = delta[:, None]
@@ -155,16 +158,23 @@ def solve_game(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter
         if k % check_every == 0 or k == max_iter:
             bad = ~(np.isfinite(rx) & np.isfinite(rp))
             conv = (rx < tol) & (rp < tol) & ~bad
-            stop = bad | conv | (k == max_iter)
+            vstop = np.zeros_like(conv)
+            if value_tol > 0:
+                v = game_value(game, cost, z, P, delta)
+                vstop = (np.abs(v - vprev) < value_tol) & ~bad & ~conv
+                vprev = v
+            stop = bad | conv | vstop | (k == max_iter)
             if np.any(stop):
                 ids = act[stop]
                 z_all[ids], P_all[ids] = z[stop], P[stop]
                 iters[ids] = k
                 rx_all[ids], rp_all[ids] = rx[stop], rp[stop]
                 status[ids] = np.where(bad[stop], NONFINITE,
-                                       np.where(conv[stop], CONVERGED, MAX_ITER))
+                                       np.where(conv[stop], CONVERGED,
+                                                np.where(vstop[stop], VALUE_STOP, MAX_ITER)))
                 keep = ~stop
                 act = act[keep]
                 z, P, zb, delta = z[keep], P[keep], zb[keep], delta[keep]
+                vprev = vprev[keep]
     V = game_value(game, cost, z_all, P_all, delta_all)
     return dict(V=V, iters=iters, status=status, x=z_all, p=P_all, rx=rx_all, rp=rp_all)

@@ -38,6 +38,7 @@ from .counter_rng import uniform_pm1
 from .families import QuadCost, make_family
 
 CONVERGED, MAX_ITER, NONFINITE = 0, 1, 2
+VALUE_STOP = 4     # stopped by the value test (the paper's switch for slow points)
 
 
 def eikonal_sign(w):
@@ -70,11 +71,15 @@ def lax_value(fam, cost, x, p, delta):
 
 def solve(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter=None,
           check_every=None, inner_steps=1, seed=None, init_radius=None,
-          x_init=None, p_init=None, activation="tanh"):
+          x_init=None, p_init=None, activation="tanh", value_tol=0.0):
     """Run Algorithm 1 on every query point of workload `w` (uniform N).
 
     Returns dict(V [B], iters [B], status [B], x [B, N+1, d], p [B, N+1, d],
     rx [B], rp [B]) where rx, rp are the last squared increments.
+
+    value_tol > 0 adds the paper's other stopping rule for slow points
+    (Section 6.2): at a test, a point whose value fval moved by less than
+    value_tol since the previous test stops with status VALUE_STOP.
     """
     fam = make_family(w, activation=activation)
     sign = eikonal_sign(w)
@@ -108,6 +113,7 @@ def solve(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter=None
 
     act = np.arange(B)                     # points still iterating
     x, p, z, delta = x_all[act], p_all[act], z_all[act], delta_all[act]
+    vprev = np.full(B, np.nan)             # fval at the previous test
     lam = sigma * delta[:, None]           # sigma * delta for every node j = 1..N
     k = 0
     while act.size and k < max_iter:
@@ -135,18 +141,25 @@ def solve(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter=None
         if k % check_every == 0 or k == max_iter:
             bad = ~(np.isfinite(rx) & np.isfinite(rp))
             conv = (rx < tol) & (rp < tol) & ~bad
-            stop = bad | conv | (k == max_iter)
+            vstop = np.zeros_like(conv)
+            if value_tol > 0:
+                v = lax_value(fam, cost, x, p, delta)
+                vstop = (np.abs(v - vprev) < value_tol) & ~bad & ~conv
+                vprev = v
+            stop = bad | conv | vstop | (k == max_iter)
             if np.any(stop):
                 ids = act[stop]
                 x_all[ids], p_all[ids], z_all[ids] = x[stop], p[stop], z[stop]
                 iters[ids] = k
                 rx_all[ids], rp_all[ids] = rx[stop], rp[stop]
                 status[ids] = np.where(bad[stop], NONFINITE,
-                                       np.where(conv[stop], CONVERGED, MAX_ITER))
+                                       np.where(conv[stop], CONVERGED,
+                                                np.where(vstop[stop], VALUE_STOP, MAX_ITER)))
                 keep = ~stop
                 act = act[keep]
                 x, p, z, delta = x[keep], p[keep], z[keep], delta[keep]
                 lam = lam[keep]
+                vprev = vprev[keep]
     V = lax_value(fam, cost, x_all, p_all, delta_all)
     return dict(V=sign * V, iters=iters, status=status, x=x_all, p=sign * p_all,
                 rx=rx_all, rp=rp_all)

@@ -12,7 +12,9 @@ MAX_ITER after round r - 1 and solves them again with
 either from a fresh random guess drawn with seed + r (warm = False: the point is
 rerun) or from its last iterate (warm = True: the iteration continues with the
 new steps, z restarting at x).  A point's iterations add up over its rounds and
-`rounds` records the last round it ran in.
+`rounds` records the last round it ran in.  value_tol > 0: the last round also
+stops a point whose value moved by less than value_tol between two tests (the
+paper's switch to a value criterion after a maximum count).
 """
 import numpy as np
 
@@ -25,7 +27,7 @@ def _solver(w):
     return game_pdhg.solve_game if w["family"] == "game_norms" else lax_pdhg.solve
 
 
-def solve_retry(w, *, rounds, sigma_step, step_product=0.0, warm=False, **kw):
+def solve_retry(w, *, rounds, sigma_step, step_product=0.0, warm=False, value_tol=0.0, **kw):
     solve = _solver(w)
     out = solve(w, **kw)
     out = {k: np.array(v) for k, v in out.items()}
@@ -45,6 +47,8 @@ def solve_retry(w, *, rounds, sigma_step, step_product=0.0, warm=False, **kw):
         sub["point_index"] = pidx[ids]
         sig = sigma0 + r * sigma_step
         args = dict(kw, sigma=sig, tau=prod / sig)
+        if r == rounds and value_tol > 0:
+            args.update(value_tol=value_tol)      # the last round may also stop on the value
         if warm:
             args.update(x_init=out["x"][ids], p_init=out["p"][ids])
         else:

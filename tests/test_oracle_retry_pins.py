@@ -93,3 +93,39 @@ def test_game_sigma_raise_converges_slow_points():
     # a converged point satisfies the stopping rule at its last iterate
     ok = b["status"] == O.CONVERGED
     assert np.all((b["rx"][ok] < w["tol"]) & (b["rp"][ok] < w["tol"]))
+
+
+def _plain_values(solve, w, ks, **kw):
+    return {k: solve(w, tol=0.0, max_iter=k, check_every=k, **kw)["V"] for k in ks}
+
+
+def test_value_stop_is_the_first_test_with_a_small_value_change():
+    """A point stopped by the value test at iteration k moved its value by less
+    than value_tol between the tests at k - c and k, and by at least value_tol
+    between the tests before (values from plain runs of k, k - c, k - 2c
+    iterations)."""
+    w = _td(max_iter=4000)
+    w["tol"] = 1e-30                              # the residual test never fires
+    vt = 1e-5
+    o = O.solve(w, value_tol=vt)
+    stopped = np.where(o["status"] == O.VALUE_STOP)[0]
+    assert stopped.size == len(o["V"])
+    c = w["check_every"]
+    for b in stopped[:4]:
+        k = int(o["iters"][b])
+        sub = W.subset(w, np.array([b]))
+        ks = [kk for kk in (k, k - c, k - 2 * c) if kk > 0]
+        v = _plain_values(O.solve, sub, ks)
+        np.testing.assert_allclose(o["V"][b], v[k][0], rtol=0, atol=1e-12)
+        assert abs(v[k][0] - v[k - c][0]) < vt
+        if k - 2 * c > 0:
+            assert abs(v[k - c][0] - v[k - 2 * c][0]) >= vt
+
+
+def test_value_stop_on_the_game_slow_points():
+    """The paper's remedy for points that neither converge nor settle their
+    trajectories: after the sigma raises, the last round stops on the value."""
+    w = W.subset(W.game_norms(d=2, t=0.3), np.array(GAME_SLOW[:6]))
+    b = R.solve_retry(w, rounds=1, sigma_step=20.0, step_product=0.24, value_tol=1e-5)
+    assert np.mean(b["status"] == O.VALUE_STOP) >= 0.5
+    assert np.all(b["iters"][b["status"] == O.VALUE_STOP] > w["max_iter"])   # in the last round
