@@ -292,7 +292,7 @@ def measure_other_configs(dev, flush, stream, peak, only=None):
             gopts = binding.make_opts(sigma=wg["sigma"], tau=wg["tau"], tol=wg["tol"],
                                       max_iter=wg["max_iter"], check_every=wg["check_every"],
                                       seed=wg["seed"], init_radius=wg["init_radius"])
-            pol = binding.RetryPolicy(3, 20.0, 0.24, 0)
+            pol = binding.RetryPolicy(3, 20.0, 0.24, 0, 0.0)
             xq = torch.as_tensor(wg["xq"], device=dev)
             t = torch.as_tensor(wg["t"], device=dev)
             res = binding.solve_batch_retry(prob, xq, t, int(wg["N"]), gopts, pol)

@@ -120,7 +120,7 @@ enum { HJ_SCHEME_BE = 0, HJ_SCHEME_FE = 1, HJ_SCHEME_TRAP = 2 };
  * own N was outside the range of the kernel it was routed to (ragged batches:
  * N[b] outside 1..256); such a point is not iterated.                        */
 enum { HJ_POINT_CONVERGED = 0, HJ_POINT_MAX_ITER = 1, HJ_POINT_NONFINITE = 2,
-       HJ_POINT_INVALID = 3 };
+       HJ_POINT_INVALID = 3, HJ_POINT_VALUE_STOP = 4 };
 
 typedef struct hj_problem_s* hj_problem;
 
@@ -162,7 +162,12 @@ hj_status hj_problem_destroy(hj_problem prob);
  *   formulation  HJ_FORM_LAX (0, the default of a zeroed struct) or HJ_FORM_HOPF;
  *                Hopf needs every W_i nonzero (HJ_ERR_INVALID_ARG otherwise).
  *   scheme       HJ_SCHEME_BE (0, the default), HJ_SCHEME_FE or HJ_SCHEME_TRAP
- *                (Lax form only).                                              */
+ *                (Lax form only).
+ *   value_tol    0 (the default) or > 0: the value test of Section 6.2's slow
+ *                points as well: at a test, a point whose fval moved by less
+ *                than value_tol (absolute) since the previous test stops with
+ *                status HJ_POINT_VALUE_STOP.  Backward-Euler Lax form in the
+ *                register-resident kernel only (HJ_ERR_UNSUPPORTED otherwise).  */
 typedef struct {
   double sigma, tau, theta, tol;
   int32_t max_iter, check_every, inner_steps, precision;
@@ -171,6 +176,7 @@ typedef struct {
   int64_t point_offset;
   int32_t formulation;
   int32_t scheme;
+  double value_tol;
 } hj_solver_opts;
 
 /* Solve B independent points with a common N (Algorithm 1, Eq. (disclaxBE); with
@@ -366,12 +372,16 @@ hj_status hj_ragged_plan_destroy(hj_ragged_plan plan);
  *   step_product  tau_r = step_product / sigma_r; 0 keeps opts->sigma * opts->tau.
  *   warm          0: round r reruns the point from a fresh random guess drawn
  *                 with seed + r; 1: it continues from the point's last iterate
- *                 (z restarts at x).                                          */
+ *                 (z restarts at x).
+ *   value_tol     > 0: the last round also applies the value test
+ *                 (hj_solver_opts.value_tol), the paper's switch to a value
+ *                 criterion after a maximum count; 0: off.                     */
 typedef struct {
   int32_t rounds;
   double sigma_step;
   double step_product;
   int32_t warm;
+  double value_tol;
 } hj_retry_policy;
 
 /* hj_solve_batch, then up to policy->rounds more rounds, each over the points
@@ -384,8 +394,7 @@ typedef struct {
  * (sigma_r > 0, 4 sigma_r tau_r < 1, ...) or nothing runs.  Allocates a
  * stream-ordered workspace of 2B int32 (+ 2 or 4 trajectory arrays with
  * warm = 1) and synchronises `stream` once per extra round (to read how many
- * points it retries).  The paper's other remedy, switching to a stopping test
- * on the value after a maximum count, is not provided.
+ * points it retries).
  * Errors: those of hj_solve_batch, HJ_ERR_OOM.                               */
 hj_status hj_solve_batch_retry(hj_problem prob, int64_t B, const double* xq, const double* t,
                                int32_t N, const hj_solver_opts* opts, const hj_retry_policy* policy,

@@ -31,7 +31,7 @@ class SolverOpts(ctypes.Structure):
                 ("inner_steps", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("init_radius", ctypes.c_double),
                 ("point_offset", ctypes.c_int64), ("formulation", ctypes.c_int32),
-                ("scheme", ctypes.c_int32)]
+                ("scheme", ctypes.c_int32), ("value_tol", ctypes.c_double)]
 
 
 _LIB = None
@@ -233,10 +233,11 @@ SCHEME = {"be": 0, "fe": 1, "trap": 2}
 
 def make_opts(*, sigma, tau, theta=1.0, tol=1e-8, max_iter=20000, check_every=16,
               inner_steps=1, precision="fp32", seed=0, init_radius=0.1, point_offset=0,
-              formulation="lax", scheme="be"):
+              formulation="lax", scheme="be", value_tol=0.0):
     return SolverOpts(float(sigma), float(tau), float(theta), float(tol), int(max_iter),
                       int(check_every), int(inner_steps), PREC[precision], int(seed),
-                      float(init_radius), int(point_offset), FORM[formulation], SCHEME[scheme])
+                      float(init_radius), int(point_offset), FORM[formulation], SCHEME[scheme],
+                      float(value_tol))
 
 
 def solve_batch(problem, xq, t, N, opts, *, return_traj=False, warm_x=None, warm_p=None,
@@ -277,7 +278,8 @@ def solve_batch(problem, xq, t, N, opts, *, return_traj=False, warm_x=None, warm
 class RetryPolicy(ctypes.Structure):
     """hj_retry_policy: extra rounds for points that reach the iteration cap."""
     _fields_ = [("rounds", ctypes.c_int32), ("sigma_step", ctypes.c_double),
-                ("step_product", ctypes.c_double), ("warm", ctypes.c_int32)]
+                ("step_product", ctypes.c_double), ("warm", ctypes.c_int32),
+                ("value_tol", ctypes.c_double)]
 
 
 def solve_batch_retry(problem, xq, t, N, opts, policy, *, return_traj=False, stream=None):

@@ -33,6 +33,10 @@ struct SolveArgs {
   int32_t scheme;
   T mix_wr_t, mix_wl_t;
   double mix_wr, mix_wl;
+  // value test (value_tol > 0): stop when fval moved less than value_tol
+  // between two tests
+  int32_t value_stop;
+  double value_tol;
   uint64_t seed;
   double radius;
   int64_t point_offset;

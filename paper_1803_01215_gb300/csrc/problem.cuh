@@ -76,7 +76,7 @@ hj_status dispatch(hj_problem_s* p, const hj::SolveArgs<T>& a, hj::WarpConfig cf
     const hj_status r = hj::launch_warp_solver<T>(p->family, a, cfg, s);
     if (r != HJ_ERR_UNSUPPORTED) return r;
   }
-  if (a.scheme != HJ_SCHEME_BE) return HJ_ERR_UNSUPPORTED;   // register kernel only
+  if (a.scheme != HJ_SCHEME_BE || a.value_stop) return HJ_ERR_UNSUPPORTED;   // register kernel only
   if (p->family == HJ_FAMILY_TANH_DRIFT) return hj::launch_td_cta_solver<T>(a, true, s);
   if (p->family == HJ_FAMILY_EIKONAL) return hj::launch_eik_cta_solver<T>(a, s);
   if (p->family == HJ_FAMILY_GAME_NORMS) return HJ_ERR_UNSUPPORTED;   // register kernel only
@@ -132,6 +132,8 @@ hj::SolveArgs<T> make_args(const hj_problem_s* prob, int64_t B, int32_t N,
   a.mix_wr = a.scheme == HJ_SCHEME_BE ? 1.0 : (a.scheme == HJ_SCHEME_FE ? 0.0 : 0.5);
   a.mix_wl = 1.0 - a.mix_wr;
   a.mix_wr_t = T(a.mix_wr); a.mix_wl_t = T(a.mix_wl);
+  a.value_tol = o.value_tol;
+  a.value_stop = o.value_tol > 0.0 ? 1 : 0;
   a.xq = xq; a.t = t; a.V = V; a.iters = iters; a.status = status;
   a.W2 = prob->W2; a.c = prob->c; a.A64 = prob->Ad;
   a.qc_m = prob->qc[0]; a.qc_ah = prob->qc[1]; a.qc_gz = prob->qc[2]; a.qc_eps = prob->qc[3];
@@ -154,6 +156,7 @@ inline hj_status check_opts(const hj_solver_opts& o) {
   if (o.formulation != HJ_FORM_LAX && o.formulation != HJ_FORM_HOPF) return HJ_ERR_INVALID_ARG;
   if (o.scheme != HJ_SCHEME_BE && o.scheme != HJ_SCHEME_FE && o.scheme != HJ_SCHEME_TRAP)
     return HJ_ERR_INVALID_ARG;
+  if (!(o.value_tol >= 0.0) || !std::isfinite(o.value_tol)) return HJ_ERR_INVALID_ARG;
   if (!(std::isfinite(o.init_radius) && o.init_radius >= 0.0) || o.point_offset < 0)
     return HJ_ERR_INVALID_ARG;
   if (4.0 * o.sigma * o.tau >= 1.0) return HJ_ERR_STEP_SIZE;
@@ -164,6 +167,10 @@ inline hj_status check_opts(const hj_solver_opts& o) {
 // solved in the Lax form only, and its negative equation's concave x_0 prox
 // needs tau W_i^2 < 1.
 inline hj_status check_formulation(const hj_problem_s* p, const hj_solver_opts& o) {
+  // the value test: the backward-Euler Lax form (register kernel, checked at dispatch)
+  if (o.value_tol > 0.0 && (o.formulation != HJ_FORM_LAX ||
+                            (o.scheme != HJ_SCHEME_BE && p->family != HJ_FAMILY_QUADRATIC)))
+    return HJ_ERR_UNSUPPORTED;
   // the forward-Euler and trapezoid forms: Lax form, one gradient step
   if (o.scheme != HJ_SCHEME_BE && p->family != HJ_FAMILY_QUADRATIC &&
       (o.formulation != HJ_FORM_LAX || o.inner_steps != 1))

@@ -9,7 +9,9 @@
 // round r then launches the same solver kernels on that list (SolveArgs::idx)
 // with sigma_r = sigma + r * sigma_step, tau_r = step_product / sigma_r, from a
 // fresh initial guess drawn with seed + r or, with warm = 1, from a copy of the
-// point's last iterate.  Each round reads the list length back to the host.
+// point's last iterate; with policy value_tol > 0 the last round also applies
+// the value test (the paper's switch to a value criterion after a maximum
+// count).  Each round reads the list length back to the host.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -56,6 +58,7 @@ hj_solver_opts round_opts(const hj_solver_opts& o, const hj_retry_policy& pol, i
   q.sigma = o.sigma + r * pol.sigma_step;
   q.tau = prod / q.sigma;
   if (!pol.warm) q.seed = o.seed + (uint64_t)r;
+  if (r == pol.rounds && pol.value_tol > 0.0) q.value_tol = pol.value_tol;   // the last round
   return q;
 }
 
@@ -129,6 +132,7 @@ hj_status hj_solve_batch_retry(hj_problem prob, int64_t B, const double* xq, con
   const hj_retry_policy& pol = *policy;
   if (pol.rounds < 0 || pol.rounds > 127 || !std::isfinite(pol.sigma_step) ||
       !(pol.step_product >= 0.0) || !std::isfinite(pol.step_product) ||
+      !(pol.value_tol >= 0.0) || !std::isfinite(pol.value_tol) ||
       (pol.warm != 0 && pol.warm != 1))
     return HJ_ERR_INVALID_ARG;
   const hj_solver_opts& o = *opts;

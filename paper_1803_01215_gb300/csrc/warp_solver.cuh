@@ -221,7 +221,17 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
 
   // One iteration; CHK adds the squared increments (test iterations only, so
   // the plain iterations carry no residual code at all).
-  auto step = [&](auto chk_tag, T& rx, T& rp) {
+  // On test iterations with the value test on (value_tol > 0, Lax form,
+  // backward Euler) vacc collects this lane's part of fval at (x^{k+1}, p^{k+1})
+  // in the summed-by-parts form
+  //   g(x_0) - <p_1, x_0> + sum_{j<N} <p_j - p_{j+1}, x_j> + <p_N, x_N> - delta sum_j H(x_j, p_j)
+  // (for the game the q-pairings enter with the opposite sign).
+  constexpr bool kValueTest = !MIX && !HOPF;
+  auto coord_sign = [&](int k) -> T {
+    if constexpr (F::kGame) return k < fam.d1 ? T(1) : T(-1);
+    else return T(1);
+  };
+  auto step = [&](auto chk_tag, T& rx, T& rp, T& vacc) {
     constexpr bool CHK = decltype(chk_tag)::value;
     typename F::Ctx ctx[NPL];
     // ---- z_{j-1} of the first owned node: the left lane's slot (z^k of its last node)
@@ -232,8 +242,9 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     slot_load<T, D>(gl > 0 ? zslot + (gl - 1) * DP : x0slot, zl);
     // MIX: x_{j-1}^k of the first owned node and its H quantities; x_0^k whole
     // (read here, before the next barrier, since the x_0 step rewrites its slot)
-    T xlv[MIX ? D : 1], x0v[MIX ? D : 1];
-    typename F::Ctx ctxl;
+    [[maybe_unused]] T xlv[MIX ? D : 1];
+    [[maybe_unused]] T x0v[MIX ? D : 1];
+    [[maybe_unused]] typename F::Ctx ctxl;
     if constexpr (MIX) {
       slot_load<T, D>(gl > 0 ? xslot + (gl - 1) * DP : x0xslot, xlv);
       if (own0) slot_load<T, D>(x0xslot, x0v);
@@ -303,6 +314,12 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         xn = (v0 + goff) * ginv;
       }
       if constexpr (CHK) { const T e = xn - x0; rx += e * e; }
+      if constexpr (CHK && kValueTest) {
+        if (a.value_stop) {                              // g(x_0) - <p_1, x_0>, coordinate k0
+          const T e = xn - T(sh.cd[k0]);
+          vacc += T(0.5) * T(sh.w2d[k0]) * e * e - coord_sign(k0) * pslot[k0] * xn;
+        }
+      }
       z0 = relax<T, TH1>(xn, x0, th);
       x0 = xn;
       x0slot[k0] = z0;
@@ -355,6 +372,14 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
           v_sub<T, D>(e, xn, x[i]);
           rx += v_sumsq<T, D>(e);
         }
+        if constexpr (CHK && kValueTest) {
+          if (a.value_stop) {                            // <p_j - p_{j+1}, x_j> - delta H(x_j, p_j)
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += coord_sign(k) * dp[k] * xn[k];
+            vacc += s - delta_t * fam.Ht(xn, p[i]);
+          }
+        }
         if constexpr (TH1) {
           v_fms<T, D>(z[i], T(2), xn, x[i]);                // z = 2 x_new - x
         } else {
@@ -363,6 +388,15 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         }
 #pragma unroll
         for (int k = 0; k < D; ++k) x[i][k] = xn[k];
+      } else if (jbase + i == N) {
+        if constexpr (CHK && kValueTest) {
+          if (a.value_stop) {                            // <p_N, x_N> - delta H(x_N, p_N)
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += coord_sign(k) * p[i][k] * x[i][k];
+            vacc += s - delta_t * fam.Ht(x[i], p[i]);
+          }
+        }
       }
     }
   };
@@ -370,14 +404,17 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   // Test after every check_every-th iteration and after iteration max_iter.
   int k_it = 0;
   int8_t st = HJ_POINT_MAX_ITER;
+  double vprev = 0.0;                                // fval at the previous test
+  bool have_prev = false;
   const int max_iter = a.max_iter, check_every = a.check_every;
   while (k_it < max_iter) {
     const int left = max_iter - k_it;
     const int plain = (check_every - 1 < left - 1) ? check_every - 1 : left - 1;
-    T dummy_x = T(0), dummy_p = T(0);
-    for (int r = 0; r < plain; ++r) step(std::integral_constant<bool, false>{}, dummy_x, dummy_p);
-    T rx = T(0), rp = T(0);
-    step(std::integral_constant<bool, true>{}, rx, rp);
+    T dummy_x = T(0), dummy_p = T(0), dummy_v = T(0);
+    for (int r = 0; r < plain; ++r)
+      step(std::integral_constant<bool, false>{}, dummy_x, dummy_p, dummy_v);
+    T rx = T(0), rp = T(0), vacc = T(0);
+    step(std::integral_constant<bool, true>{}, rx, rp, vacc);
     k_it += plain + 1;
     // lane partials summed across the warp (and the group's warps) in the
     // iterate type; the test against tol_t is then exactly the FP64 test of
@@ -392,6 +429,22 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     }
     if (!(isfinite(sx) && isfinite(sp))) { st = HJ_POINT_NONFINITE; break; }
     if (sx < a.tol_t && sp < a.tol_t) { st = HJ_POINT_CONVERGED; break; }
+    if constexpr (kValueTest) {
+      if (a.value_stop) {                 // the value moved less than value_tol since the last test
+        double v = lanes_sum<G, double>((double)vacc);
+        if constexpr (G > 1) {
+          if (lane == 0) sh.vred[wg] = v;
+          __syncthreads();
+          v = 0.0;
+#pragma unroll
+          for (int w = 0; w < G; ++w) v += sh.vred[w];
+          __syncthreads();                // every warp has read before the next write
+        }
+        if (have_prev && fabs(v - vprev) < a.value_tol) { st = HJ_POINT_VALUE_STOP; break; }
+        vprev = v;
+        have_prev = true;
+      }
+    }
   }
 
   // ---- value (fval of Algorithm 1), summed in FP64, and outputs

@@ -18,13 +18,13 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _run(w, precision, rounds, sigma_step, step_product=0.24, warm=False):
+def _run(w, precision, rounds, sigma_step, step_product=0.24, warm=False, value_tol=0.0):
     from paper_1803_01215_gb300 import binding
     prob = binding.Problem.from_workload(w)
     opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], tol=w["tol"], max_iter=w["max_iter"],
                              check_every=w["check_every"], seed=w["seed"],
                              init_radius=w["init_radius"], precision=precision)
-    pol = binding.RetryPolicy(rounds, sigma_step, step_product, int(warm))
+    pol = binding.RetryPolicy(rounds, sigma_step, step_product, int(warm), value_tol)
     xq = torch.as_tensor(w["xq"], device="cuda")
     t = torch.as_tensor(w["t"], device="cuda")
     out = binding.solve_batch_retry(prob, xq, t, int(w["N"]), opts, pol, return_traj=True)
@@ -88,11 +88,69 @@ def test_retry_argument_errors():
     xq = torch.as_tensor(w["xq"], device="cuda")
     t = torch.as_tensor(w["t"], device="cuda")
     opts = binding.make_opts(sigma=1.0, tau=0.24)
-    cases = [(binding.RetryPolicy(-1, 0.0, 0.0, 0), 1),        # rounds < 0
-             (binding.RetryPolicy(2, 0.0, 0.0, 3), 1),         # warm not 0/1
-             (binding.RetryPolicy(3, -0.5, 0.0, 0), 1),        # sigma_3 < 0
-             (binding.RetryPolicy(2, 1.0, 0.3, 0), 3)]         # 4 sigma tau >= 1
+    cases = [(binding.RetryPolicy(-1, 0.0, 0.0, 0, 0.0), 1),   # rounds < 0
+             (binding.RetryPolicy(2, 0.0, 0.0, 3, 0.0), 1),    # warm not 0/1
+             (binding.RetryPolicy(3, -0.5, 0.0, 0, 0.0), 1),   # sigma_3 < 0
+             (binding.RetryPolicy(2, 1.0, 0.3, 0, 0.0), 3),    # 4 sigma tau >= 1
+             (binding.RetryPolicy(2, 1.0, 0.0, 0, -1.0), 1)]   # value_tol < 0
     for pol, code in cases:
         with pytest.raises(binding.HJError) as e:
             binding.solve_batch_retry(prob, xq, t, int(w["N"]), opts, pol)
         assert e.value.code == code
+
+
+@pytest.mark.parametrize("family", ["tanh_drift", "quadcopter"])
+def test_value_stop_fp64_matches_the_oracle(family):
+    """The value test in the kernel (summed by parts on test iterations, one
+    group of warps for the 12-D N = 64 problem) stops at the oracle's test."""
+    from gpu_common import gpu
+    if family == "tanh_drift":
+        w = _td(max_iter=4000)
+    else:
+        w = W.quadcopter(B=24, seed=33, N=64, t=1.0)
+        w.update(max_iter=4000)
+    w["tol"] = 1e-30                                   # only the value test can stop
+    vt = 1e-5
+    g = gpu(w, "fp64", value_tol=vt)
+    o = O.solve(w, value_tol=vt)
+    assert np.all(o["status"] == O.VALUE_STOP)
+    assert np.all(g["status"] == O.VALUE_STOP)
+    same = g["iters"] == o["iters"]
+    assert np.mean(same) >= 0.8
+    assert value_err(g["V"][same], o["V"][same]).max() <= 1e-9
+
+
+def test_value_stop_fp32_and_game_retry():
+    from gpu_common import gpu
+    w = _td(max_iter=4000)
+    w["tol"] = 1e-30
+    g = gpu(w, "fp32", value_tol=1e-5)
+    o = O.solve(w, value_tol=1e-5)
+    assert np.all(g["status"] == O.VALUE_STOP)
+    assert np.all(np.abs(g["iters"] - o["iters"]) <= 2 * w["check_every"])
+    # the game's slow grid points: sigma raise, then the value test in the last round
+    wg = W.subset(W.game_norms(d=2, t=0.3), np.array(GAME_SLOW[:6]))
+    r = _run(wg, "fp64", 1, 20.0, value_tol=1e-5)
+    assert np.mean(r["status"] == O.VALUE_STOP) >= 0.5
+    assert np.all(r["iters"][r["status"] == O.VALUE_STOP] > wg["max_iter"])
+
+
+def test_value_stop_argument_errors():
+    from paper_1803_01215_gb300 import binding
+    from test_parity_gpu import _custom
+    w = _td()
+    prob = binding.Problem.from_workload(w)
+    xq = torch.as_tensor(w["xq"], device="cuda")
+    t = torch.as_tensor(w["t"], device="cuda")
+    for kw, code in ((dict(formulation="hopf"), 2), (dict(scheme="trap"), 2), (dict(), 1)):
+        opts = binding.make_opts(sigma=1.0, tau=0.24, value_tol=1e-6 if kw else -1.0, **kw)
+        with pytest.raises(binding.HJError) as e:
+            binding.solve_batch(prob, xq, t, int(w["N"]), opts)
+        assert e.value.code == code
+    wt = _custom("tanh_drift", 8, 8, B=3)                # shared-memory kernel: no value test
+    pt = binding.Problem.from_workload(wt)
+    with pytest.raises(binding.HJError) as e:
+        binding.solve_batch(pt, torch.as_tensor(wt["xq"], device="cuda"),
+                            torch.as_tensor(wt["t"], device="cuda"), 8,
+                            binding.make_opts(sigma=1.0, tau=0.24, value_tol=1e-6))
+    assert e.value.code == 2
