@@ -9,6 +9,8 @@ control-affine dynamics f = f0(x) + B(x) u, so H = <p, f0> + |B^T p|^2 / 2.
 Every array argument has the coordinate axis last: x, p have shape [..., d].
 prox_p(x, v, lam) returns argmin_p { lam * H(x, p) + |p - v|^2 / 2 }, the
 dual proximal map of Algorithm 1 with lam = sigma * delta.
+A time-dependent H (the moving-bump eikonal of Section 6.1) takes the node
+time s (shape x.shape[:-1]) as the keyword s; the other families ignore it.
 prox_p_mix(xl, xr, wl, wr, v, lam) returns
 argmin_p { lam (wl H(xl, p) + wr H(xr, p)) + |p - v|^2 / 2 }, the dual map of
 the forward-Euler (wl = 1, wr = 0) and trapezoid (wl = wr = 1/2) forms.
@@ -24,16 +26,16 @@ class Quadratic:
     def __init__(self, d):
         self.d = d
 
-    def H(self, x, p):
+    def H(self, x, p, s=None):
         return 0.5 * np.sum(p * p, axis=-1)
 
-    def grad_p(self, x, p):
+    def grad_p(self, x, p, s=None):
         return p.copy()
 
-    def grad_x(self, x, p):
+    def grad_x(self, x, p, s=None):
         return np.zeros_like(p)
 
-    def prox_p(self, x, v, lam):
+    def prox_p(self, x, v, lam, s=None):
         # lam * p + (p - v) = 0
         return v / (1.0 + lam[..., None])
 
@@ -61,19 +63,19 @@ class TanhDrift:
         a = np.tanh(y)
         return a, 1.0 - a * a                 # value and derivative of tanh
 
-    def H(self, x, p):
+    def H(self, x, p, s=None):
         a, _ = self._act(x)
         return np.sum(p * a, axis=-1) + 0.5 * np.sum(p * p, axis=-1)
 
-    def grad_p(self, x, p):
+    def grad_p(self, x, p, s=None):
         a, _ = self._act(x)
         return a + p
 
-    def grad_x(self, x, p):
+    def grad_x(self, x, p, s=None):
         _, da = self._act(x)
         return (da * p) @ self.A              # A^T (tanh'(Ax) * p)
 
-    def prox_p(self, x, v, lam):
+    def prox_p(self, x, v, lam, s=None):
         # lam * (a + p) + (p - v) = 0
         a, _ = self._act(x)
         lam = lam[..., None]
@@ -152,17 +154,17 @@ class Quadcopter:
         Bm[..., 11, 3] = 1.0
         return Bm
 
-    def H(self, x, p):
+    def H(self, x, p, s=None):
         u = np.einsum("...ik,...i->...k", self.Bmat(x), p)
         return (np.sum(p * self.f0(x), axis=-1) + 0.5 * np.sum(u * u, axis=-1)
                 + 0.5 * self.eps * np.sum(p * p, axis=-1))
 
-    def grad_p(self, x, p):
+    def grad_p(self, x, p, s=None):
         Bm = self.Bmat(x)
         u = np.einsum("...ik,...i->...k", Bm, p)
         return self.f0(x) + np.einsum("...ik,...k->...i", Bm, u) + self.eps * p
 
-    def grad_x(self, x, p):
+    def grad_x(self, x, p, s=None):
         a, J = self.thrust_dir(x)
         q = p[..., 6:9]
         u0 = np.sum(a * q, axis=-1) / self.m              # thrust control B_0 . p
@@ -174,7 +176,7 @@ class Quadcopter:
         g[..., 9:12] = p[..., 3:6]                         # d/dv_ang of <p_ang, v_ang>
         return g
 
-    def prox_p(self, x, v, lam):
+    def prox_p(self, x, v, lam, s=None):
         # lam (f0 + B B^T p + eps p) + (p - v) = 0
         #   ->  ((1 + lam eps) I + lam B B^T) p = v - lam f0
         Bm = self.Bmat(x)
@@ -197,47 +199,55 @@ class Quadcopter:
 
 
 class Eikonal:
-    """H(x, p) = c(x) |p|_2 with the speed of Section 6.1,
-    c(x) = c0 + c1 exp(-c2 |x - x_b|^2) (a bump of height c1 at x_b on a floor c0).
+    """H(x, p, s) = c(x - s v_b) |p|_2 with the speed of Section 6.1,
+    c(y) = c0 + c1 exp(-c2 |y - x_b|^2) (a bump of height c1 at x_b on a floor c0).
+    v_b (default none: 0) moves the bump with velocity v_b as time s grows,
+    Section 6.1's state-and-time-dependent example (v_b = (-1, 1)).
 
     The dual proximal map is the shrink_2 operator of Section 6.1:
-    argmin_p lam c(x) |p| + |p - v|^2 / 2 = v max(|v| - lam c(x), 0) / |v|.
-    grad_x H = |p| grad c(x); H is not differentiable in p at p = 0, and
+    argmin_p lam c |p| + |p - v|^2 / 2 = v max(|v| - lam c, 0) / |v|.
+    grad_x H = |p| grad c; H is not differentiable in p at p = 0, and
     grad_p H is only used away from it.
     """
 
-    def __init__(self, c0, c1, c2, xb):
+    def __init__(self, c0, c1, c2, xb, vb=None):
         self.c0, self.c1, self.c2 = float(c0), float(c1), float(c2)
         self.xb = np.asarray(xb, dtype=np.float64)
         self.d = self.xb.shape[0]
+        self.vb = None if vb is None or not np.any(vb) else np.asarray(vb, dtype=np.float64)
+        self.time_dependent = self.vb is not None
 
-    def speed(self, x):
-        """c(x) and grad c(x)."""
+    def speed(self, x, s=None):
+        """c and grad c at x (node time s for a moving bump)."""
         y = x - self.xb
+        if self.vb is not None:
+            y = y - np.asarray(s)[..., None] * self.vb
         e = np.exp(-self.c2 * np.sum(y * y, axis=-1))
         return self.c0 + self.c1 * e, (-2.0 * self.c1 * self.c2 * e)[..., None] * y
 
-    def H(self, x, p):
-        c, _ = self.speed(x)
+    def H(self, x, p, s=None):
+        c, _ = self.speed(x, s)
         return c * np.sqrt(np.sum(p * p, axis=-1))
 
-    def grad_p(self, x, p):
-        c, _ = self.speed(x)
+    def grad_p(self, x, p, s=None):
+        c, _ = self.speed(x, s)
         n = np.sqrt(np.sum(p * p, axis=-1))
         return np.where(n[..., None] > 0, c[..., None] * p / np.where(n > 0, n, 1.0)[..., None], 0.0)
 
-    def grad_x(self, x, p):
-        _, gc = self.speed(x)
+    def grad_x(self, x, p, s=None):
+        _, gc = self.speed(x, s)
         return np.sqrt(np.sum(p * p, axis=-1))[..., None] * gc
 
-    def prox_p(self, x, v, lam):
-        c, _ = self.speed(x)
+    def prox_p(self, x, v, lam, s=None):
+        c, _ = self.speed(x, s)
         n = np.sqrt(np.sum(v * v, axis=-1))
         keep = np.maximum(n - lam * c, 0.0) / np.where(n > 0, n, 1.0)
         return keep[..., None] * v
 
     def prox_p_mix(self, xl, xr, wl, wr, v, lam):
         # (wl c(xl) + wr c(xr)) |p|: shrink_2 with the weighted speed
+        if self.time_dependent:
+            raise ValueError("the moving bump is solved in the backward-Euler form only")
         cl, _ = self.speed(xl)
         cr, _ = self.speed(xr)
         n = np.sqrt(np.sum(v * v, axis=-1))
@@ -278,6 +288,8 @@ def make_family(w, activation="tanh"):
     if fam == "quadcopter":
         return Quadcopter(*dyn[:4])
     if fam == "eikonal":
-        # dyn = (s, c0, c1, c2, x_b): s = +1 the positive equation, -1 the negative
-        return Eikonal(dyn[1], dyn[2], dyn[3], dyn[4:4 + d])
+        # dyn = (s, c0, c1, c2, x_b[, v_b]): s = +1 the positive equation, -1 the
+        # negative; v_b (optional) the bump's velocity
+        vb = dyn[4 + d:4 + 2 * d] if dyn.size >= 4 + 2 * d else None
+        return Eikonal(dyn[1], dyn[2], dyn[3], dyn[4:4 + d], vb)
     raise ValueError(fam)

@@ -84,6 +84,8 @@ def solve_hopf(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter
     if w["family"] == "eikonal":
         raise ValueError("the Hopf form here needs H quadratic in p (not the eikonal family)")
     fam = make_family(w, activation=activation)
+    if getattr(fam, "time_dependent", False):
+        raise ValueError("a time-dependent H is solved in the backward-Euler Lax form only")
     cost = QuadCost(w["W"], w["c"])
     if np.any(cost.w2 == 0.0):
         raise ValueError("the Hopf form needs every W_i nonzero (g* finite)")

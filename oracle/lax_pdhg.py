@@ -61,11 +61,17 @@ def initial_guess(xq, N, seed, radius, point_index):
     return x0, p0
 
 
+def node_times(delta, N):
+    """s_j = j delta, j = 0..N (uniform nodes, s_N = t), shape [B, N+1]."""
+    return np.arange(N + 1)[None, :] * np.asarray(delta, dtype=np.float64)[:, None]
+
+
 def lax_value(fam, cost, x, p, delta):
     """fval of Algorithm 1 for stacked x [B, N+1, d], p [B, N+1, d] (p_0 unused)."""
     dx = x[:, 1:, :] - x[:, :-1, :]
     pair = np.sum(p[:, 1:, :] * dx, axis=(1, 2))
-    ham = np.sum(fam.H(x[:, 1:, :], p[:, 1:, :]), axis=1)
+    S = node_times(delta, x.shape[1] - 1)
+    ham = np.sum(fam.H(x[:, 1:, :], p[:, 1:, :], s=S[:, 1:]), axis=1)
     return cost.g(x[:, 0, :]) + pair - delta * ham
 
 
@@ -117,11 +123,12 @@ def solve(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter=None
     lam = sigma * delta[:, None]           # sigma * delta for every node j = 1..N
     k = 0
     while act.size and k < max_iter:
-        # dual step, j = 1..N, H evaluated at x^k
+        # dual step, j = 1..N, H evaluated at x^k (and the node times s_j = j delta)
+        S = node_times(delta, N)
         v = p[:, 1:, :] + sigma * (z[:, 1:, :] - z[:, :-1, :])
         p_new = np.empty_like(p)
         p_new[:, 0, :] = 0.0
-        p_new[:, 1:, :] = fam.prox_p(x[:, 1:, :], v, lam)
+        p_new[:, 1:, :] = fam.prox_p(x[:, 1:, :], v, lam, s=S[:, 1:])
         # primal step, x_0: prox of g, (D^T p)_0 = -p_1
         x_new = np.empty_like(x)
         x_new[:, 0, :] = cost.prox(x[:, 0, :] + tau * p_new[:, 1, :], tau)
@@ -129,7 +136,7 @@ def solve(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter=None
         base = x[:, 1:N, :] - tau * (p_new[:, 1:N, :] - p_new[:, 2:N + 1, :])
         xj = x[:, 1:N, :]
         for _ in range(inner_steps):
-            xj = base + tau * delta[:, None, None] * fam.grad_x(xj, p_new[:, 1:N, :])
+            xj = base + tau * delta[:, None, None] * fam.grad_x(xj, p_new[:, 1:N, :], s=S[:, 1:N])
         x_new[:, 1:N, :] = xj
         x_new[:, N, :] = x[:, N, :]
         # over-relaxation
@@ -175,9 +182,10 @@ def kkt_residual(w, x, p, activation="tanh"):
     cost = QuadCost(w["W"], w["c"])
     N = x.shape[1] - 1
     delta = (np.asarray(w["t"], dtype=np.float64) / N)[:, None, None]
-    r1 = x[:, 1:] - x[:, :-1] - delta * fam.grad_p(x[:, 1:], p[:, 1:])
+    S = node_times(delta[:, 0, 0], N)
+    r1 = x[:, 1:] - x[:, :-1] - delta * fam.grad_p(x[:, 1:], p[:, 1:], s=S[:, 1:])
     r2 = p[:, 1] - cost.grad(x[:, 0])
-    r3 = p[:, 2:] - p[:, 1:N] + delta * fam.grad_x(x[:, 1:N], p[:, 1:N])
+    r3 = p[:, 2:] - p[:, 1:N] + delta * fam.grad_x(x[:, 1:N], p[:, 1:N], s=S[:, 1:N])
     return np.maximum(np.max(np.abs(r1), axis=(1, 2)),
                       np.maximum(np.max(np.abs(r2), axis=1),
                                  np.max(np.abs(r3), axis=(1, 2)) if N > 1 else 0.0))

@@ -59,6 +59,8 @@ def solve_scheme(w, scheme, *, N=None, sigma=None, tau=None, theta=1.0, tol=None
     """
     wl, wr = SCHEMES[scheme]
     fam = make_family(w, activation=activation)
+    if getattr(fam, "time_dependent", False):
+        raise ValueError("a time-dependent H is solved in the backward-Euler Lax form only")
     sign = eikonal_sign(w)
     cost = QuadCost(w["W"], w["c"], sign=sign)
     N = int(w["N"] if N is None else N)

@@ -121,3 +121,40 @@ def test_bump_speed_positive_direct_collocation():
                        constraints=cons, options=dict(ftol=1e-15, maxiter=2000))
         assert res.success
         assert abs(res.fun - o["V"][b]) < 1e-7, (b, res.fun, o["V"][b])
+
+
+def test_moving_bump_direct_collocation():
+    """Section 6.1's state-and-time-dependent eikonal, c(x - s(-1, 1)) |p|: the
+    primal problem min g(x_0) subject to |x_j - x_{j-1}| <= delta c(x_j - s_j v),
+    s_j = j delta, x_N = x, solved by SLSQP from the straight-line start, matches
+    the oracle's value (a node time shifted by one step fails it)."""
+    d, N, t = 2, 5, 0.4
+    W = np.array([1 / 2.5, 1.0])
+    xb, vb = np.array([1.0, 1.0]), np.array([-1.0, 1.0])
+    xq = np.array([[0.6, 0.8], [1.6, 0.2], [-0.5, 1.4]])
+    w = _eik(d, xq, t, N, +1, sigma=0.5, xb=xb, W=W)
+    w["dyn"] = np.concatenate([w["dyn"], vb])
+    o = O.solve(w)
+    assert np.all(o["status"] == O.CONVERGED)
+    delta = t / N
+    cfun = lambda y, s: 1.0 + 3.0 * np.exp(-4.0 * np.sum((y - s * vb - xb) ** 2))
+    for b, x in enumerate(xq):
+        def unpack(z):
+            return np.vstack([z.reshape(N, d), x])
+        cons = [{"type": "ineq",
+                 "fun": (lambda z, j=j: (delta * cfun(unpack(z)[j], j * delta)) ** 2
+                         - np.sum((unpack(z)[j] - unpack(z)[j - 1]) ** 2))}
+                for j in range(1, N + 1)]
+        z0 = np.repeat(x[None], N, 0).ravel()
+        res = minimize(lambda z: 0.5 * np.sum(W ** 2 * unpack(z)[0] ** 2), z0, method="SLSQP",
+                       constraints=cons, options=dict(ftol=1e-15, maxiter=2000))
+        assert res.success
+        assert abs(res.fun - o["V"][b]) < 1e-7, (b, res.fun, o["V"][b])
+
+
+def test_zero_velocity_is_the_static_bump():
+    w = _eik(2, [[0.6, 0.8], [-1.0, 0.4]], 0.3, 6, +1, sigma=0.5, xb=[1.0, 1.0])
+    a = O.solve(w, tol=0.0, max_iter=50, check_every=50)
+    w["dyn"] = np.concatenate([w["dyn"], [0.0, 0.0]])
+    b = O.solve(w, tol=0.0, max_iter=50, check_every=50)
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["V"], b["V"])
