@@ -41,7 +41,7 @@ SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # kernel (lax_warp_kernel<float, FamQuadcopter, 12, 1, 2>) from the ncu capture
 # summarised in profiles/quadcopter12d_B4096_N64_fp32_warp_kernel.md; set to
 # None whenever that kernel changes until it is captured again.
-QC_TRAFFIC_BYTES = 469504
+QC_TRAFFIC_BYTES = 473344
 
 
 def workload_config():
@@ -268,6 +268,18 @@ def measure_other_configs(dev, flush, stream, peak, only=None):
                             "tflops": flops / (ms * 1e-3) / 1e12,
                             "paper_cpu_fit_s_per_point": 1.14e-4 * d + 0.0021}
         out["eikonal_negative_t0.2_slice3721_fp32"] = eik
+        # Section 6.1's state-and-time-dependent eikonal (the bump moving with
+        # velocity (-1, 1)), d = 2, t = 0.1 .. 0.4 on the same grid, FP32; the
+        # paper's C++ average, 5.012e-4 s per point, is context only
+        mov = {}
+        for t_m in (0.1, 0.2, 0.3, 0.4):
+            wm = W.eikonal_moving(t=t_m)
+            ms, conv, iters, _ = run_uniform(wm, "fp32", f"timed_eikonal_moving_t{t_m}")
+            mov[f"t{t_m}"] = {"solves_per_s": conv / (ms * 1e-3), "ms_per_step": ms,
+                              "converged": conv, "points": len(wm["xq"]),
+                              "mean_iters": iters / len(wm["xq"]),
+                              "paper_cpu_s_per_point": 5.012e-4}
+        out["eikonal_moving_bump_d2_slice3721_fp32"] = mov
 
     if want("game"):
         # Section 6.2's difference-of-norms game, 2-D and its 7-D slice, on the

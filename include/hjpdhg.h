@@ -61,7 +61,11 @@ enum {
    * is the shrink_2 operator.  s = -1 is solved as in Section 6.1: phi = -psi
    * with psi the s = +1 solution for the initial data -g (concave; its x_0
    * proximal map needs tau W_i^2 < 1, HJ_ERR_STEP_SIZE otherwise), and V and
-   * the returned p are those of phi.  Lax form only.                        */
+   * the returned p are those of phi.  Lax form only.  With 4 + 2d doubles the
+   * last d are a bump velocity v_b: H(x, p, s) = c(x - s v_b)|p|_2 at the node
+   * times s_j = j delta (Section 6.1's state-and-time-dependent example, v_b =
+   * (-1, 1)); a nonzero v_b runs in the register kernel only (d in {2, 10}),
+   * backward Euler.                                                         */
   HJ_FAMILY_EIKONAL = 3,
   /* Difference-of-norms differential game of Section 6.2 (Algorithm 3):
    * state z = (x, y), x = z[0..d1) the minimising player, y = z[d1..d) the

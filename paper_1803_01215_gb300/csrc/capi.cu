@@ -60,7 +60,7 @@ hj_status hj_problem_create(hj_problem* out, int32_t family, int32_t d, const do
         return HJ_ERR_INVALID_ARG;
       break;
     case HJ_FAMILY_EIKONAL:
-      if (n_dyn != 4 + (int64_t)d) return HJ_ERR_INVALID_ARG;
+      if (n_dyn != 4 + (int64_t)d && n_dyn != 4 + 2 * (int64_t)d) return HJ_ERR_INVALID_ARG;
       if (!(dyn[0] == 1.0 || dyn[0] == -1.0) || !(dyn[1] > 0.0) || !(dyn[2] >= 0.0) ||
           !(dyn[3] >= 0.0))
         return HJ_ERR_INVALID_ARG;
@@ -96,6 +96,17 @@ hj_status hj_problem_create(hj_problem* out, int32_t family, int32_t d, const do
     for (int i = 0; i < d; ++i) xf[i] = (float)dyn[4 + i];
     r = upload(&p->xbd, dyn + 4, d);
     if (r == HJ_OK) r = upload(&p->xbf, xf.data(), d);
+    // eikonal with a moving bump: velocity v_b after x_b (kept only when nonzero)
+    bool moving = false;
+    if (family == HJ_FAMILY_EIKONAL && n_dyn == 4 + 2 * (int64_t)d)
+      for (int i = 0; i < d; ++i) moving = moving || dyn[4 + d + i] != 0.0;
+    if (r == HJ_OK && moving) {
+      p->eik_moving = true;
+      std::vector<float> vf(d);
+      for (int i = 0; i < d; ++i) vf[i] = (float)dyn[4 + d + i];
+      r = upload(&p->vbd, dyn + 4 + d, d);
+      if (r == HJ_OK) r = upload(&p->vbf, vf.data(), d);
+    }
   }
   if (r == HJ_OK && family == HJ_FAMILY_TANH_DRIFT) {
     const size_t n = (size_t)d * d;

@@ -19,6 +19,8 @@
 //                           schemes; cr, cl the contexts at xr, xl)
 // All families have L = |u|^2/2, so H = <p, f0(x)> + |B(x)^T p|^2/2 (Section 2).
 #pragma once
+#include <type_traits>
+
 #include "hj_internal.cuh"
 
 namespace hj {
@@ -133,6 +135,7 @@ template <typename T, int D>
 struct FamQuadratic {
   static constexpr bool kHasGradX = false;
   static constexpr bool kGame = false;
+  static constexpr bool kTimeDep = false;
   struct Shared {};
   struct Ctx {};
   struct PC { T s, lam; };
@@ -179,6 +182,7 @@ struct FamQuadcopter {
   static_assert(D == 12, "quadcopter state is 12-D");
   static constexpr bool kHasGradX = true;
   static constexpr bool kGame = false;
+  static constexpr bool kTimeDep = false;
   struct Shared {};
   struct Ctx { T a[3]; T J[9]; };
   T m_inv, ah, gz, eps;
@@ -381,6 +385,7 @@ template <typename T, int D>
 struct FamTanhDrift {
   static constexpr bool kHasGradX = true;
   static constexpr bool kGame = false;
+  static constexpr bool kTimeDep = false;
   struct Shared { T A[D * D]; };
   struct Ctx { T a[D]; };
   const T* A;
@@ -461,32 +466,50 @@ struct FamTanhDrift {
 // H = c(x) |p|_2 with c(x) = c0 + c1 exp(-c2 |x - x_b|^2) (Section 6.1).  The
 // dual step is the shrink_2 operator, p = v max(|v| - lam c, 0) / |v|, and
 // grad_x H = |p| grad c(x) = |p| (-2 c1 c2 e) (x - x_b), e = exp(-c2 |x - x_b|^2).
-template <typename T, int D>
-struct FamEikonal {
+// MOVING: the bump moves with velocity v_b, c(x - s v_b) at the node time s
+// (Section 6.1's state-and-time-dependent example); the kernel then calls the
+// time-aware members (context_t, Ht_t, H64_t) with s = j delta.
+template <typename T, int D, bool MOVING>
+struct FamEikonalT {
   static constexpr bool kHasGradX = true;
   static constexpr bool kGame = false;
-  struct Shared { T xb[D]; };
-  struct Ctx { T c, gf; };                 // c(x) and -2 c1 c2 e at x^k
+  static constexpr bool kTimeDep = MOVING;
+  struct Shared { T xb[D]; T vb[MOVING ? D : 1]; };
+  struct CtxS { T c, gf; };                // c(x) and -2 c1 c2 e at x^k
+  struct CtxM { T c, gf, s; };             // and the node time
+  using Ctx = typename std::conditional<MOVING, CtxM, CtxS>::type;
   struct PC { T lam; };
   const T* xb;
+  const T* vb;
   const double* xb64;
+  const double* vb64;
   T c0, c1, c2;
   double c0d, c1d, c2d;
   __device__ static void load_shared(const SolveArgs<T>& s, Shared& sh) {
-    for (int i = threadIdx.x; i < D; i += blockDim.x) sh.xb[i] = s.xb[i];
+    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+      sh.xb[i] = s.xb[i];
+      if constexpr (MOVING) sh.vb[i] = s.vb[i];
+    }
   }
-  __device__ FamEikonal(const SolveArgs<T>& s, const Shared& sh)
-      : xb(sh.xb), xb64(s.xb64), c0(T(s.eik_c0)), c1(T(s.eik_c1)), c2(T(s.eik_c2)),
-        c0d(s.eik_c0), c1d(s.eik_c1), c2d(s.eik_c2) {}
+  __device__ FamEikonalT(const SolveArgs<T>& s, const Shared& sh)
+      : xb(sh.xb), vb(sh.vb), xb64(s.xb64), vb64(s.vb64), c0(T(s.eik_c0)), c1(T(s.eik_c1)),
+        c2(T(s.eik_c2)), c0d(s.eik_c0), c1d(s.eik_c1), c2d(s.eik_c2) {}
   __device__ __forceinline__ PC point(T lam) const { return PC{lam}; }
-  __device__ __forceinline__ void context(const T (&x)[D], Ctx& c) const {
+  // the bump centre at time s
+  __device__ __forceinline__ T centre(int k, T s) const {
+    if constexpr (MOVING) return xb[k] + s * vb[k];
+    else return xb[k];
+  }
+  __device__ __forceinline__ void context_t(const T (&x)[D], T s, Ctx& c) const {
     T r2 = T(0);
 #pragma unroll
-    for (int k = 0; k < D; ++k) { const T y = x[k] - xb[k]; r2 += y * y; }
+    for (int k = 0; k < D; ++k) { const T y = x[k] - centre(k, s); r2 += y * y; }
     const T e = exp_t<T>(-c2 * r2);
     c.c = c0 + c1 * e;
     c.gf = T(-2) * c1 * c2 * e;
+    if constexpr (MOVING) c.s = s;
   }
+  __device__ __forceinline__ void context(const T (&x)[D], Ctx& c) const { context_t(x, T(0), c); }
   __device__ __forceinline__ void prox(const Ctx& c, const PC& pc, const T (&)[D],
                                        T (&v)[D]) const {
     T n2 = T(0);
@@ -513,29 +536,40 @@ struct FamEikonal {
     T n2 = T(0);
 #pragma unroll
     for (int k = 0; k < D; ++k) n2 += p[k] * p[k];
-    const T s = sqrt_t<T>(n2) * c.gf;
+    const T sc = sqrt_t<T>(n2) * c.gf;
+    T s = T(0);
+    if constexpr (MOVING) s = c.s;
 #pragma unroll
-    for (int k = 0; k < D; ++k) g[k] = s * (x[k] - xb[k]);
+    for (int k = 0; k < D; ++k) g[k] = sc * (x[k] - centre(k, s));
   }
-  __device__ __forceinline__ double H64(const T (&x)[D], const T (&p)[D]) const {
+  __device__ __forceinline__ double H64_t(const T (&x)[D], const T (&p)[D], double s) const {
     double r2 = 0.0, n2 = 0.0;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const double y = (double)x[k] - xb64[k];
+      const double cb = MOVING ? xb64[k] + s * vb64[k] : xb64[k];
+      const double y = (double)x[k] - cb;
       r2 += y * y;
       n2 += (double)p[k] * (double)p[k];
     }
     return (c0d + c1d * exp(-c2d * r2)) * sqrt(n2);
   }
-  __device__ __forceinline__ T Ht(const T (&x)[D], const T (&p)[D]) const {
+  __device__ __forceinline__ double H64(const T (&x)[D], const T (&p)[D]) const {
+    return H64_t(x, p, 0.0);
+  }
+  __device__ __forceinline__ T Ht_t(const T (&x)[D], const T (&p)[D], T s) const {
     Ctx c;
-    context(x, c);
+    context_t(x, s, c);
     T n2 = T(0);
 #pragma unroll
     for (int k = 0; k < D; ++k) n2 += p[k] * p[k];
     return c.c * sqrt_t<T>(n2);
   }
+  __device__ __forceinline__ T Ht(const T (&x)[D], const T (&p)[D]) const { return Ht_t(x, p, T(0)); }
 };
+template <typename T, int D>
+using FamEikonal = FamEikonalT<T, D, false>;
+template <typename T, int D>
+using FamEikonalMoving = FamEikonalT<T, D, true>;
 
 // ---------------------------------------------------------------- difference-of-norms game
 // Section 6.2's differential game: state z = (x, y), x = z[0..d1) (the
@@ -548,6 +582,7 @@ template <typename T, int D>
 struct FamGame {
   static constexpr bool kHasGradX = true;
   static constexpr bool kGame = true;
+  static constexpr bool kTimeDep = false;
   struct Shared { T zb[D]; };
   struct Ctx { T c1, c2, g1, g2; };        // speeds and gradient factors -2 a b e at z^k
   struct PC { T lam; };

@@ -58,6 +58,10 @@ struct SolveArgs {
   double eik_c0, eik_c1, eik_c2;       // eikonal speed c(x) = c0 + c1 exp(-c2 |x - x_b|^2)
   const double* xb64;                  // [d] eikonal bump centre x_b
   const T* xb;                         // [d] the same in T
+  // eikonal bump moving with velocity v_b: c(x - s v_b) at node time s = j delta
+  int32_t eik_moving;
+  const double* vb64;                  // [d] v_b (null when static)
+  const T* vb;
   // +1, or -1 for the negative eikonal equation: the kernels solve the positive
   // one with the initial data -g (x_0 prox and value with -W^2) and return
   // V and p multiplied by cost_sign
@@ -244,6 +248,8 @@ template <typename T>
 hj_status launch_warp_eikonal_mix(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 template <typename T>
 hj_status launch_warp_game_mix(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
+template <typename T>
+hj_status launch_warp_eikonal_moving(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 template <typename T>
 hj_status launch_warp_game(const SolveArgs<T>& a, WarpConfig cfg, cudaStream_t s);
 // Default launch shape for (family, d, Nmax); {0, 0} when no warp kernel fits.

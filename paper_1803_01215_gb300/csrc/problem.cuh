@@ -19,6 +19,9 @@ struct hj_problem_s {
   double w2max_max = 0.0;             // game: max W_i^2 over the maximiser's coordinates
   double* xbd = nullptr;              // [d] eikonal bump centre
   float* xbf = nullptr;
+  bool eik_moving = false;            // eikonal bump moving with velocity v_b
+  double* vbd = nullptr;              // [d] v_b
+  float* vbf = nullptr;
   double* W2 = nullptr;               // [d]  W_i^2
   double* W = nullptr;                // [d]  W_i as given (sign kept for dV/dW)
   double* c = nullptr;                // [d]
@@ -53,6 +56,7 @@ inline void release(hj_problem_s* p) {
   cudaFree(p->W2); cudaFree(p->W); cudaFree(p->c);
   cudaFree(p->Af); cudaFree(p->Atf); cudaFree(p->Ad); cudaFree(p->Atd);
   cudaFree(p->xbd); cudaFree(p->xbf);
+  cudaFree(p->vbd); cudaFree(p->vbf);
   cudaFree(p->counter);
   delete p;
 }
@@ -78,7 +82,8 @@ hj_status dispatch(hj_problem_s* p, const hj::SolveArgs<T>& a, hj::WarpConfig cf
   }
   if (a.scheme != HJ_SCHEME_BE || a.value_stop) return HJ_ERR_UNSUPPORTED;   // register kernel only
   if (p->family == HJ_FAMILY_TANH_DRIFT) return hj::launch_td_cta_solver<T>(a, true, s);
-  if (p->family == HJ_FAMILY_EIKONAL) return hj::launch_eik_cta_solver<T>(a, s);
+  if (p->family == HJ_FAMILY_EIKONAL)
+    return a.eik_moving ? HJ_ERR_UNSUPPORTED : hj::launch_eik_cta_solver<T>(a, s);
   if (p->family == HJ_FAMILY_GAME_NORMS) return HJ_ERR_UNSUPPORTED;   // register kernel only
   if (p->family == HJ_FAMILY_QUADRATIC) return hj::launch_td_cta_solver<T>(a, false, s);
   return HJ_ERR_UNSUPPORTED;
@@ -95,7 +100,7 @@ inline void fill_args<float>(hj::SolveArgs<float>& a, const hj_problem_s* prob, 
                       const hj_solver_opts& o, const double* xq, const double* t, double* V,
                       int32_t* iters, int8_t* status, void* traj_x, void* traj_p,
                       const void* warm_x, const void* warm_p) {
-  a.A = prob->Af; a.At = prob->Atf; a.xb = prob->xbf;
+  a.A = prob->Af; a.At = prob->Atf; a.xb = prob->xbf; a.vb = prob->vbf;
   a.traj_x = static_cast<float*>(traj_x); a.traj_p = static_cast<float*>(traj_p);
   a.warm_x = static_cast<const float*>(warm_x); a.warm_p = static_cast<const float*>(warm_p);
   (void)B; (void)N; (void)o; (void)xq; (void)t; (void)V; (void)iters; (void)status;
@@ -106,7 +111,7 @@ inline void fill_args<double>(hj::SolveArgs<double>& a, const hj_problem_s* prob
                        const hj_solver_opts& o, const double* xq, const double* t, double* V,
                        int32_t* iters, int8_t* status, void* traj_x, void* traj_p,
                        const void* warm_x, const void* warm_p) {
-  a.A = prob->Ad; a.At = prob->Atd; a.xb = prob->xbd;
+  a.A = prob->Ad; a.At = prob->Atd; a.xb = prob->xbd; a.vb = prob->vbd;
   a.traj_x = static_cast<double*>(traj_x); a.traj_p = static_cast<double*>(traj_p);
   a.warm_x = static_cast<const double*>(warm_x); a.warm_p = static_cast<const double*>(warm_p);
   (void)B; (void)N; (void)o; (void)xq; (void)t; (void)V; (void)iters; (void)status;
@@ -139,6 +144,8 @@ hj::SolveArgs<T> make_args(const hj_problem_s* prob, int64_t B, int32_t N,
   a.qc_m = prob->qc[0]; a.qc_ah = prob->qc[1]; a.qc_gz = prob->qc[2]; a.qc_eps = prob->qc[3];
   a.eik_c0 = prob->eik[1]; a.eik_c1 = prob->eik[2]; a.eik_c2 = prob->eik[3];
   a.xb64 = prob->xbd;
+  a.vb64 = prob->vbd;
+  a.eik_moving = prob->eik_moving ? 1 : 0;
   a.cost_sign = (prob->family == HJ_FAMILY_EIKONAL && prob->eik[0] < 0) ? -1.0 : 1.0;
   a.game_d1 = (prob->family == HJ_FAMILY_GAME_NORMS) ? (int32_t)prob->eik[0] : prob->d;
   a.counter = prob->counter;
@@ -176,6 +183,8 @@ inline hj_status check_formulation(const hj_problem_s* p, const hj_solver_opts& 
       (o.formulation != HJ_FORM_LAX || o.inner_steps != 1))
     return HJ_ERR_UNSUPPORTED;
   if (o.formulation == HJ_FORM_HOPF && p->family == HJ_FAMILY_EIKONAL) return HJ_ERR_UNSUPPORTED;
+  // a moving bump: backward-Euler Lax form (the register kernel)
+  if (p->eik_moving && o.scheme != HJ_SCHEME_BE) return HJ_ERR_UNSUPPORTED;
   if (o.formulation == HJ_FORM_HOPF && !p->w_nonzero) return HJ_ERR_INVALID_ARG;
   if (p->family == HJ_FAMILY_EIKONAL && p->eik[0] < 0 && !(o.tau * p->w2max < 1.0))
     return HJ_ERR_STEP_SIZE;

@@ -73,7 +73,8 @@ hj_status launch_warp_solver(int family, const SolveArgs<T>& a, WarpConfig cfg, 
     case HJ_FAMILY_TANH_DRIFT:
       return hopf ? launch_warp_tanh_hopf<T>(a, cfg, s) : launch_warp_tanh<T>(a, cfg, s);
     case HJ_FAMILY_EIKONAL:
-      return hopf ? HJ_ERR_UNSUPPORTED : launch_warp_eikonal<T>(a, cfg, s);
+      if (hopf) return HJ_ERR_UNSUPPORTED;
+      return a.eik_moving ? launch_warp_eikonal_moving<T>(a, cfg, s) : launch_warp_eikonal<T>(a, cfg, s);
     case HJ_FAMILY_GAME_NORMS:
       return hopf ? HJ_ERR_UNSUPPORTED : launch_warp_game<T>(a, cfg, s);
     default: return HJ_ERR_UNSUPPORTED;

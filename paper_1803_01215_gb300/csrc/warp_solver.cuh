@@ -138,6 +138,25 @@ __device__ __forceinline__ void slot_load(const T* src, T (&v)[D]) {
   }
 }
 
+// H quantities of node j at its time s_j = j delta (time-dependent families)
+template <class F, typename T, int D>
+__device__ __forceinline__ void node_context(const F& fam, const T (&x)[D], T sj,
+                                             typename F::Ctx& c) {
+  if constexpr (F::kTimeDep) fam.context_t(x, sj, c);
+  else fam.context(x, c);
+}
+template <class F, typename T, int D>
+__device__ __forceinline__ T node_Ht(const F& fam, const T (&x)[D], const T (&p)[D], T sj) {
+  if constexpr (F::kTimeDep) return fam.Ht_t(x, p, sj);
+  else return fam.Ht(x, p);
+}
+template <class F, typename T, int D>
+__device__ __forceinline__ double node_H64(const F& fam, const T (&x)[D], const T (&p)[D],
+                                           double sj) {
+  if constexpr (F::kTimeDep) return fam.H64_t(x, p, sj);
+  else return fam.H64(x, p);
+}
+
 // relaxation z = x_new + theta (x_new - x); TH1: theta = 1 (the paper's choice,
 // Section 6), one fused multiply-add per coordinate
 template <typename T, bool TH1>
@@ -253,7 +272,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
       if (jbase + i <= N) {
-        fam.context(x[i], ctx[i]);
+        node_context(fam, x[i], T(jbase + i) * delta_t, ctx[i]);
         T v[D], dz[D];
         if (i == 0) v_sub<T, D>(dz, z[i], zl);
         else v_sub<T, D>(dz, z[i], z[i > 0 ? i - 1 : 0]);
@@ -362,7 +381,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
           v_fma<T, D>(xn, taud, g, base);                    // + tau delta grad_x H
           for (int s = 1; s < a.inner_steps; ++s) {
             typename F::Ctx c2;
-            fam.context(xn, c2);
+            node_context(fam, xn, T(jbase + i) * delta_t, c2);
             fam.gradx(c2, xn, p[i], g);
             v_fma<T, D>(xn, taud, g, base);
           }
@@ -377,7 +396,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
             T s = T(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) s += coord_sign(k) * dp[k] * xn[k];
-            vacc += s - delta_t * fam.Ht(xn, p[i]);
+            vacc += s - delta_t * node_Ht(fam, xn, p[i], T(jbase + i) * delta_t);
           }
         }
         if constexpr (TH1) {
@@ -394,7 +413,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
             T s = T(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) s += coord_sign(k) * p[i][k] * x[i][k];
-            vacc += s - delta_t * fam.Ht(x[i], p[i]);
+            vacc += s - delta_t * node_Ht(fam, x[i], p[i], T(jbase + i) * delta_t);
           }
         }
       }
@@ -474,7 +493,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
             const T hl = (i == 0) ? fam.Ht(xl, p[i]) : fam.Ht(x[i > 0 ? i - 1 : 0], p[i]);
             acc += (double)(s - delta_t * (wr * fam.Ht(x[i], p[i]) + wl * hl));
           } else {
-            acc += (double)(s - delta_t * fam.Ht(x[i], p[i]));
+            acc += (double)(s - delta_t * node_Ht(fam, x[i], p[i], T(jbase + i) * delta_t));
           }
         } else {
           double s = 0.0;
@@ -489,7 +508,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
             const double hl = (i == 0) ? fam.H64(xl, p[i]) : fam.H64(x[i > 0 ? i - 1 : 0], p[i]);
             acc += s - delta * (a.mix_wr * fam.H64(x[i], p[i]) + a.mix_wl * hl);
           } else {
-            acc += s - delta * fam.H64(x[i], p[i]);
+            acc += s - delta * node_H64(fam, x[i], p[i], (double)(jbase + i) * delta);
           }
         }
       }

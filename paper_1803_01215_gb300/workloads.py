@@ -119,6 +119,17 @@ def eikonal(d=2, sign=1, t=0.2, B=None, grid_step=0.1, seed=8):
                 seed=seed, init_radius=0.1, g_const=EIK_G_CONST)
 
 
+def eikonal_moving(t=0.2, B=None, grid_step=0.1, seed=8, d=2):
+    """Section 6.1's state-and-time-dependent eikonal: H(x, p, s) = c(x - s v_b)|p|
+    with the bump of eikonal() moving with velocity v_b = (-1, 1, 0, ...), the
+    positive equation, the same g, delta = 0.02 and sigma = 0.5 (tau = 0.24 / sigma)."""
+    w = eikonal(d=d, sign=1, t=t, B=B, grid_step=grid_step, seed=seed)
+    vb = np.zeros(d)
+    vb[0], vb[1] = -1.0, 1.0
+    w["dyn"] = np.concatenate([w["dyn"], vb])
+    return w
+
+
 def game_norms(d=2, t=0.1, B=None, grid_step=1.0 / 12.0, seed=9):
     """Section 6.2's difference-of-norms game: z = (x, y) with x = z[0] (d1 = 1)
     and y = z[1..d), H = c1(z)|p| - c2(z)|q|, c1(z) = 1 + 3 exp(-4 |z - (1, 1, 0, ...)|^2),

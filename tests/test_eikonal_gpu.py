@@ -115,3 +115,59 @@ def test_eikonal_argument_errors():
     bad["dyn"][0] = 0.5                           # the sign must be +1 or -1
     with pytest.raises(binding.HJError):
         binding.Problem.from_workload(bad)
+
+
+def _wm(d, N, B, seed=54):
+    w = W.eikonal_moving(d=d, B=B, seed=seed)
+    w["N"] = N
+    w["t"] = np.full(B, N * W.EIK_DELTA)
+    return w
+
+
+@pytest.mark.parametrize("d,N", [(2, 10), (2, 40), (10, 23)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_moving_bump_fixed_iterations_elementwise(d, N, precision):
+    """H(x, p, s) = c(x - s v_b)|p| at the node times s_j = j delta (Section
+    6.1's moving bump), element-wise against the oracle."""
+    w = _wm(d, N, 21)
+    K = 150
+    g = gpu(w, precision, tol=0.0, max_iter=K, check_every=K)
+    o = O.solve(w, tol=0.0, max_iter=K, check_every=K)
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    ex = np.max(np.abs(g["traj_x"] - o["x"]))
+    ep = np.max(np.abs(g["traj_p"] - o["p"]))
+    print(f"moving bump d={d} N={N} {precision}: |dx| {ex:.2e} |dp| {ep:.2e}")
+    assert ex <= tol and ep <= tol
+    assert np.max(value_err(g["V"], o["V"])) <= (1e-9 if precision == "fp64" else 1e-4)
+
+
+def test_moving_bump_same_stop_value_test_and_errors():
+    from paper_1803_01215_gb300 import binding
+    w = _wm(2, 10, 24, seed=55)
+    o = O.solve(w)
+    g = gpu(w, "fp64")
+    assert np.all(o["status"] == O.CONVERGED)
+    same = g["iters"] == o["iters"]
+    assert np.mean(same) >= 0.8
+    assert value_err(g["V"][same], o["V"][same]).max() <= 1e-9
+    g32 = gpu(w, "fp32")
+    oc = O.solve(w, tol=1e-22, max_iter=200000, check_every=8)
+    ok = (g32["status"] == O.CONVERGED) & (oc["status"] == O.CONVERGED)
+    assert np.mean(ok) >= 0.9 and value_err(g32["V"][ok], oc["V"][ok]).max() <= 1e-4
+    # the value test evaluates H at the node times too
+    wv = dict(w, tol=1e-30, max_iter=4000)
+    gv, ov = gpu(wv, "fp64", value_tol=1e-6), O.solve(wv, value_tol=1e-6)
+    same = (gv["iters"] == ov["iters"]) & (ov["status"] == O.VALUE_STOP)
+    assert np.mean(same) >= 0.8 and value_err(gv["V"][same], ov["V"][same]).max() <= 1e-9
+    prob = binding.Problem.from_workload(w)
+    xq = torch.as_tensor(w["xq"], device="cuda")
+    t = torch.as_tensor(w["t"], device="cuda")
+    with pytest.raises(binding.HJError) as e:
+        binding.solve_batch(prob, xq, t, 10, binding.make_opts(sigma=0.5, tau=0.48, scheme="trap"))
+    assert e.value.code == 2
+    w3 = _wm(3, 10, 3)                                   # d = 3: coordinate-parallel kernel, static only
+    p3 = binding.Problem.from_workload(w3)
+    with pytest.raises(binding.HJError) as e:
+        binding.solve_batch(p3, torch.as_tensor(w3["xq"], device="cuda"), t[:3], 10,
+                            binding.make_opts(sigma=0.5, tau=0.48))
+    assert e.value.code == 2
