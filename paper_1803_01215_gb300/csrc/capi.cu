@@ -32,7 +32,7 @@ const char* hj_status_str(hj_status s) {
   return "unknown status";
 }
 
-int32_t hj_version(void) { return 101; }
+int32_t hj_version(void) { return 102; }
 
 hj_status hj_problem_create(hj_problem* out, int32_t family, int32_t d, const double* dyn,
                             int64_t n_dyn, const double* W, const double* c) {
