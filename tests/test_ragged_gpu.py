@@ -164,3 +164,36 @@ def test_ragged_autotune_of_inner_steps_keeps_the_fixed_point():
     ok = (out["status"].cpu().numpy() == 0) & (ref["status"].cpu().numpy() == 0)
     assert np.mean(ok) >= 0.95
     assert np.max(value_err(out["V"].cpu().numpy()[ok], V0[ok])) <= 1e-4
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ragged_small_N_with_autotuned_shapes(precision):
+    """Eikonal and game points with N <= 16 in one plan: after the autotuner has
+    timed every shape (half-warp groups included) the plan still reproduces the
+    oracles element-wise."""
+    from oracle import game_pdhg as GO
+    from paper_1803_01215_gb300 import workloads as Wl
+    we = Wl.eikonal(d=2, sign=1, B=1, seed=91)
+    wg = Wl.game_norms(d=2, B=1, seed=92)
+    keys = ("family", "d", "dyn", "W", "c")
+    rw = dict(problems=[{k: we[k] for k in keys}, {k: wg[k] for k in keys}],
+              sigma=50.0, tau=0.0048, tol=0.0, max_iter=40, check_every=40, seed=7,
+              init_radius=0.1)                   # the game's steps (Section 6.2) for both
+    r = np.random.default_rng(93)
+    B = 50
+    rw["prob_of"] = r.integers(0, 2, size=B).astype(np.int32)
+    rw["N_of"] = r.choice(np.array([5, 10, 15], dtype=np.int32), size=B)
+    rw["xq"] = [r.uniform(-3, 3, 2) for _ in range(B)]
+    rw["t"] = 0.02 * rw["N_of"].astype(np.float64)
+    plan, xq, t = _plan(rw, precision)
+    plan.autotune(xq, t, repeats=1)
+    out = {k: v.cpu().numpy() for k, v in plan.solve(xq, t, return_traj=True).items()}
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    for k, N in _groups(rw):
+        g = W.ragged_group(rw, k, N)
+        solve = GO.solve_game if k == 1 else O.solve
+        o = solve(g, tol=0.0, max_iter=40, check_every=40)
+        for i, b in enumerate(g["point_index"]):
+            assert np.max(np.abs(plan.point_traj(out["traj_x"], b) - o["x"][i])) <= tol, (k, N, b)
+        assert np.max(value_err(out["V"][g["point_index"]], o["V"])) <= \
+            (1e-9 if precision == "fp64" else 1e-4)
