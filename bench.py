@@ -32,9 +32,10 @@ from paper_1803_01215_gb300 import workloads as W  # noqa: E402
 METRIC = "converged HJ solves/sec (V at 1e-4 rel vs FP64) and % FP32 peak, FP32 vs FP64 GPU"
 UNIT = "solves/s"
 # FP32 flops of one (node, iteration) of the quadcopter update (FMA = 2): the
-# dual prox with its Sherman-Morrison solve, the thrust direction and Jacobian
-# from the three sin/cos pairs, the x-gradient, the x step and the relaxation.
-# sin/cos are transcendental and not counted.  Derivation in the design doc.
+# dual increment 36, the thrust direction and Jacobian from the three sin/cos
+# pairs 21, the prox with its Sherman-Morrison solve 61, the x-gradient 26, the
+# x step with its gradient term and the relaxation 96.  sin/cos are
+# transcendental and not counted.
 QC_FLOPS_PER_NODE_ITER = 240
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the timed FP32
