@@ -231,14 +231,16 @@ hj_status hj_solve_batch(hj_problem prob, int64_t B,
  *   dL_dV    (device) [B] weights w_b (e.g. 1/B for the mean value).
  *   dW, dc   (device) [d] double out: sum_b w_b dV_b/dW, dV_b/dc (zeroed first).
  *   ddyn     (device) [n_dyn] double out, the family's dyn layout (quadcopter:
- *            m, a_h, g_z, eps; tanh drift: A row-major; NULL for quadratic).
+ *            m, a_h, g_z, eps; tanh drift: A row-major; eikonal: 0 for the
+ *            sign, then c0, c1, c2, x_b, and v_b for a moving bump; NULL for
+ *            quadratic).
  *   dxq      (device, may be NULL) [B][d] double out: w_b dV_b/dx_q.
  * Node arithmetic runs in the trajectory type, all sums in FP64.  The result is
  * the gradient of the value at the given iterates; it equals the derivative of
  * the converged value to the accuracy the iterates satisfy the saddle
  * conditions (Appendix A.1 stopping rule).
  * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_UNSUPPORTED (tanh drift with d > 128; the
- * eikonal family, whose H is not differentiable in p at 0), HJ_ERR_CUDA.     */
+ * game), HJ_ERR_CUDA.                                                        */
 hj_status hj_solve_grad(hj_problem prob, int64_t B, const double* t, int32_t N,
                         int32_t precision, const void* traj_x, const void* traj_p,
                         const double* dL_dV, double* dW, double* dc, double* ddyn, double* dxq,

@@ -112,6 +112,7 @@ class Problem:
         h = ctypes.c_void_p()
         r = _lib().hj_problem_create(ctypes.byref(h), self.family, self.d,
                                      dyn_p if dyn_a.size else None, dyn_a.size, w_p, c_p)
+        self.n_dyn = int(dyn_a.size)
         if r != HJ_OK:
             raise HJError(r, "hj_problem_create")
         self.handle = h
@@ -177,7 +178,8 @@ def _ptr(t):
 
 
 def n_dyn(problem):
-    return {0: 0, 1: 4, 2: problem.d * problem.d, 3: 4 + problem.d, 4: 4 + problem.d}[problem.family]
+    """Length of the problem's dyn array (the layout hj_solve_grad's ddyn follows)."""
+    return problem.n_dyn
 
 
 def solve_grad(problem, t, N, precision, traj_x, traj_p, dL_dV, want_dxq=True, stream=None):

@@ -176,10 +176,11 @@ hj_status hj_solve_grad(hj_problem prob, int64_t B, const double* t, int32_t N,
                         void* stream) {
   if (prob == nullptr || B < 0 || N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;
   if (precision != HJ_PREC_FP32 && precision != HJ_PREC_FP64) return HJ_ERR_INVALID_ARG;
-  if (prob->family == HJ_FAMILY_EIKONAL || prob->family == HJ_FAMILY_GAME_NORMS)
-    return HJ_ERR_UNSUPPORTED;
+  if (prob->family == HJ_FAMILY_GAME_NORMS) return HJ_ERR_UNSUPPORTED;
   const int n_dyn = prob->family == HJ_FAMILY_QUADCOPTER ? 4
-                    : prob->family == HJ_FAMILY_TANH_DRIFT ? prob->d * prob->d : 0;
+                    : prob->family == HJ_FAMILY_TANH_DRIFT ? prob->d * prob->d
+                    : prob->family == HJ_FAMILY_EIKONAL ? 4 + prob->d * (prob->eik_moving ? 2 : 1)
+                    : 0;
   if (dW == nullptr || dc == nullptr || (n_dyn > 0 && ddyn == nullptr)) return HJ_ERR_INVALID_ARG;
   int cur = 0;
   if (cudaGetDevice(&cur) != cudaSuccess) return HJ_ERR_CUDA;
@@ -198,6 +199,9 @@ hj_status hj_solve_grad(hj_problem prob, int64_t B, const double* t, int32_t N,
     g.X = static_cast<const float*>(traj_x); g.P = static_cast<const float*>(traj_p);
     g.w = dL_dV; g.W = prob->W; g.W2 = prob->W2; g.c = prob->c; g.A = prob->Af;
     g.qc_m = prob->qc[0]; g.qc_ah = prob->qc[1]; g.qc_gz = prob->qc[2]; g.qc_eps = prob->qc[3];
+    g.cost_sign = prob->eik[0] < 0 ? -1.0 : 1.0;
+    g.eik_c0 = prob->eik[1]; g.eik_c1 = prob->eik[2]; g.eik_c2 = prob->eik[3];
+    g.xb64 = prob->xbd; g.vb64 = prob->vbd;
     g.dW = dW; g.dc = dc; g.ddyn = ddyn; g.dxq = dxq;
     return hj::launch_value_grad<float>(prob->family, g, s);
   }
@@ -206,6 +210,9 @@ hj_status hj_solve_grad(hj_problem prob, int64_t B, const double* t, int32_t N,
   g.X = static_cast<const double*>(traj_x); g.P = static_cast<const double*>(traj_p);
   g.w = dL_dV; g.W = prob->W; g.W2 = prob->W2; g.c = prob->c; g.A = prob->Ad;
   g.qc_m = prob->qc[0]; g.qc_ah = prob->qc[1]; g.qc_gz = prob->qc[2]; g.qc_eps = prob->qc[3];
+  g.cost_sign = prob->eik[0] < 0 ? -1.0 : 1.0;
+  g.eik_c0 = prob->eik[1]; g.eik_c1 = prob->eik[2]; g.eik_c2 = prob->eik[3];
+  g.xb64 = prob->xbd; g.vb64 = prob->vbd;
   g.dW = dW; g.dc = dc; g.ddyn = ddyn; g.dxq = dxq;
   return hj::launch_value_grad<double>(prob->family, g, s);
 }

@@ -181,6 +181,10 @@ struct GradArgs {
   const double* c;       // [d]
   const T* A;            // tanh drift [d][d]
   double qc_m, qc_ah, qc_gz, qc_eps;
+  // eikonal: V = cost_sign V_int, speed c(x - s v_b) = c0 + c1 exp(-c2 |x - s v_b - x_b|^2)
+  double cost_sign, eik_c0, eik_c1, eik_c2;
+  const double* xb64;    // [d]
+  const double* vb64;    // [d] or null (static bump)
   double* dW;            // [d]      accumulated (atomicAdd)
   double* dc;            // [d]
   double* ddyn;          // [n_dyn]

@@ -11,6 +11,13 @@
 //   dV/dx_q     = p_N - delta grad_x H(x_N, p_N)        (x_N = x_q is pinned)
 // Per-node arithmetic runs in the trajectory's type; every sum over nodes,
 // points and the batch is accumulated in FP64.
+// Eikonal family (V = s V_int, V_int the positive equation's value for the
+// data s g, returned p = s p_int): H = c(x_j - s_j v_b)|p_j|, so with
+// e_j = exp(-c2 r_j^2), r_j = |x_j - x_b - s_j v_b| and a_j = 2 c1 c2 e_j |p_j|,
+//   dV/d(c0, c1, c2) = -s delta sum_j |p_j| (1, e_j, -c1 r_j^2 e_j),
+//   dV/dx_b = -s delta sum_j a_j (x_j - x_b - s_j v_b),   dV/dv_b: the same times s_j,
+//   dV/dx_q = p_N + s delta a_N (x_N - x_b - t v_b);
+// W and c keep the formulas above (the sign enters g and V alike).
 #include <cuda_runtime.h>
 
 #include "families.cuh"
@@ -24,7 +31,7 @@ __device__ __forceinline__ void qc_dir(T psi, T th, T ph, T (&a)[3], T (&J)[9]) 
   FamQuadcopter<T, 12>::template thrust<T>(psi, th, ph, a, J);
 }
 
-// family 0: quadratic, 1: quadcopter, 2: tanh drift
+// family 0: quadratic, 1: quadcopter, 2: tanh drift, 3: eikonal
 template <typename T, int FAM>
 __global__ void __launch_bounds__(256) value_grad_kernel(const GradArgs<T> g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -35,6 +42,7 @@ __global__ void __launch_bounds__(256) value_grad_kernel(const GradArgs<T> g) {
   T* sA = reinterpret_cast<T*>(acc_dyn + g.n_dyn);         // tanh drift: [d][d]
   T* su = sA + (FAM == 2 ? d * d : 0);                     // tanh drift: [d]
   T* sx = su + (FAM == 2 ? d : 0);                         // tanh drift: [d]
+  double* nodeA = reinterpret_cast<double*>(acc_dyn + g.n_dyn);   // eikonal: [N + 1] a_j
   for (int e = tid; e < 2 * d + g.n_dyn; e += nthr) acc_W[e] = 0.0;
   if (FAM == 2)
     for (int e = tid; e < d * d; e += nthr) sA[e] = g.A[e];
@@ -95,6 +103,52 @@ __global__ void __launch_bounds__(256) value_grad_kernel(const GradArgs<T> g) {
         for (int k = 0; k < 3; ++k) gx[9 + k] = (double)p[3 + k];
         for (int k = 0; k < 12; ++k) g.dxq[b * d + k] = wb * ((double)p[k] - delta * gx[k]);
       }
+    } else if (FAM == 3) {
+      // node scalars |p_j|, e_j, r_j^2 (threads over nodes), then the x_b and v_b
+      // sums (threads over coordinates)
+      const double sgn = g.cost_sign, c1 = g.eik_c1, c2 = g.eik_c2;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+      for (int j = 1 + tid; j <= N; j += nthr) {
+        const double sj = j * delta;
+        double r2 = 0.0, n2 = 0.0;
+        for (int k = 0; k < d; ++k) {
+          const double ctr = g.xb64[k] + (g.vb64 ? sj * g.vb64[k] : 0.0);
+          const double y = (double)X[(size_t)j * d + k] - ctr;
+          const double pk = (double)P[(size_t)j * d + k];
+          r2 += y * y;
+          n2 += pk * pk;
+        }
+        const double e = exp(-c2 * r2), np = sqrt(n2);
+        s0 += np;
+        s1 += np * e;
+        s2 += -c1 * r2 * e * np;
+        nodeA[j] = 2.0 * c1 * c2 * e * np;
+      }
+      s0 = warp_sum<double>(s0); s1 = warp_sum<double>(s1); s2 = warp_sum<double>(s2);
+      if ((tid & 31) == 0) {
+        atomicAdd(&acc_dyn[1], -sgn * wb * delta * s0);
+        atomicAdd(&acc_dyn[2], -sgn * wb * delta * s1);
+        atomicAdd(&acc_dyn[3], -sgn * wb * delta * s2);
+      }
+      __syncthreads();
+      for (int k = tid; k < d; k += nthr) {
+        double sb = 0.0, sv = 0.0;
+        for (int j = 1; j <= N; ++j) {
+          const double sj = j * delta;
+          const double ctr = g.xb64[k] + (g.vb64 ? sj * g.vb64[k] : 0.0);
+          const double term = nodeA[j] * ((double)X[(size_t)j * d + k] - ctr);
+          sb += term;
+          sv += term * sj;
+        }
+        acc_dyn[4 + k] += -sgn * wb * delta * sb;
+        if (g.vb64) acc_dyn[4 + d + k] += -sgn * wb * delta * sv;
+        if (g.dxq != nullptr) {
+          const double ctr = g.xb64[k] + (g.vb64 ? N * delta * g.vb64[k] : 0.0);
+          g.dxq[b * d + k] = wb * ((double)P[(size_t)N * d + k] +
+                                   sgn * delta * nodeA[N] * ((double)X[(size_t)N * d + k] - ctr));
+        }
+      }
+      __syncthreads();                             // nodeA is rewritten for the next point
     } else {
       // dH/dA_ik = u_i x_k with u = p * (1 - tanh(A x)^2); node sums in T, point sum in FP64
       T part[kPairs];
@@ -147,7 +201,8 @@ hj_status launch_value_grad(int family, const GradArgs<T>& g, cudaStream_t s) {
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return HJ_ERR_CUDA;
   const size_t smem = (size_t)(2 * g.d + g.n_dyn) * sizeof(double) +
-                      (family == HJ_FAMILY_TANH_DRIFT ? (size_t)(g.d * g.d + 2 * g.d) * sizeof(T) : 0);
+                      (family == HJ_FAMILY_TANH_DRIFT ? (size_t)(g.d * g.d + 2 * g.d) * sizeof(T) : 0) +
+                      (family == HJ_FAMILY_EIKONAL ? (size_t)(g.N + 1) * sizeof(double) : 0);
   if (smem > 227u * 1024u) return HJ_ERR_UNSUPPORTED;
   const int64_t grid64 = g.B < (int64_t)nsm * 2 ? g.B : (int64_t)nsm * 2;
   const int grid = (int)(grid64 > 0 ? grid64 : 1);
@@ -166,6 +221,12 @@ hj_status launch_value_grad(int family, const GradArgs<T>& g, cudaStream_t s) {
                                (int)smem);
       if (e != cudaSuccess) return HJ_ERR_CUDA;
       value_grad_kernel<T, 2><<<grid, threads, smem, s>>>(g);
+      break;
+    case HJ_FAMILY_EIKONAL:
+      e = cudaFuncSetAttribute(value_grad_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return HJ_ERR_CUDA;
+      value_grad_kernel<T, 3><<<grid, threads, smem, s>>>(g);
       break;
     default:
       return HJ_ERR_UNSUPPORTED;

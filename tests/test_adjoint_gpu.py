@@ -196,3 +196,39 @@ def test_unrolled_matches_envelope_at_convergence_fp32():
     for key in ("dW", "ddyn", "dxq"):
         a, b = gu[key].cpu().numpy(), ge[key].cpu().numpy()
         assert np.max(np.abs(a - b)) <= 2e-3 * max(1.0, np.max(np.abs(b))), key
+
+
+def _fd_tol(w, field, i, tol, h=1e-4):
+    wp, wm = dict(w), dict(w)
+    vp = np.array(w[field], dtype=float).copy(); vp.reshape(-1)[i] += h
+    vm = np.array(w[field], dtype=float).copy(); vm.reshape(-1)[i] -= h
+    wp[field], wm[field] = vp, vm
+    kw = dict(tol=tol, check_every=1, max_iter=200000)
+    return (np.mean(O.solve(wp, **kw)["V"]) - np.mean(O.solve(wm, **kw)["V"])) / (2 * h)
+
+
+@pytest.mark.parametrize("sign,moving", [(1, False), (-1, False), (1, True)])
+def test_eikonal_gradient_vs_finite_differences(sign, moving):
+    """Envelope gradient of the eikonal value (Section 6.1's bump, the negative
+    equation through phi = -psi, the moving bump) against central differences
+    of the FP64 oracle's converged value: cost weights and centre, the speed's
+    c0, c1, c2, the bump centre and velocity, and the query point."""
+    w = (W.eikonal_moving(d=2, B=3, seed=57) if moving else
+         W.eikonal(d=2, sign=sign, B=3, seed=56))
+    w["N"] = 6
+    w["t"] = np.full(3, 6 * W.EIK_DELTA)
+    tol = 1e-20 if sign < 0 else 1e-24
+    g = _gpu_grads(w, "fp64")
+    def close(a, b):
+        return abs(a - b) <= 2e-5 * max(1.0, abs(b))
+    for field, i, got in [("W", 0, g["dW"][0]), ("c", 1, g["dc"][1]),
+                          ("dyn", 1, g["ddyn"][1]), ("dyn", 2, g["ddyn"][2]),
+                          ("dyn", 3, g["ddyn"][3]), ("dyn", 4, g["ddyn"][4]),
+                          ("dyn", 5, g["ddyn"][5])] + \
+                         ([("dyn", 6, g["ddyn"][6]), ("dyn", 7, g["ddyn"][7])] if moving else []):
+        fd = _fd_tol(w, field, i, tol)
+        assert close(got, fd), (field, i, got, fd)
+    for k in (0, 1):
+        fd = _fd_tol(w, "xq", np.ravel_multi_index((1, k), w["xq"].shape), tol)
+        assert close(g["dxq"][1, k], fd), ("xq", k, g["dxq"][1, k], fd)
+    assert g["ddyn"][0] == 0.0
