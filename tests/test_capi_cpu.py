@@ -65,3 +65,31 @@ def test_invalid_arguments_rejected_before_device_use(lib):
     assert lib.hj_solve_batch(None, 4, None, None, 8, ctypes.byref(opts),
                               None, None, None, None, None, None, None, None) == 1
     assert lib.hj_problem_destroy(None) == 0
+
+
+def test_option_structs_match_the_header_layout(tmp_path):
+    """The ctypes mirrors of hj_solver_opts and hj_retry_policy have the C
+    header's size and field offsets (a plain C probe compiled with the host
+    compiler prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"hj_solver_opts": binding.SolverOpts, "hj_retry_policy": binding.RetryPolicy}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "hjpdhg.h"', 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
