@@ -8,7 +8,6 @@ backward = hj_solve_grad  (adjoint="envelope": the adjoint of the value at the
            hj_solve_grad_unrolled (adjoint="unrolled": reverse sweep through the
            iterations each point ran, checkpointed every `checkpoint_every`)
 """
-import numpy as np
 import torch
 
 from . import binding
