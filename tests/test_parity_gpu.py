@@ -360,3 +360,19 @@ def test_half_warp_groups_match_the_oracle(family, d, N, precision):
     assert np.max(value_err(g["V"], o["V"])) <= (1e-9 if precision == "fp64" else 1e-4)
     with pytest.raises(binding.HJError):
         binding.set_launch_shape(prob, precision, 17, 0, 1)        # 16 lanes hold N <= 16
+
+
+def test_gpu_trajectories_certified_by_the_kkt_residual():
+    """Any trajectory, GPU or CPU, is certified by the discrete characteristic
+    equations evaluated in FP64 (the oracle's kkt_residual): the FP64 path's
+    converged iterates satisfy them to 1e-9, the FP32 path's to its rounding,
+    and the two precisions land on the same saddle (same value to 1e-4)."""
+    w = W.quadcopter(B=16, seed=41, N=32, t=0.5)
+    g64 = gpu(w, "fp64", tol=1e-24, check_every=16, max_iter=100000)
+    g32 = gpu(w, "fp32", tol=1e-11, check_every=16, max_iter=100000)
+    r64 = O.kkt_residual(w, g64["traj_x"], g64["traj_p"])
+    r32 = O.kkt_residual(w, g32["traj_x"].astype(np.float64), g32["traj_p"].astype(np.float64))
+    print(f"KKT residual: FP64 max {r64.max():.2e}, FP32 max {r32.max():.2e}")
+    assert r64.max() <= 1e-9
+    assert r32.max() <= 1e-4
+    assert value_err(g32["V"], g64["V"]).max() <= 1e-4
