@@ -35,7 +35,7 @@ returned V and p are those of phi (V = -V_psi, p = -p_psi), x is shared.
 import numpy as np
 
 from .counter_rng import uniform_pm1
-from .families import QuadCost, make_family
+from .families import Eikonal, QuadCost, make_family
 
 CONVERGED, MAX_ITER, NONFINITE = 0, 1, 2
 VALUE_STOP = 4     # stopped by the value test (the paper's switch for slow points)
@@ -172,20 +172,42 @@ def solve(w, *, N=None, sigma=None, tau=None, theta=1.0, tol=None, max_iter=None
                 rx=rx_all, rp=rp_all)
 
 
-def kkt_residual(w, x, p, activation="tanh"):
-    """Max-norm residual of the discrete characteristic equations at (x, p):
-        x_j - x_{j-1} = delta grad_p H(x_j, p_j)           j = 1..N
-        p_1 = grad g(x_0)
-        p_{j+1} = p_j - delta grad_x H(x_j, p_j)           j = 1..N-1
-    (stationarity of the Lagrangian of Eq. disclaxBE).  Zero at every saddle."""
+def kkt_residual(w, x, p, activation="tanh", parts=False):
+    """Max-norm residual of the discrete characteristic equations at (x, p), the
+    stationarity conditions of the Lagrangian of Eq. disclaxBE (the discrete form
+    of x' = H_p, p' = -H_x with p(0) = grad g(x(0)), Section 4):
+        r1_j = x_j - x_{j-1} - delta grad_p H(x_j, p_j)           j = 1..N
+        r2   = p_1 - grad g(x_0)
+        r3_j = p_{j+1} - p_j + delta grad_x H(x_j, p_j)           j = 1..N-1
+    Zero at every saddle.  x, p are as `solve` returns them; for the negative
+    eikonal equation p is phi's costate and the equations are taken in the
+    solver's variables (psi = -phi: costate -p, initial data -g), which have the
+    same residual magnitudes as phi's own characteristic equations.  Where the
+    eikonal H = c(x)|p| is not differentiable (p_j = 0), r1_j is the distance from
+    x_j - x_{j-1} to delta times the subdifferential, the ball of radius c(x_j).
+    Returns [B], or with parts=True the three maxima (r1, r2, r3), each [B]."""
     fam = make_family(w, activation=activation)
-    cost = QuadCost(w["W"], w["c"])
+    sign = eikonal_sign(w)
+    cost = QuadCost(w["W"], w["c"], sign=sign)
+    q = sign * np.asarray(p, dtype=np.float64)          # the solver's costate
+    x = np.asarray(x, dtype=np.float64)
     N = x.shape[1] - 1
     delta = (np.asarray(w["t"], dtype=np.float64) / N)[:, None, None]
     S = node_times(delta[:, 0, 0], N)
-    r1 = x[:, 1:] - x[:, :-1] - delta * fam.grad_p(x[:, 1:], p[:, 1:], s=S[:, 1:])
-    r2 = p[:, 1] - cost.grad(x[:, 0])
-    r3 = p[:, 2:] - p[:, 1:N] + delta * fam.grad_x(x[:, 1:N], p[:, 1:N], s=S[:, 1:N])
-    return np.maximum(np.max(np.abs(r1), axis=(1, 2)),
-                      np.maximum(np.max(np.abs(r2), axis=1),
-                                 np.max(np.abs(r3), axis=(1, 2)) if N > 1 else 0.0))
+    dx = x[:, 1:] - x[:, :-1]
+    r1 = dx - delta * fam.grad_p(x[:, 1:], q[:, 1:], s=S[:, 1:])
+    if isinstance(fam, Eikonal):
+        # p_j = 0: distance of dx_j to the ball of radius delta c(x_j)
+        c, _ = fam.speed(x[:, 1:], S[:, 1:])
+        n = np.sqrt(np.sum(dx * dx, axis=-1))
+        out = np.maximum(0.0, 1.0 - delta[..., 0] * c / np.where(n > 0, n, 1.0))
+        zero = np.all(q[:, 1:] == 0.0, axis=-1)
+        r1 = np.where(zero[..., None], dx * out[..., None], r1)
+    r2 = q[:, 1] - cost.grad(x[:, 0])
+    r3 = q[:, 2:] - q[:, 1:N] + delta * fam.grad_x(x[:, 1:N], q[:, 1:N], s=S[:, 1:N])
+    m1 = np.max(np.abs(r1), axis=(1, 2))
+    m2 = np.max(np.abs(r2), axis=1)
+    m3 = np.max(np.abs(r3), axis=(1, 2)) if N > 1 else np.zeros_like(m1)
+    if parts:
+        return m1, m2, m3
+    return np.maximum(m1, np.maximum(m2, m3))
