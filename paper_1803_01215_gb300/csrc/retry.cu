@@ -106,7 +106,8 @@ hj_status run_rounds(hj_problem_s* prob, int64_t B, int32_t N, const hj_solver_o
     hj::SolveArgs<T> a = make_args<T>(prob, n, N, q, xq, t, V, iters, status, traj_x, traj_p,
                                       wx, wp);
     a.idx = idx;
-    if (cudaMemsetAsync(prob->counter, 0, sizeof(unsigned long long), s) != cudaSuccess) {
+    if (cudaMemsetAsync(prob->counter, 0, hj::kCounterWords * sizeof(unsigned long long), s) !=
+        cudaSuccess) {
       r = HJ_ERR_CUDA;
       break;
     }
@@ -128,6 +129,7 @@ hj_status hj_solve_batch_retry(hj_problem prob, int64_t B, const double* xq, con
                                double* V, int32_t* iters, int8_t* status, int8_t* rounds,
                                void* traj_x, void* traj_p, void* stream) {
   if (prob == nullptr || opts == nullptr || policy == nullptr || B < 0) return HJ_ERR_INVALID_ARG;
+  if (B > INT32_MAX) return HJ_ERR_INVALID_ARG;   // the retry list holds 32-bit point indices
   if (N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;
   const hj_retry_policy& pol = *policy;
   if (pol.rounds < 0 || pol.rounds > 127 || !std::isfinite(pol.sigma_step) ||

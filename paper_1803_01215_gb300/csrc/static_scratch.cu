@@ -11,6 +11,7 @@
 // hj_solve_batch runs; only where the parameters and the counter live differs.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -97,9 +98,20 @@ hj_status hj_solve_batch_static(int32_t family, int32_t d, const double* dyn, in
   if (N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;
   const hj_status oc = check_opts(*opts);
   if (oc != HJ_OK) return oc;
-  if (opts->formulation == HJ_FORM_HOPF)
-    for (int i = 0; i < d; ++i)
-      if (W[i] == 0.0) return HJ_ERR_INVALID_ARG;
+  // the problem view below, with the host-side facts hj_problem_create records
+  // about W, so that the option checks of hj_solve_batch apply unchanged
+  hj_problem_s view;
+  view.family = family;
+  view.d = d;
+  view.w_nonzero = true;
+  view.w2max = 0.0;
+  for (int i = 0; i < d; ++i) {
+    if (W[i] == 0.0) view.w_nonzero = false;
+    view.w2max = std::max(view.w2max, W[i] * W[i]);
+  }
+  for (int i = 0; i < 4; ++i) view.qc[i] = (family == HJ_FAMILY_QUADCOPTER) ? dyn[i] : 0.0;
+  const hj_status fc = check_formulation(&view, *opts);
+  if (fc != HJ_OK) return fc;
   if (opts->point_offset + B > (int64_t(1) << 32)) return HJ_ERR_INVALID_ARG;
   const bool has_A = family == HJ_FAMILY_TANH_DRIFT;
   const size_t tsize = opts->precision == HJ_PREC_FP32 ? sizeof(float) : sizeof(double);
@@ -144,13 +156,8 @@ hj_status hj_solve_batch_static(int32_t family, int32_t d, const double* dyn, in
       return HJ_ERR_CUDA;
   }
 
-  // a problem view whose device pointers all point into the array
-  hj_problem_s view;
-  view.family = family;
-  view.d = d;
-  view.w_nonzero = true;
+  // the view's device pointers all point into the array
   view.device = dev;
-  for (int i = 0; i < 4; ++i) view.qc[i] = (family == HJ_FAMILY_QUADCOPTER) ? dyn[i] : 0.0;
   view.W2 = reinterpret_cast<double*>(base + L.W2);
   view.W = reinterpret_cast<double*>(base + L.W);
   view.c = reinterpret_cast<double*>(base + L.c);

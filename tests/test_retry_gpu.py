@@ -5,6 +5,8 @@ FP64: the same rounds, iteration totals and values (1e-9) for the points whose
 every round stops at the same iteration on both sides; FP32: values within 1e-4
 of the FP64 oracle for the points both sides converge.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -97,6 +99,13 @@ def test_retry_argument_errors():
         with pytest.raises(binding.HJError) as e:
             binding.solve_batch_retry(prob, xq, t, int(w["N"]), opts, pol)
         assert e.value.code == code
+    # the retry list holds 32-bit point indices: a batch above 2^31 - 1 points is
+    # refused before any output pointer is looked at or anything runs
+    pol = binding.RetryPolicy(1, 0.0, 0.0, 0, 0.0)
+    r = binding._lib().hj_solve_batch_retry(prob.handle, 2 ** 31, None, None, int(w["N"]),
+                                            ctypes.byref(opts), ctypes.byref(pol), None, None,
+                                            None, None, None, None, None)
+    assert r == binding.HJ_ERR_INVALID_ARG
 
 
 @pytest.mark.parametrize("family", ["tanh_drift", "quadcopter"])

@@ -75,6 +75,91 @@ def test_static_entry_point_matches_solve_batch_twice(which, precision):
         assert torch.allclose(out["traj_p"], ref["traj_p"], rtol=0, atol=tol)
 
 
+def _quadratic(d, B, seed, N=20):
+    r = np.random.default_rng(seed)
+    return dict(family="quadratic", d=d, dyn=np.zeros(0), W=r.uniform(0.5, 2.0, d),
+                c=r.standard_normal(d), xq=r.uniform(-2.0, 2.0, (B, d)), t=r.uniform(0.5, 2.0, B),
+                N=N, sigma=0.5, tau=0.48, tol=1e-8, max_iter=4000, check_every=1, seed=seed,
+                init_radius=0.1)
+
+
+def _empty_out(B, N, d, precision):
+    it = torch.float32 if precision == "fp32" else torch.float64
+    return dict(V=torch.full((B,), np.nan, dtype=torch.float64, device="cuda"),
+                iters=torch.zeros(B, dtype=torch.int32, device="cuda"),
+                status=torch.full((B,), -1, dtype=torch.int8, device="cuda"),
+                traj_x=torch.zeros(B, N + 1, d, dtype=it, device="cuda"),
+                traj_p=torch.zeros(B, N + 1, d, dtype=it, device="cuda"))
+
+
+@pytest.mark.parametrize("case", ["quadratic_d3", "quadratic_d6", "quadcopter_hopf",
+                                  "quadcopter_trap", "tanh_d4_fe", "quadratic_d6_fp64"])
+def test_static_entry_point_matches_other_kernels_and_forms(case):
+    """The register kernel (quadratic d <= 4) and the shared-memory kernel
+    (quadratic d > 4), the Hopf form and the forward-Euler / trapezoid schemes:
+    the same status, iterations, values and trajectories as hj_solve_batch."""
+    from paper_1803_01215_gb300 import binding
+    precision = "fp64" if case.endswith("fp64") else "fp32"
+    form, scheme = "lax", "be"
+    if case.startswith("quadratic"):
+        w = _quadratic(3 if "d3" in case else 6, 120, 46)
+    elif case.startswith("quadcopter"):
+        w = W.quadcopter(B=160, seed=47, N=32, t=0.5)
+        form, scheme = ("hopf", "be") if case.endswith("hopf") else ("lax", "trap")
+    else:
+        w = W.tanh_drift(4, B=140, seed=48, N=24)
+        scheme = "fe"
+    opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], tol=w["tol"], max_iter=w["max_iter"],
+                             check_every=w["check_every"], precision=precision, seed=w["seed"],
+                             formulation=form, scheme=scheme)
+    xq = torch.as_tensor(w["xq"], device="cuda")
+    t = torch.as_tensor(w["t"], device="cuda")
+    ref = binding.solve_batch(binding.Problem.from_workload(w), xq, t, int(w["N"]), opts,
+                              return_traj=True)
+    for _ in range(2):
+        out = _empty_out(xq.shape[0], int(w["N"]), w["d"], precision)
+        assert _static_solve(w, opts, xq, t, out) == binding.HJ_OK
+        torch.cuda.synchronize()
+        assert torch.equal(out["status"], ref["status"])
+        assert torch.equal(out["iters"], ref["iters"])
+        tol = 1e-9 if precision == "fp64" else 1e-4
+        assert np.max(value_err(out["V"].cpu().numpy(), ref["V"].cpu().numpy())) <= tol
+        assert torch.allclose(out["traj_x"], ref["traj_x"], rtol=0, atol=tol)
+        assert torch.allclose(out["traj_p"], ref["traj_p"], rtol=0, atol=tol)
+
+
+@pytest.mark.parametrize("case", ["value_tol_hopf", "fe_inner_steps_2"])
+def test_static_entry_point_refuses_what_solve_batch_refuses(case):
+    """Option sets that hj_solve_batch refuses are refused here with the same
+    status, before anything runs."""
+    from paper_1803_01215_gb300 import binding
+    w = W.quadcopter(B=8, seed=49, N=32, t=0.5)
+    if case == "value_tol_hopf":
+        opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], formulation="hopf", value_tol=1e-6)
+    else:
+        opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], scheme="fe", inner_steps=2)
+    xq = torch.as_tensor(w["xq"], device="cuda")
+    t = torch.as_tensor(w["t"], device="cuda")
+    with pytest.raises(binding.HJError) as e:
+        binding.solve_batch(binding.Problem.from_workload(w), xq, t, 32, opts, return_traj=True)
+    assert e.value.code == binding.HJ_ERR_UNSUPPORTED
+    out = _empty_out(8, 32, 12, "fp32")
+    assert _static_solve(w, opts, xq, t, out) == e.value.code
+    torch.cuda.synchronize()
+    assert torch.all(out["status"] == -1)               # nothing ran
+
+
+@pytest.mark.parametrize("family", ["eikonal", "game_norms"])
+def test_static_entry_point_refuses_families_with_device_centres(family):
+    from paper_1803_01215_gb300 import binding
+    w = W.eikonal(d=2, sign=1, t=0.2, B=8) if family == "eikonal" else W.game_norms(d=2, t=0.1, B=8)
+    opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"])
+    xq = torch.as_tensor(w["xq"], device="cuda")
+    t = torch.as_tensor(w["t"], device="cuda")
+    out = _empty_out(8, int(w["N"]), 2, "fp32")
+    assert _static_solve(w, opts, xq, t, out) == binding.HJ_ERR_UNSUPPORTED
+
+
 def test_static_entry_point_rejects_oversized_parameters():
     from paper_1803_01215_gb300 import binding
     w = W.tanh_drift(100, B=4, seed=45)          # A of 100 x 100 does not fit the array
