@@ -124,7 +124,7 @@ class Quadcopter:
                       -cps * sph + cph * sth * sps,
                       cth * cph], axis=-1)
         # J[..., r, c] = d a_r / d (psi, theta, phi)_c
-        J = np.empty(x.shape[:-1] + (3, 3))
+        J = np.empty(x.shape[:-1] + (3, 3), dtype=np.result_type(x, float))
         J[..., 0, 0] = sph * cps - cph * sps * sth
         J[..., 0, 1] = cph * cps * cth
         J[..., 0, 2] = cph * sps - sph * cps * sth
@@ -147,7 +147,7 @@ class Quadcopter:
 
     def Bmat(self, x):
         a, _ = self.thrust_dir(x)
-        Bm = np.zeros(x.shape[:-1] + (12, 4))
+        Bm = np.zeros(x.shape[:-1] + (12, 4), dtype=np.result_type(x, float))
         Bm[..., 6:9, 0] = a / self.m
         Bm[..., 9, 1] = 1.0
         Bm[..., 10, 2] = 1.0
