@@ -81,8 +81,11 @@ enum {
   HJ_FAMILY_GAME_NORMS = 4
 };
 
-/* Iterate precision.  FP32 iterates keep the increment reductions and the
- * value sum in FP64; FP64 runs everything in double.                        */
+/* Iterate precision.  With FP32 iterates the stopping test's squared
+ * increments (each lane's or thread's partial in FP32) are accumulated over the
+ * point in FP64 and compared with tol in FP64, the value's terms are summed in
+ * FP64, and the optional residual (kkt) is evaluated in FP64; FP64 runs
+ * everything in double.                                                     */
 enum { HJ_PREC_FP32 = 0, HJ_PREC_FP64 = 1 };
 
 /* Saddle problem solved (hj_solver_opts.formulation).
@@ -113,18 +116,25 @@ enum { HJ_FORM_LAX = 0, HJ_FORM_HOPF = 1 };
  * both g and (for wL > 0) H act, takes one gradient step on -delta wL H(x_0, p_1)
  * followed by the exact prox of g.  For the game (HJ_FAMILY_GAME_NORMS) the
  * same weights apply to both players in Algorithm 3's order: the y-block's H
- * terms, y_0's included, are taken at (x^{k+1}, y^k).  FE and TRAP run in the
- * register-resident kernel only (quadcopter, tanh drift d in {2, 4}, eikonal
- * d in {2, 10}, the game d in {2, 7}; N <= 128 in FP64) with the Lax form and
- * inner_steps = 1; the quadratic family, whose H does not depend on x, has the
- * same problem under every scheme.  Other cases return HJ_ERR_UNSUPPORTED.   */
+ * terms, y_0's included, are taken at (x^{k+1}, y^k).  FE and TRAP run with
+ * the Lax form and inner_steps = 1 in every kernel but the tiled FP32 one:
+ * the register-resident kernel (quadcopter, tanh drift d in {2, 4}, eikonal
+ * d in {2, 10}, the game d in {2, 7}; N <= 128 in FP64), the shared-memory
+ * tanh-drift kernel (any other d, and d = 4 with N > 128 in FP64) and the
+ * coordinate-parallel eikonal kernel (any other d, static bump); the quadratic
+ * family, whose H does not depend on x, has the same problem under every
+ * scheme.  Other cases (the quadcopter or the game in FP64 with N > 128, a
+ * moving bump) return HJ_ERR_UNSUPPORTED.                                    */
 enum { HJ_SCHEME_BE = 0, HJ_SCHEME_FE = 1, HJ_SCHEME_TRAP = 2 };
 
 /* Per-point outcome written to status[].  HJ_POINT_INVALID marks a point whose
  * own N was outside the range of the kernel it was routed to (ragged batches:
- * N[b] outside 1..256); such a point is not iterated.                        */
+ * N[b] outside 1..256); such a point is not iterated.  HJ_POINT_TIMEOUT marks a
+ * point the launch did not solve because its budget (hj_solver_opts
+ * time_budget_ms, iter_budget) had run out when the point came up: it is not
+ * iterated, iters = 0, V = NaN, and its trajectory rows are not written.      */
 enum { HJ_POINT_CONVERGED = 0, HJ_POINT_MAX_ITER = 1, HJ_POINT_NONFINITE = 2,
-       HJ_POINT_INVALID = 3, HJ_POINT_VALUE_STOP = 4 };
+       HJ_POINT_INVALID = 3, HJ_POINT_VALUE_STOP = 4, HJ_POINT_TIMEOUT = 5 };
 
 typedef struct hj_problem_s* hj_problem;
 
@@ -171,7 +181,17 @@ hj_status hj_problem_destroy(hj_problem prob);
  *                points as well: at a test, a point whose fval moved by less
  *                than value_tol (absolute) since the previous test stops with
  *                status HJ_POINT_VALUE_STOP.  Backward-Euler Lax form in the
- *                register-resident kernel only (HJ_ERR_UNSUPPORTED otherwise).  */
+ *                register-resident kernel only (HJ_ERR_UNSUPPORTED otherwise).
+ *   time_budget_ms, iter_budget
+ *                budget of one kernel launch (0, the default: none): the
+ *                milliseconds since the launch's first point was drawn (the
+ *                device's global timer), and the iterations of the points it
+ *                has finished.  Once either is used up, every point drawn after
+ *                that is marked HJ_POINT_TIMEOUT instead of solved, so the launch
+ *                drains its batch and ends; points already being solved finish
+ *                (each is bounded by max_iter).  A ragged plan applies it to each
+ *                bucket's launch.  The call itself stays asynchronous: the
+ *                outcome is in status[].                                      */
 typedef struct {
   double sigma, tau, theta, tol;
   int32_t max_iter, check_every, inner_steps, precision;
@@ -181,6 +201,8 @@ typedef struct {
   int32_t formulation;
   int32_t scheme;
   double value_tol;
+  double time_budget_ms;
+  int64_t iter_budget;
 } hj_solver_opts;
 
 /* Solve B independent points with a common N (Algorithm 1, Eq. (disclaxBE); with
@@ -192,6 +214,19 @@ typedef struct {
  *            summed in FP64.
  *   iters    (device) [B] int32 out: iterations run.
  *   status   (device) [B] int8 out: HJ_POINT_*.
+ *   kkt      (device, may be NULL) [B] double out: the residual of the discrete
+ *            characteristic equations at the returned iterates (Section 4, the
+ *            stationarity conditions of Eq. (disclaxBE): x' = H_p, p' = -H_x,
+ *            p(0) = grad g in discrete form), evaluated in FP64:
+ *              max over j, k of |x_j - x_{j-1} - delta grad_p H(x_j, p_j)|,
+ *              |p_1 - grad g(x_0)| and |p_{j+1} - p_j + delta grad_x H(x_j, p_j)|.
+ *            Zero at a saddle, so it certifies each point without a reference
+ *            solver (see hj_kkt_residual for the eikonal conventions).  It is
+ *            hj_kkt_residual's kernel run after the solve on traj_x, traj_p (or on
+ *            a stream-ordered workspace when those are NULL).  Backward Euler
+ *            only, families quadratic, quadcopter, tanh drift and eikonal
+ *            (HJ_ERR_UNSUPPORTED otherwise).  Every point gets the residual of the
+ *            iterate it returned, converged or not.
  *   traj_x   (device, may be NULL) [B][N+1][d] out: x_0..x_N (Hopf: x_0 is the
  *            minimiser grad g*(p_1) = c + p_1 / W^2 of g(x_0) - <p_1, x_0>).
  *   traj_p   (device, may be NULL) [B][N+1][d] out: p_0 (= 0), p_1..p_N
@@ -209,10 +244,34 @@ typedef struct {
 hj_status hj_solve_batch(hj_problem prob, int64_t B,
                          const double* xq, const double* t, int32_t N,
                          const hj_solver_opts* opts,
-                         double* V, int32_t* iters, int8_t* status,
+                         double* V, int32_t* iters, int8_t* status, double* kkt,
                          void* traj_x, void* traj_p,
                          const void* warm_x, const void* warm_p,
                          void* stream);
+
+/* Residual of the discrete characteristic equations (Section 4) at given
+ * trajectories, per point, in FP64: the kkt output of hj_solve_batch for
+ * trajectories from any source (a ragged plan, retry rounds, a warm start).
+ *   t        (device) [B] horizons, delta = t / N.
+ *   traj_x, traj_p (device) [B][N+1][d] in the type of `precision`, in the
+ *            layout hj_solve_batch writes (traj_p[b][0] ignored).
+ *   kkt      (device) [B] double out: max over j, k of
+ *              |x_j - x_{j-1} - delta grad_p H(x_j, p_j, s_j)| (j = 1..N),
+ *              |p_1 - grad g(x_0)|,
+ *              |p_{j+1} - p_j + delta grad_x H(x_j, p_j, s_j)| (j = 1..N-1),
+ *            s_j = j delta.  For the negative eikonal equation (dyn[0] = -1)
+ *            the equations are those of the solver's variables (costate -p,
+ *            initial data -g; Section 6.1 solves phi = -psi), whose residuals
+ *            have the magnitudes of phi's own.  Where the eikonal H = c(x)|p| is
+ *            not differentiable (p_j = 0) the first term is the distance from
+ *            x_j - x_{j-1} to delta times the subdifferential, the ball of
+ *            radius delta c(x_j).
+ * Backward-Euler equations; families quadratic, quadcopter, tanh drift and
+ * eikonal (HJ_ERR_UNSUPPORTED for the game).
+ * Errors: HJ_ERR_INVALID_ARG, HJ_ERR_UNSUPPORTED, HJ_ERR_CUDA.               */
+hj_status hj_kkt_residual(hj_problem prob, int64_t B, const double* t, int32_t N,
+                          int32_t precision, const void* traj_x, const void* traj_p,
+                          double* kkt, void* stream);
 
 /* Gradient of L = sum_b w_b V_b at solved points (the adjoint of the value).
  * At a saddle of Eq. (disclaxBE) (trajectories of HJ_SCHEME_BE, Lax or Hopf
@@ -302,6 +361,21 @@ hj_status hj_get_launch_shape(hj_problem prob, int32_t precision, int32_t N,
 hj_status hj_autotune(hj_problem prob, int64_t B, const double* xq, const double* t, int32_t N,
                       const hj_solver_opts* opts, int32_t repeats, int32_t* warps_per_point,
                       int32_t* nodes_per_lane, float* best_ms, void* stream);
+
+/* Persisted launch shapes (the tuning of hj_autotune kept across processes).
+ * hj_shapes_save writes every (precision, N) shape stored on the handle to the
+ * text file `path` (host, NUL-terminated), one line per shape keyed by the
+ * device's name, the family, d, the precision and N; lines of the file with
+ * another key are kept, lines with the same key are replaced (the file is
+ * rewritten through a temporary file next to it).  hj_shapes_load applies the
+ * file's lines whose device name, family and d match the handle (through the
+ * checks of hj_set_launch_shape, so a line naming a shape this build lacks is
+ * skipped) and reports how many it applied (host, may be NULL).  A missing
+ * file loads nothing.  The paper has no counterpart; it is configuration.
+ * Errors: HJ_ERR_INVALID_ARG (null arguments, a file that cannot be written),
+ * HJ_ERR_CUDA.                                                               */
+hj_status hj_shapes_save(hj_problem prob, const char* path);
+hj_status hj_shapes_load(hj_problem prob, const char* path, int32_t* n_loaded);
 
 /* ---------------------------------------------------------------- ragged batches
  * A ragged batch mixes points of several problems (family, d) and their own

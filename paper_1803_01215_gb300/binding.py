@@ -16,6 +16,7 @@ from .workloads import FAMILIES
 HJ_OK, HJ_ERR_INVALID_ARG, HJ_ERR_UNSUPPORTED, HJ_ERR_STEP_SIZE, HJ_ERR_CUDA, HJ_ERR_OOM = range(6)
 PREC = {"fp32": 0, "fp64": 1}
 POINT_CONVERGED, POINT_MAX_ITER, POINT_NONFINITE = 0, 1, 2
+POINT_TIMEOUT = 5
 
 
 class HJError(RuntimeError):
@@ -31,7 +32,8 @@ class SolverOpts(ctypes.Structure):
                 ("inner_steps", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("init_radius", ctypes.c_double),
                 ("point_offset", ctypes.c_int64), ("formulation", ctypes.c_int32),
-                ("scheme", ctypes.c_int32), ("value_tol", ctypes.c_double)]
+                ("scheme", ctypes.c_int32), ("value_tol", ctypes.c_double),
+                ("time_budget_ms", ctypes.c_double), ("iter_budget", ctypes.c_int64)]
 
 
 _LIB = None
@@ -41,7 +43,7 @@ EXPORTED = ("hj_problem_create", "hj_problem_destroy", "hj_solve_batch",
             "hj_ragged_solve", "hj_ragged_autotune", "hj_ragged_plan_destroy",
             "hj_solve_grad", "hj_solve_grad_unrolled", "hj_solve_batch_static",
             "hj_static_scratch_bytes", "hj_probe_fp32_fma", "hj_solve_batch_retry",
-            "hj_status_str", "hj_version")
+            "hj_kkt_residual", "hj_shapes_save", "hj_shapes_load", "hj_status_str", "hj_version")
 
 
 def _lib():
@@ -56,7 +58,13 @@ def _lib():
         lib.hj_problem_create.argtypes = [ctypes.POINTER(P), I32, I32, D, I64, D, D]
         lib.hj_problem_destroy.argtypes = [P]
         lib.hj_solve_batch.argtypes = [P, I64, P, P, I32, ctypes.POINTER(SolverOpts),
-                                       P, P, P, P, P, P, P, P]
+                                       P, P, P, P, P, P, P, P, P]
+        lib.hj_kkt_residual.argtypes = [P, I64, P, I32, I32, P, P, P, P]
+        lib.hj_kkt_residual.restype = ctypes.c_int
+        lib.hj_shapes_save.argtypes = [P, ctypes.c_char_p]
+        lib.hj_shapes_save.restype = ctypes.c_int
+        lib.hj_shapes_load.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(I32)]
+        lib.hj_shapes_load.restype = ctypes.c_int
         lib.hj_set_launch_shape.argtypes = [P, I32, I32, I32, I32]
         lib.hj_get_launch_shape.argtypes = [P, I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I32)]
         lib.hj_autotune.argtypes = [P, I64, P, P, I32, ctypes.POINTER(SolverOpts), I32,
@@ -150,6 +158,22 @@ def get_launch_shape(problem, precision, N):
     return g.value, n.value
 
 
+def save_shapes(problem, path):
+    """hj_shapes_save: write the launch shapes stored on `problem` to a text cache."""
+    r = _lib().hj_shapes_save(problem.handle, os.fsencode(path))
+    if r != HJ_OK:
+        raise HJError(r, "hj_shapes_save")
+
+
+def load_shapes(problem, path):
+    """hj_shapes_load: apply the cached shapes for this GPU and problem; returns how many."""
+    n = ctypes.c_int32(0)
+    r = _lib().hj_shapes_load(problem.handle, os.fsencode(path), ctypes.byref(n))
+    if r != HJ_OK:
+        raise HJError(r, "hj_shapes_load")
+    return n.value
+
+
 def probe_fp32_fma(iters=50000, packed=False, stream=None):
     """hj_probe_fp32_fma: measured FP32 FMA throughput of the current device, TFLOP/s."""
     out = ctypes.c_double(0.0)
@@ -235,17 +259,19 @@ SCHEME = {"be": 0, "fe": 1, "trap": 2}
 
 def make_opts(*, sigma, tau, theta=1.0, tol=1e-8, max_iter=20000, check_every=16,
               inner_steps=1, precision="fp32", seed=0, init_radius=0.1, point_offset=0,
-              formulation="lax", scheme="be", value_tol=0.0):
+              formulation="lax", scheme="be", value_tol=0.0, time_budget_ms=0.0, iter_budget=0):
     return SolverOpts(float(sigma), float(tau), float(theta), float(tol), int(max_iter),
                       int(check_every), int(inner_steps), PREC[precision], int(seed),
                       float(init_radius), int(point_offset), FORM[formulation], SCHEME[scheme],
-                      float(value_tol))
+                      float(value_tol), float(time_budget_ms), int(iter_budget))
 
 
 def solve_batch(problem, xq, t, N, opts, *, return_traj=False, warm_x=None, warm_p=None,
-                out=None, stream=None):
+                out=None, stream=None, kkt=False):
     """hj_solve_batch on device tensors.  xq [B, d] float64 cuda, t [B] float64 cuda.
-    Returns dict(V, iters, status[, traj_x, traj_p]) of device tensors."""
+    Returns dict(V, iters, status[, traj_x, traj_p][, kkt]) of device tensors; kkt
+    (FP64, [B]) is the residual of the discrete characteristic equations at the
+    returned iterates.  With `out` given, its "kkt" entry (if any) is filled."""
     if not (xq.is_cuda and t.is_cuda):
         raise ValueError("xq and t must be CUDA tensors")
     xq = xq.contiguous()
@@ -262,6 +288,8 @@ def solve_batch(problem, xq, t, N, opts, *, return_traj=False, warm_x=None, warm
         if return_traj:
             out["traj_x"] = torch.empty(B, N + 1, d, dtype=it_dtype, device=dev)
             out["traj_p"] = torch.empty(B, N + 1, d, dtype=it_dtype, device=dev)
+        if kkt:
+            out["kkt"] = torch.empty(B, dtype=torch.float64, device=dev)
     for key in ("warm_x", "warm_p"):
         w = warm_x if key == "warm_x" else warm_p
         if w is not None and (w.dtype != it_dtype or tuple(w.shape) != (B, N + 1, d)
@@ -270,10 +298,25 @@ def solve_batch(problem, xq, t, N, opts, *, return_traj=False, warm_x=None, warm
     s = stream if stream is not None else torch.cuda.current_stream(dev)
     r = _lib().hj_solve_batch(problem.handle, B, _ptr(xq), _ptr(t), int(N), ctypes.byref(opts),
                               _ptr(out["V"]), _ptr(out["iters"]), _ptr(out["status"]),
-                              _ptr(out.get("traj_x")), _ptr(out.get("traj_p")),
-                              _ptr(warm_x), _ptr(warm_p), ctypes.c_void_p(s.cuda_stream))
+                              _ptr(out.get("kkt")), _ptr(out.get("traj_x")),
+                              _ptr(out.get("traj_p")), _ptr(warm_x), _ptr(warm_p),
+                              ctypes.c_void_p(s.cuda_stream))
     if r != HJ_OK:
         raise HJError(r, "hj_solve_batch")
+    return out
+
+
+def kkt_residual(problem, t, N, precision, traj_x, traj_p, stream=None):
+    """hj_kkt_residual: FP64 residual of the discrete characteristic equations at
+    the given trajectories ([B, N+1, d] in the precision's type), [B] device tensor."""
+    B = t.shape[0]
+    out = torch.empty(B, dtype=torch.float64, device=t.device)
+    s = stream if stream is not None else torch.cuda.current_stream(t.device)
+    r = _lib().hj_kkt_residual(problem.handle, B, _ptr(t.contiguous()), int(N), PREC[precision],
+                               _ptr(traj_x.contiguous()), _ptr(traj_p.contiguous()), _ptr(out),
+                               ctypes.c_void_p(s.cuda_stream))
+    if r != HJ_OK:
+        raise HJError(r, "hj_kkt_residual")
     return out
 
 
@@ -316,13 +359,14 @@ def solve_workload(w, *, precision="fp32", return_traj=False, problem=None, devi
                    **overrides):
     """Convenience: run a workload dict (workloads.py) end to end on the GPU."""
     prob = problem if problem is not None else Problem.from_workload(w)
+    kkt = bool(overrides.pop("kkt", False))
     o = dict(sigma=w["sigma"], tau=w["tau"], tol=w["tol"], max_iter=w["max_iter"],
              check_every=w["check_every"], seed=w["seed"], init_radius=w["init_radius"])
     o.update(overrides)
     opts = make_opts(precision=precision, **o)
     xq = torch.as_tensor(np.asarray(w["xq"], dtype=np.float64), device=device)
     t = torch.as_tensor(np.asarray(w["t"], dtype=np.float64), device=device)
-    return solve_batch(prob, xq, t, int(w["N"]), opts, return_traj=return_traj)
+    return solve_batch(prob, xq, t, int(w["N"]), opts, return_traj=return_traj, kkt=kkt)
 
 
 class RaggedPlan:

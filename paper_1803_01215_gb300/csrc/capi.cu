@@ -32,7 +32,7 @@ const char* hj_status_str(hj_status s) {
   return "unknown status";
 }
 
-int32_t hj_version(void) { return 102; }
+int32_t hj_version(void) { return 200; }
 
 hj_status hj_problem_create(hj_problem* out, int32_t family, int32_t d, const double* dyn,
                             int64_t n_dyn, const double* W, const double* c) {
@@ -124,7 +124,7 @@ hj_status hj_problem_create(hj_problem* out, int32_t family, int32_t d, const do
     if (r == HJ_OK) r = upload(&p->Atf, atf.data(), n);
   }
   if (r == HJ_OK && cudaMalloc(reinterpret_cast<void**>(&p->counter),
-                               sizeof(unsigned long long)) != cudaSuccess)
+                               hj::kCounterWords * sizeof(unsigned long long)) != cudaSuccess)
     r = HJ_ERR_OOM;
   if (r != HJ_OK) { release(p); return r; }
   *out = p;
@@ -144,8 +144,8 @@ hj_status hj_problem_destroy(hj_problem prob) {
 
 hj_status hj_solve_batch(hj_problem prob, int64_t B, const double* xq, const double* t,
                          int32_t N, const hj_solver_opts* opts, double* V, int32_t* iters,
-                         int8_t* status, void* traj_x, void* traj_p, const void* warm_x,
-                         const void* warm_p, void* stream) {
+                         int8_t* status, double* kkt, void* traj_x, void* traj_p,
+                         const void* warm_x, const void* warm_p, void* stream) {
   if (prob == nullptr || opts == nullptr || B < 0) return HJ_ERR_INVALID_ARG;
   if (N < 1 || N > hj::kMaxN) return HJ_ERR_INVALID_ARG;
   const hj_solver_opts& o = *opts;
@@ -155,6 +155,11 @@ hj_status hj_solve_batch(hj_problem prob, int64_t B, const double* xq, const dou
   if (fc != HJ_OK) return fc;
   if ((warm_x == nullptr) != (warm_p == nullptr)) return HJ_ERR_INVALID_ARG;
   if (o.point_offset + B > (int64_t(1) << 32)) return HJ_ERR_INVALID_ARG;
+  // the residual of the backward-Euler characteristic equations (control and
+  // eikonal families; the quadratic family's every scheme is backward Euler)
+  if (kkt != nullptr && (!hj::kkt_family_supported(prob->family) ||
+                         (o.scheme != HJ_SCHEME_BE && prob->family != HJ_FAMILY_QUADRATIC)))
+    return HJ_ERR_UNSUPPORTED;
   if (B == 0) return HJ_OK;
   if (xq == nullptr || t == nullptr || V == nullptr || iters == nullptr || status == nullptr)
     return HJ_ERR_INVALID_ARG;
@@ -163,6 +168,13 @@ hj_status hj_solve_batch(hj_problem prob, int64_t B, const double* xq, const dou
   if (cur != prob->device) return HJ_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const hj::WarpConfig cfg = shape_for(prob, o.precision, N);
+  if (kkt != nullptr) {
+    if (o.precision == HJ_PREC_FP32)
+      return run_solve_kkt<float>(prob, B, N, o, cfg, xq, t, V, iters, status, kkt, traj_x,
+                                  traj_p, warm_x, warm_p, s);
+    return run_solve_kkt<double>(prob, B, N, o, cfg, xq, t, V, iters, status, kkt, traj_x,
+                                 traj_p, warm_x, warm_p, s);
+  }
   if (o.precision == HJ_PREC_FP32)
     return run_solve<float>(prob, B, N, o, cfg, xq, t, V, iters, status, traj_x, traj_p,
                             warm_x, warm_p, s);

@@ -17,6 +17,12 @@
 //                           v <- argmin_p lam (wr H(xr, p) + wl H(xl, p)) + |p - v|^2/2
 //                           for weights wr + wl = 1 (forward-Euler and trapezoid
 //                           schemes; cr, cl the contexts at xr, xl)
+//   kkt_node(x, xl, p, pr, delta, s, r3)
+//                           node j's part of the residual of the discrete
+//                           characteristic equations (Section 4), in FP64 from
+//                           the iterates x = x_j, xl = x_{j-1}, p = p_j, pr = p_{j+1}:
+//                           max_k |x_j - x_{j-1} - delta grad_p H(x_j, p_j)|_k and,
+//                           with r3, max_k |p_{j+1} - p_j + delta grad_x H(x_j, p_j)|_k
 // All families have L = |u|^2/2, so H = <p, f0(x)> + |B(x)^T p|^2/2 (Section 2).
 #pragma once
 #include <type_traits>
@@ -169,6 +175,18 @@ struct FamQuadratic {
 #pragma unroll
     for (int k = 0; k < D; ++k) h += p[k] * p[k];
     return T(0.5) * h;
+  }
+  // grad_p H = p, grad_x H = 0
+  __device__ double kkt_node(const T (&x)[D], const T (&xl)[D], const T (&p)[D], const T (&pr)[D],
+                             double delta, double, bool r3) const {
+    double r = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double pk = (double)p[k];
+      r = max_nan(r, fabs((double)x[k] - (double)xl[k] - delta * pk));
+      if (r3) r = max_nan(r, fabs((double)pr[k] - pk));
+    }
+    return r;
   }
 };
 
@@ -377,6 +395,55 @@ struct FamQuadcopter {
     for (int k = 9; k < 12; ++k) rr += p[k] * p[k];
     return h + T(0.5) * (u0 * u0 + rr) + T(0.5) * eps * pp;
   }
+  // grad_p H = f0 + B B^T p + eps p: (v_pos, v_ang, a_h a - g_z e3 + a u0 / m, tau) + eps p
+  // with u0 = <a, p_7..9> / m; grad_x H = (0, (a_h + u0 / m) J^T p_7..9, p_1..3, p_4..6).
+  // FP32 iterates take the three sine/cosine pairs from the accurate FP32 sincosf
+  // (within 2 ulp) and form everything else in FP64: the evaluation error of the
+  // residual is then below about delta (a_h + |u0|) 2^-22 (1e-7 for the 12-D
+  // workload), far below an FP32 iterate's own residual; FP64 iterates use the
+  // FP64 functions throughout.
+  __device__ double kkt_node(const T (&x)[D], const T (&xl)[D], const T (&p)[D], const T (&pr)[D],
+                             double delta, double, bool r3) const {
+    double a[3], J[9];
+    if constexpr (sizeof(T) == 4) {
+      float s0, c0, s1, c1, s2, c2;
+      sincosf(x[3], &s0, &c0);
+      sincosf(x[4], &s1, &c1);
+      sincosf(x[5], &s2, &c2);
+      const double sps = s0, cps = c0, sth = s1, cth = c1, sph = s2, cph = c2;
+      const double cc = cph * cps, cs = cph * sps, sc = sph * cps, ss = sph * sps;
+      a[0] = ss + cc * sth;
+      a[1] = -sc + cs * sth;
+      a[2] = cth * cph;
+      J[0] = sc - cs * sth; J[1] = cc * cth;   J[2] = cs - sc * sth;
+      J[3] = ss + cc * sth; J[4] = cs * cth;   J[5] = -cc - ss * sth;
+      J[6] = 0.0;           J[7] = -sth * cph; J[8] = -cth * sph;
+    } else {
+      thrust<double>((double)x[3], (double)x[4], (double)x[5], a, J);
+    }
+    const double q6 = (double)p[6], q7 = (double)p[7], q8 = (double)p[8];
+    const double u0 = (a[0] * q6 + a[1] * q7 + a[2] * q8) / m64;
+    const double coef = ah64 + u0 / m64;
+    double r = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double pk = (double)p[k];
+      double gp;
+      if (k < 6) gp = (double)x[6 + k];
+      else if (k < 9) gp = ah64 * a[k - 6] - (k == 8 ? gz64 : 0.0) + a[k - 6] * u0 / m64;
+      else gp = pk;
+      gp += eps64 * pk;
+      r = max_nan(r, fabs((double)x[k] - (double)xl[k] - delta * gp));
+      if (r3) {
+        double gx;
+        if (k < 3) gx = 0.0;
+        else if (k < 6) gx = coef * (J[k - 3] * q6 + J[k] * q7 + J[k + 3] * q8);
+        else gx = (double)p[k - 6];
+        r = max_nan(r, fabs((double)pr[k] - pk + delta * gx));
+      }
+    }
+    return r;
+  }
 };
 
 // ---------------------------------------------------------------- tanh drift, small D
@@ -459,6 +526,31 @@ struct FamTanhDrift {
       h += p[i] * tanh_t<T>(y) + T(0.5) * p[i] * p[i];
     }
     return h;
+  }
+  // grad_p H = tanh(A x) + p, grad_x H = A^T ((1 - tanh(A x)^2) p), A in FP64
+  __device__ double kkt_node(const T (&x)[D], const T (&xl)[D], const T (&p)[D], const T (&pr)[D],
+                             double delta, double, bool r3) const {
+    double w[D];
+    double r = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      double y = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) y += A64[i * D + k] * (double)x[k];
+      const double av = tanh(y), pi = (double)p[i];
+      r = max_nan(r, fabs((double)x[i] - (double)xl[i] - delta * (av + pi)));
+      w[i] = (1.0 - av * av) * pi;
+    }
+    if (r3) {
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        double g = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) g += A64[k * D + i] * w[k];
+        r = max_nan(r, fabs((double)pr[i] - (double)p[i] + delta * g));
+      }
+    }
+    return r;
   }
 };
 
@@ -565,6 +657,34 @@ struct FamEikonalT {
     return c.c * sqrt_t<T>(n2);
   }
   __device__ __forceinline__ T Ht(const T (&x)[D], const T (&p)[D]) const { return Ht_t(x, p, T(0)); }
+  // grad_p H = c(x) p / |p| (for p = 0: r1 is the distance of x_j - x_{j-1} to the
+  // ball of radius delta c(x_j), delta times the subdifferential), grad_x H = |p| grad c
+  __device__ double kkt_node(const T (&x)[D], const T (&xl)[D], const T (&p)[D], const T (&pr)[D],
+                             double delta, double s, bool r3) const {
+    double r2 = 0.0, n2 = 0.0, d2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double cb = MOVING ? xb64[k] + s * vb64[k] : xb64[k];
+      const double y = (double)x[k] - cb, pk = (double)p[k], dk = (double)x[k] - (double)xl[k];
+      r2 += y * y;
+      n2 += pk * pk;
+      d2 += dk * dk;
+    }
+    const double e = exp(-c2d * r2), c = c0d + c1d * e, gf = -2.0 * c1d * c2d * e;
+    const double n = sqrt(n2);
+    const double out = n2 > 0.0 ? 0.0 : fmax(0.0, 1.0 - delta * c / (d2 > 0.0 ? sqrt(d2) : 1.0));
+    double r = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double pk = (double)p[k], dk = (double)x[k] - (double)xl[k];
+      r = max_nan(r, fabs(n2 > 0.0 ? dk - delta * c * pk / n : dk * out));
+      if (r3) {
+        const double cb = MOVING ? xb64[k] + s * vb64[k] : xb64[k];
+        r = max_nan(r, fabs((double)pr[k] - pk + delta * n * gf * ((double)x[k] - cb)));
+      }
+    }
+    return r;
+  }
 };
 template <typename T, int D>
 using FamEikonal = FamEikonalT<T, D, false>;

@@ -23,9 +23,6 @@ struct SolveArgs {
   // iteration loop holds no double-derived value the compiler could recompute
   // there (FP64 instructions are ~64x the cost of FP32 ones on this GPU).
   T sigma_t, tau_t, theta_t;
-  // tol rounded up to the iterate type: for a sum s of that type,
-  // (double)s < tol exactly when s < tol_t, so the test needs no FP64 operation.
-  T tol_t;
   int32_t max_iter, check_every, inner_steps;
   int32_t formulation;   // HJ_FORM_LAX or HJ_FORM_HOPF
   // HJ_SCHEME_*: H on interval j weighted wR at x_j and wL at x_{j-1}
@@ -68,7 +65,11 @@ struct SolveArgs {
   double cost_sign;
   int32_t game_d1;                     // difference-of-norms game: coordinates of the
                                        // minimising player (d for every other family)
-  unsigned long long* counter;        // work counter (zeroed before launch)
+  // budget of the launch (0: none): nanoseconds since its first draw, and
+  // iterations of the points finished; when either runs out the remaining
+  // points are drained with status HJ_POINT_TIMEOUT
+  int64_t budget_ns, iter_budget;
+  unsigned long long* counter;        // work counter block, kCounterWords (zeroed before launch)
   // Ragged batches: the launch processes items i = 0..B-1, point id idx[i]
   // (idx null: id = i).  Per-point N (Nv null: N), xq offset in doubles
   // (xq_off null: id*d) and trajectory offset in elements (traj_off null:
@@ -95,6 +96,54 @@ __device__ __forceinline__ PointRef<T> point_ref(const SolveArgs<T>& a, int64_t 
   r.xq = a.xq + (a.xq_off ? a.xq_off[r.id] : r.id * (int64_t)a.d);
   r.traj = a.traj_off ? (size_t)a.traj_off[r.id] : (size_t)r.id * (size_t)(r.N + 1) * a.d;
   return r;
+}
+
+// The work counter block of a persistent launch, zeroed before the launch:
+// [0] the next item to draw, [1] the launch's start time on the global timer
+// (set by the first draw when a time budget is on), [2] the iterations of the
+// points finished so far (counted when an iteration budget is on).
+constexpr int kCounterWords = 3;
+constexpr unsigned long long kItemTimedOut = 1ull << 62;   // flag on a drawn item
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Draw the next item (one thread of the group).  When the launch's budget has
+// run out, an item below B comes back with kItemTimedOut set: the caller marks
+// that point HJ_POINT_TIMEOUT instead of solving it, and so drains the batch.
+template <typename T>
+__device__ __forceinline__ unsigned long long draw_item(const SolveArgs<T>& a) {
+  const unsigned long long it = atomicAdd(a.counter, 1ull);
+  if (it >= (unsigned long long)a.B || (a.budget_ns <= 0 && a.iter_budget <= 0)) return it;
+  bool out = false;
+  if (a.budget_ns > 0) {
+    const unsigned long long now = global_ns();
+    unsigned long long t0 = atomicCAS(a.counter + 1, 0ull, now);
+    if (t0 == 0ull) t0 = now;
+    out = (long long)(now - t0) > (long long)a.budget_ns;
+  }
+  if (a.iter_budget > 0)
+    out = out || *reinterpret_cast<volatile unsigned long long*>(a.counter + 2) >=
+                     (unsigned long long)a.iter_budget;
+  return out ? (it | kItemTimedOut) : it;
+}
+
+// A point drained after the budget ran out: not iterated, V = NaN (one thread).
+template <typename T>
+__device__ __forceinline__ void mark_timed_out(const SolveArgs<T>& a, int64_t item) {
+  const int64_t id = a.idx ? (int64_t)a.idx[item] : item;
+  a.status[id] = HJ_POINT_TIMEOUT;
+  a.iters[id] = 0;
+  a.V[id] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// A finished point's iterations, for the iteration budget (one thread).
+template <typename T>
+__device__ __forceinline__ void count_iterations(const SolveArgs<T>& a, int k) {
+  if (a.iter_budget > 0) atomicAdd(a.counter + 2, (unsigned long long)k);
 }
 
 // Launch shape of the register-resident kernel: G warps per point, NPL time
@@ -156,6 +205,9 @@ struct InitGuess<float> {
     return r * u(splitmix_at(seed, pt, 1, j, k));
   }
 };
+
+// max that keeps a NaN (fmax drops it): a non-finite residual must not read as small
+__device__ __forceinline__ double max_nan(double a, double b) { return (a > b || a != a) ? a : b; }
 
 template <typename U>
 __device__ __forceinline__ U warp_sum(U v) {
@@ -276,8 +328,9 @@ int td_tile_group_warps(int d, int N);
 
 template <typename T>
 hj_status launch_td_cta_solver(const SolveArgs<T>& a, bool drift, cudaStream_t s);
-// Shared memory that kernel needs for (d, N); 0 if it does not fit.
+// Shared memory that kernel needs for (d, N) (mix: the forward-Euler /
+// trapezoid schemes' extra state array); 0 if it does not fit.
 template <typename T>
-size_t td_cta_smem_bytes(int d, int N, bool drift);
+size_t td_cta_smem_bytes(int d, int N, bool drift, bool mix = false);
 
 }  // namespace hj

@@ -23,6 +23,13 @@
 // a stream-ordered workspace (the d = 2000 problems: L2-resident).
 // The negative equation (cost_sign = -1) runs the positive one with -g and
 // returns -V and -p, as in Section 6.1.
+//
+// MIX = true runs the forward-Euler and trapezoid schemes (HJ_SCHEME_FE/TRAP):
+// H on interval j is (wR c(x_j) + wL c(x_{j-1}))|p_j|, so node 0's distance to the
+// bump is summed too, the shrink threshold takes the averaged speed, the
+// x-gradient of node j is grad c(x_j) (wR |p_j| + wL |p_{j+1}|), and x_0 takes the
+// gradient step tau delta wL |p_1| grad c(x_0) before the prox of g (two more
+// barriers per iteration for the node scalars).
 #include <cuda_runtime.h>
 
 #include "hj_internal.cuh"
@@ -42,20 +49,24 @@ template <>
 __device__ __forceinline__ float sqrtk<float>(float y) { return sqrtf(y); }
 
 // shared memory past the state: red[nwarps][2 (Nmax + 1)] partial sums,
-// keep[Nmax + 1], coef[Nmax + 1] node scalars, xbs[d], goff[d], ginv[d], tred[2 nwarps]
+// keep[Nmax + 1], coef[Nmax + 1] node scalars (and, for the mixed schemes,
+// the speed c, the gradient factor and |p| of every node: 3 (Nmax + 1)),
+// xbs[d], goff[d], ginv[d], then tred[2 nwarps] doubles (the stopping sums) at
+// the next 8-byte boundary
 struct EikLayout {
   size_t state;       // elements of one state array: (Nmax + 1) d
   size_t scal;        // elements past the state arrays
   __host__ __device__ EikLayout(int d, int Nmax, int nwarps) {
     state = (size_t)(Nmax + 1) * d;
-    scal = (size_t)nwarps * 2 * (Nmax + 1) + 2 * (size_t)(Nmax + 1) + 3 * (size_t)d +
-           2 * (size_t)nwarps;
+    scal = (size_t)nwarps * 2 * (Nmax + 1) + 5 * (size_t)(Nmax + 1) + 3 * (size_t)d +
+           4 * (size_t)nwarps + 2;                  // 2 nwarps doubles and alignment
   }
 };
 
-template <typename T, int NMAX>
+template <typename T, int NMAX, bool MIX>
 __global__ void __launch_bounds__(512) lax_eik_kernel(const SolveArgs<T> a, T* work,
                                                       int state_in_smem) {
+  static_assert(!(MIX && NMAX > 0), "the mixed schemes run the generic pass structure");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int d = a.d;
   const int T_ = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -69,10 +80,15 @@ __global__ void __launch_bounds__(512) lax_eik_kernel(const SolveArgs<T> a, T* w
   T* red = state_in_smem ? sbase + ((3 * L.state + 1) & ~size_t(1)) : sbase;
   T* keep = red + (size_t)nwarps * 2 * (a.N + 1);
   T* coef = keep + (a.N + 1);
-  T* xbs = coef + (a.N + 1);
+  T* cvv = coef + (a.N + 1);                      // MIX: c(x_j), -2 c1 c2 e_j, |p_j|
+  T* evv = cvv + (a.N + 1);
+  T* nnv = evv + (a.N + 1);
+  T* xbs = nnv + (a.N + 1);
   T* goff = xbs + d;
   T* ginv = goff + d;
-  T* tred = ginv + d;
+  // (an offset from the shared base, so the compiler keeps shared-memory addressing)
+  double* tred = reinterpret_cast<double*>(
+      smem_raw + ((((size_t)(ginv + d - sbase)) * sizeof(T) + 7) & ~size_t(7)));
   __shared__ unsigned long long s_point;
 
   for (int k = tid; k < d; k += T_) {
@@ -84,14 +100,20 @@ __global__ void __launch_bounds__(512) lax_eik_kernel(const SolveArgs<T> a, T* w
   }
   const T sig = a.sigma_t, tau = a.tau_t, th = a.theta_t;
   const T c0 = T(a.eik_c0), c1 = T(a.eik_c1), c2 = T(a.eik_c2);
+  const T wr = a.mix_wr_t, wl = a.mix_wl_t;
   __syncthreads();
 
   for (;;) {
     __syncthreads();
-    if (tid == 0) s_point = atomicAdd(a.counter, 1ull);
+    if (tid == 0) s_point = draw_item(a);
     __syncthreads();
-    const int64_t item = (int64_t)s_point;
+    const unsigned long long drawn = s_point;
+    const int64_t item = (int64_t)(drawn & ~kItemTimedOut);
     if (item >= a.B) break;
+    if (drawn & kItemTimedOut) {                  // the launch's budget ran out: drain
+      if (tid == 0) mark_timed_out(a, item);
+      continue;
+    }
     const PointRef<T> ref = point_ref(a, item);
     const int64_t b = ref.id;
     const int N = ref.N;
@@ -127,14 +149,16 @@ __global__ void __launch_bounds__(512) lax_eik_kernel(const SolveArgs<T> a, T* w
     // node scalars: |x_j - x_b|^2 and |p_j + sigma (z_j - z_{j-1})|^2 (dual) or
     // |p_j|^2 (value), reduced over the CTA into red
     auto node_sums = [&](bool dual) {
-      for (int j = 1; j <= N; ++j) {
+      for (int j = MIX ? 0 : 1; j <= N; ++j) {        // MIX: node 0's distance too
         T pr = T(0), pv = T(0);
         for (int k = tid; k < d; k += T_) {
           const size_t e = (size_t)j * d + k;
           const T y = X[e] - xbs[k];
           pr += y * y;
-          const T v = dual ? P[e] + sig * (Z[e] - Z[e - d]) : P[e];
-          pv += v * v;
+          if (j > 0) {
+            const T v = dual ? P[e] + sig * (Z[e] - Z[e - d]) : P[e];
+            pv += v * v;
+          }
         }
         pr = warp_sum<T>(pr);
         pv = warp_sum<T>(pv);
@@ -153,16 +177,39 @@ __global__ void __launch_bounds__(512) lax_eik_kernel(const SolveArgs<T> a, T* w
       const bool chk = (k_it % a.check_every == 0) || (k_it == a.max_iter);
       if constexpr (NMAX == 0) node_sums(true);
       __syncthreads();
-      for (int j = 1 + tid; j <= N; j += T_) {
-        T r2 = T(0), n2 = T(0);
-        for (int w = 0; w < nwarps; ++w) {
-          r2 += red[(size_t)w * 2 * (N + 1) + 2 * j];
-          n2 += red[(size_t)w * 2 * (N + 1) + 2 * j + 1];
+      if constexpr (MIX) {
+        for (int j = tid; j <= N; j += T_) {      // speed and gradient factor of every node
+          T r2 = T(0);
+          for (int w = 0; w < nwarps; ++w) r2 += red[(size_t)w * 2 * (N + 1) + 2 * j];
+          const T e = expk<T>(-c2 * r2);
+          cvv[j] = c0 + c1 * e;
+          evv[j] = T(-2) * c1 * c2 * e;
         }
-        const T e = expk<T>(-c2 * r2);
-        const T n = sqrtk<T>(n2), thr = lam * (c0 + c1 * e);
-        keep[j] = (n > thr) ? (n - thr) / n : T(0);
-        coef[j] = taud * ((n > thr) ? n - thr : T(0)) * (T(-2) * c1 * c2 * e);
+        __syncthreads();
+        for (int j = 1 + tid; j <= N; j += T_) {  // shrink with the averaged speed
+          T n2 = T(0);
+          for (int w = 0; w < nwarps; ++w) n2 += red[(size_t)w * 2 * (N + 1) + 2 * j + 1];
+          const T n = sqrtk<T>(n2), thr = lam * (wr * cvv[j] + wl * cvv[j - 1]);
+          keep[j] = (n > thr) ? (n - thr) / n : T(0);
+          nnv[j] = (n > thr) ? n - thr : T(0);
+        }
+        __syncthreads();
+        for (int j = tid; j < N; j += T_) {       // grad c(x_j) (wR |p_j| + wL |p_{j+1}|)
+          const T pw = (j == 0) ? wl * nnv[1] : wr * nnv[j] + wl * nnv[j + 1];
+          coef[j] = taud * pw * evv[j];
+        }
+      } else {
+        for (int j = 1 + tid; j <= N; j += T_) {
+          T r2 = T(0), n2 = T(0);
+          for (int w = 0; w < nwarps; ++w) {
+            r2 += red[(size_t)w * 2 * (N + 1) + 2 * j];
+            n2 += red[(size_t)w * 2 * (N + 1) + 2 * j + 1];
+          }
+          const T e = expk<T>(-c2 * r2);
+          const T n = sqrtk<T>(n2), thr = lam * (c0 + c1 * e);
+          keep[j] = (n > thr) ? (n - thr) / n : T(0);
+          coef[j] = taud * ((n > thr) ? n - thr : T(0)) * (T(-2) * c1 * c2 * e);
+        }
       }
       __syncthreads();
       T rx = T(0), rp = T(0);
@@ -189,7 +236,8 @@ __global__ void __launch_bounds__(512) lax_eik_kernel(const SolveArgs<T> a, T* w
         T znew;
         {
           const T xo = X[k];
-          const T xn = (xo + tau * P[d + k] + goff[k]) * ginv[k];
+          const T v0 = MIX ? xo + tau * P[d + k] + coef[0] * (xo - xb) : xo + tau * P[d + k];
+          const T xn = (v0 + goff[k]) * ginv[k];
           if (chk) { const T df = xn - xo; rx += df * df; }
           znew = xn + th * (xn - xo);
           Z[k] = znew;
@@ -244,15 +292,21 @@ __global__ void __launch_bounds__(512) lax_eik_kernel(const SolveArgs<T> a, T* w
         }
       }
       if (chk) {
-        // squared increments summed in the iterate type and compared with tol
-        // rounded up to it: exactly the FP64 test of the sum
-        const T sx = warp_sum<T>(rx), sp = warp_sum<T>(rp);
-        if (lane == 0) { tred[2 * warp] = sx; tred[2 * warp + 1] = sp; }
+        // each thread's partial (iterate type) reduced over its warp in that type,
+        // accumulated over the CTA's warps in FP64
+        const T wx = warp_sum<T>(rx), wp = warp_sum<T>(rp);
+        if (lane == 0) { tred[2 * warp] = (double)wx; tred[2 * warp + 1] = (double)wp; }
         __syncthreads();
-        T tx = T(0), tp = T(0);
-        for (int w = 0; w < nwarps; ++w) { tx += tred[2 * w]; tp += tred[2 * w + 1]; }
-        if (!(isfinite(tx) && isfinite(tp))) { st = HJ_POINT_NONFINITE; break; }
-        if (tx < a.tol_t && tp < a.tol_t) { st = HJ_POINT_CONVERGED; break; }
+        // one lane per warp accumulates the warps' sums in FP64 and compares
+        int verdict = 0;                                  // 1 converged, 2 non-finite
+        if (lane == 0) {
+          double tx = 0.0, tp = 0.0;
+          for (int w = 0; w < nwarps; ++w) { tx += tred[2 * w]; tp += tred[2 * w + 1]; }
+          verdict = !(isfinite(tx) && isfinite(tp)) ? 2 : (tx < a.tol && tp < a.tol) ? 1 : 0;
+        }
+        verdict = __shfl_sync(kFull, verdict, 0);
+        if (verdict == 2) { st = HJ_POINT_NONFINITE; break; }
+        if (verdict == 1) { st = HJ_POINT_CONVERGED; break; }
       }
     }
 
@@ -274,12 +328,15 @@ __global__ void __launch_bounds__(512) lax_eik_kernel(const SolveArgs<T> a, T* w
     }
     __syncthreads();
     for (int j = 1 + tid; j <= N; j += T_) {
-      T r2 = T(0), n2 = T(0);
+      T r2 = T(0), n2 = T(0), rl = T(0);
       for (int w = 0; w < nwarps; ++w) {
         r2 += red[(size_t)w * 2 * (N + 1) + 2 * j];
         n2 += red[(size_t)w * 2 * (N + 1) + 2 * j + 1];
+        if (MIX) rl += red[(size_t)w * 2 * (N + 1) + 2 * (j - 1)];
       }
-      acc -= (double)(delta_t * (c0 + c1 * expk<T>(-c2 * r2)) * sqrtk<T>(n2));
+      const T cj = c0 + c1 * expk<T>(-c2 * r2);
+      const T cw = MIX ? wr * cj + wl * (c0 + c1 * expk<T>(-c2 * rl)) : cj;
+      acc -= (double)(delta_t * cw * sqrtk<T>(n2));
     }
     acc = warp_sum<double>(acc);
     __syncthreads();
@@ -292,6 +349,7 @@ __global__ void __launch_bounds__(512) lax_eik_kernel(const SolveArgs<T> a, T* w
       a.V[b] = a.cost_sign * v;
       a.iters[b] = k_it;
       a.status[b] = st;
+      count_iterations(a, k_it);
     }
     if (a.traj_x != nullptr || a.traj_p != nullptr) {
       const T sgn = T(a.cost_sign);
@@ -353,7 +411,10 @@ hj_status launch_eik_cta_solver(const SolveArgs<T>& a, cudaStream_t s) {
   // in the workspace the generic kernel keeps two CTAs per SM (62 registers
   // against the fused kernel's 94), which measured faster (898 against 1119 ms
   // at d = 2000).
-  auto kern = (in_smem && a.N <= 16) ? lax_eik_kernel<T, 16> : lax_eik_kernel<T, 0>;
+  // (the mixed schemes run the generic pass structure)
+  auto kern = a.scheme != HJ_SCHEME_BE ? lax_eik_kernel<T, 0, true>
+              : (in_smem && a.N <= 16) ? lax_eik_kernel<T, 16, false>
+                                       : lax_eik_kernel<T, 0, false>;
   if (smem > (size_t)max_optin) return HJ_ERR_UNSUPPORTED;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)

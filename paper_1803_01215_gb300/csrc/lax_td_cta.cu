@@ -13,8 +13,16 @@
 //   phase B  G = A^T W (second product, A held row-major), epilogue: the primal
 //            gradient step x_j <- x_j - tau (p_j - p_{j+1}) + tau delta G_j, the
 //            over-relaxation z_j, and the g-prox of x_0.
-// The squared increments are reduced on test iterations only.  CTAs
+// The squared increments are reduced on test iterations only (over each warp in
+// the iterate type, over the warps in FP64).  CTAs
 // draw points from a work counter (persistent grid).
+//
+// MIX = true runs the forward-Euler and trapezoid schemes (HJ_SCHEME_FE/TRAP),
+// H on interval j weighted wR at x_j and wL at x_{j-1}: phase A stores
+// a = tanh(A x) for every node 0..N in a fifth state array, the dual step
+// takes the averaged drift wR a_j + wL a_{j-1}, and W = (1 - a_j^2)(wR p_j +
+// wL p_{j+1}) (node 0: wL (1 - a_0^2) p_1) makes A^T W the weighted x-gradient
+// of every node, x_0's included (one gradient step before the prox of g).
 #include <cuda_runtime.h>
 
 #include "hj_internal.cuh"
@@ -65,9 +73,10 @@ struct Layout {
 
 // TWO: keep both A^T and A in shared memory (vector loads in both products);
 // otherwise only A, and the first product reads it with strided scalar loads.
-template <typename T, bool TWO, bool DRIFT, bool HOPF>
+template <typename T, bool TWO, bool DRIFT, bool HOPF, bool MIX>
 __global__ void __launch_bounds__(512)
 lax_td_cta_kernel(const SolveArgs<T> a) {
+  static_assert(!(MIX && (HOPF || !DRIFT)), "the mixed schemes: Lax form, tanh drift");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int d = a.d;
   const Layout L(d, a.N);                                 // a.N: the largest N of the launch
@@ -78,8 +87,9 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
   T* P = X + L.s_elems;
   T* Z = P + L.s_elems;
   T* Wk = Z + L.s_elems;
-  double* red = reinterpret_cast<double*>(Wk + L.s_elems);  // [2 * nwarps] value epilogue
-  T* tred = reinterpret_cast<T*>(red);                      // [2 * nwarps] stopping test
+  T* Asv = Wk + L.s_elems;                                  // MIX: tanh(A x) of every node
+  double* red = reinterpret_cast<double*>(Wk + (MIX ? 2 : 1) * L.s_elems);  // [2 * nwarps]
+  double* tred = red;                                       // [2 * nwarps] stopping test
   T* hsv = reinterpret_cast<T*>(red + 32);                  // Hopf form: sigma / W^2, sigma c
   T* hcv = hsv + dp;
   __shared__ unsigned long long s_point;
@@ -100,13 +110,19 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
     hcv[i] = (i < d) ? T(a.sigma * a.c[i]) : T(0);
   }
   const T sig = a.sigma_t, tau = a.tau_t, th = a.theta_t;
+  const T wr = a.mix_wr_t, wl = a.mix_wl_t;
 
   for (;;) {
     __syncthreads();
-    if (tid == 0) s_point = atomicAdd(a.counter, 1ull);
+    if (tid == 0) s_point = draw_item(a);
     __syncthreads();
-    const int64_t item = (int64_t)s_point;
+    const unsigned long long drawn = s_point;
+    const int64_t item = (int64_t)(drawn & ~kItemTimedOut);
     if (item >= a.B) break;
+    if (drawn & kItemTimedOut) {                  // the launch's budget ran out: drain
+      if (tid == 0) mark_timed_out(a, item);
+      continue;
+    }
     const PointRef<T> ref = point_ref(a, item);
     const int64_t b = ref.id;
     const int N = ref.N;
@@ -171,6 +187,14 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
 #pragma unroll
             for (int c = 0; c < kTJ; ++c) acc[r][c] += av[r] * xv[c];
         }
+        if constexpr (MIX) {                      // a of every node; the dual step below
+#pragma unroll
+          for (int r = 0; r < kTI; ++r)
+#pragma unroll
+            for (int c = 0; c < kTJ; ++c)
+              if (i0 + r < d && j0 + c <= N) Asv[(i0 + r) * Np + j0 + c] = tanh_c<T>(acc[r][c]);
+          continue;
+        }
 #pragma unroll
         for (int r = 0; r < kTI; ++r) {
           const int i = i0 + r;
@@ -189,6 +213,27 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
               Wk[e] = (T(1) - av * av) * pn;
             }
           }
+        }
+      }
+      if constexpr (MIX) {
+        __syncthreads();
+        // dual step with the averaged drift: (1 + lam) p = v - lam (wR a_j + wL a_{j-1})
+        for (int e2 = tid; e2 < d * N; e2 += nthr) {
+          const int i = e2 / N, j = 1 + (e2 - i * N);
+          const int e = i * Np + j;
+          const T v = P[e] + sig * (Z[e] - Z[e - 1]);
+          const T pn = (v - lam * (wr * Asv[e] + wl * Asv[e - 1])) * ilam;
+          if (chk) { const T df = pn - P[e]; rp += df * df; }
+          P[e] = pn;
+        }
+        __syncthreads();
+        // W = (1 - a_j^2)(wR p_j + wL p_{j+1}), j = 1..N-1; node 0: wL (1 - a_0^2) p_1
+        for (int e2 = tid; e2 < d * N; e2 += nthr) {
+          const int i = e2 / N, j = e2 - i * N;
+          const int e = i * Np + j;
+          const T av = Asv[e];
+          const T pw = (j == 0) ? wl * P[e + 1] : wr * P[e] + wl * P[e + 1];
+          Wk[e] = (T(1) - av * av) * pw;
         }
       }
       __syncthreads();
@@ -223,11 +268,21 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
               if (chk) { const T df = xn - xo; rx += df * df; }
               Z[e] = xn + th * (xn - xo);
               X[e] = xn;
+            } else if (MIX && i < d && j == 0) {
+              // x_0: gradient step on -delta wL H(x_0, p_1) (in W), then the prox of g
+              const int e = i * Np;
+              const T w2 = T(a.W2[i]), cc = T(a.c[i]);
+              const T xo = X[e];
+              const T xn = (xo + tau * P[e + 1] + taud * acc[r][c] + tau * w2 * cc) /
+                           (T(1) + tau * w2);
+              if (chk) { const T df = xn - xo; rx += df * df; }
+              Z[e] = xn + th * (xn - xo);
+              X[e] = xn;
             }
           }
         }
       }
-      if (!HOPF && tid < d) {
+      if (!HOPF && !MIX && tid < d) {
         const int e = tid * Np;
         const T w2 = T(a.W2[tid]), cc = T(a.c[tid]);
         const T xo = X[e];
@@ -236,18 +291,24 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
         Z[e] = xn + th * (xn - xo);
         X[e] = xn;
       }
-      // squared increments summed in the iterate type (lanes, then warps) and
-      // compared with tol rounded up to that type: exactly the FP64 test of the sum
+      // each thread's partial (iterate type) reduced over its warp in that type,
+      // accumulated over the CTA's warps in FP64 and compared with tol in FP64
       if (chk) {
-        const T sx = warp_sum<T>(rx), sp = warp_sum<T>(rp);
-        if (lane == 0) { tred[2 * warp] = sx; tred[2 * warp + 1] = sp; }
+        const T wx = warp_sum<T>(rx), wp = warp_sum<T>(rp);
+        if (lane == 0) { tred[2 * warp] = (double)wx; tred[2 * warp + 1] = (double)wp; }
       }
       __syncthreads();
       if (chk) {
-        T sx = T(0), sp = T(0);
-        for (int w = 0; w < nwarps; ++w) { sx += tred[2 * w]; sp += tred[2 * w + 1]; }
-        if (!(isfinite(sx) && isfinite(sp))) { st = HJ_POINT_NONFINITE; break; }
-        if (sx < a.tol_t && sp < a.tol_t) { st = HJ_POINT_CONVERGED; break; }
+        // one lane per warp accumulates the warps' sums in FP64 and compares
+        int verdict = 0;                                  // 1 converged, 2 non-finite
+        if (lane == 0) {
+          double sx = 0.0, sp = 0.0;
+          for (int w = 0; w < nwarps; ++w) { sx += tred[2 * w]; sp += tred[2 * w + 1]; }
+          verdict = !(isfinite(sx) && isfinite(sp)) ? 2 : (sx < a.tol && sp < a.tol) ? 1 : 0;
+        }
+        verdict = __shfl_sync(kFull, verdict, 0);
+        if (verdict == 2) { st = HJ_POINT_NONFINITE; break; }
+        if (verdict == 1) { st = HJ_POINT_CONVERGED; break; }
       }
     }
 
@@ -257,12 +318,16 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
     double acc = 0.0;
     for (int e = tid; e < d * N; e += nthr) {
       const int j = 1 + e / d, i = e - (j - 1) * d;
+      // the drift at x_j, and (MIX) weighted with the one at x_{j-1}
       if constexpr (sizeof(T) == 4) {
         T th_y = T(0);
         if (DRIFT) {
-          T y = T(0);
-          for (int k = 0; k < d; ++k) y += Am[i * dp + k] * X[k * Np + j];
-          th_y = tanh_c<T>(y);
+          T y = T(0), yl = T(0);
+          for (int k = 0; k < d; ++k) {
+            y += Am[i * dp + k] * X[k * Np + j];
+            if (MIX) yl += Am[i * dp + k] * X[k * Np + j - 1];
+          }
+          th_y = MIX ? wr * tanh_c<T>(y) + wl * tanh_c<T>(yl) : tanh_c<T>(y);
         }
         const T pv = P[i * Np + j];
         const T dx = X[i * Np + j] - X[i * Np + j - 1];
@@ -271,9 +336,12 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
         double th_y = 0.0;
         if (DRIFT) {
           const double* Ar = a.A64 + (size_t)i * d;
-          double y = 0.0;
-          for (int k = 0; k < d; ++k) y += Ar[k] * (double)X[k * Np + j];
-          th_y = tanh(y);
+          double y = 0.0, yl = 0.0;
+          for (int k = 0; k < d; ++k) {
+            y += Ar[k] * (double)X[k * Np + j];
+            if (MIX) yl += Ar[k] * (double)X[k * Np + j - 1];
+          }
+          th_y = MIX ? a.mix_wr * tanh(y) + a.mix_wl * tanh(yl) : tanh(y);
         }
         const double pv = (double)P[i * Np + j];
         const double dx = (double)X[i * Np + j] - (double)X[i * Np + j - 1];
@@ -299,6 +367,7 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
       a.V[b] = v;
       a.iters[b] = k_it;
       a.status[b] = st;
+      count_iterations(a, k_it);
     }
     if (a.traj_x != nullptr || a.traj_p != nullptr) {
       for (int e = tid; e < (N + 1) * d; e += nthr) {
@@ -314,15 +383,16 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
 }
 
 template <typename T, bool TWO>
-size_t smem_bytes(int d, int N, bool drift) {
+size_t smem_bytes(int d, int N, bool drift, bool mix = false) {
   const Layout L(d, N);
   const size_t na = drift ? (TWO ? 2 : 1) : 0;
-  return (na * L.a_elems + 4 * L.s_elems + 2 * L.dp) * sizeof(T) + 2 * 16 * sizeof(double);
+  return (na * L.a_elems + (mix ? 5 : 4) * L.s_elems + 2 * L.dp) * sizeof(T) +
+         2 * 16 * sizeof(double);
 }
 
-template <typename T, bool TWO, bool DRIFT, bool HOPF>
+template <typename T, bool TWO, bool DRIFT, bool HOPF, bool MIX>
 hj_status launch_form(const SolveArgs<T>& a, cudaStream_t s, size_t smem) {
-  auto kern = lax_td_cta_kernel<T, TWO, DRIFT, HOPF>;
+  auto kern = lax_td_cta_kernel<T, TWO, DRIFT, HOPF, MIX>;
   int dev = 0, nsm = 0, max_optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return HJ_ERR_CUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -352,17 +422,24 @@ hj_status launch_form(const SolveArgs<T>& a, cudaStream_t s, size_t smem) {
 
 template <typename T, bool TWO, bool DRIFT>
 hj_status launch(const SolveArgs<T>& a, cudaStream_t s, size_t smem) {
-  return a.formulation == HJ_FORM_HOPF ? launch_form<T, TWO, DRIFT, true>(a, s, smem)
-                                       : launch_form<T, TWO, DRIFT, false>(a, s, smem);
+  if constexpr (DRIFT) {
+    if (a.scheme != HJ_SCHEME_BE) {
+      if (a.formulation == HJ_FORM_HOPF) return HJ_ERR_UNSUPPORTED;
+      return launch_form<T, TWO, DRIFT, false, true>(a, s, smem);
+    }
+  }
+  return a.formulation == HJ_FORM_HOPF ? launch_form<T, TWO, DRIFT, true, false>(a, s, smem)
+                                       : launch_form<T, TWO, DRIFT, false, false>(a, s, smem);
 }
 
 }  // namespace
 
 template <typename T>
-size_t td_cta_smem_bytes(int d, int N, bool drift) {
-  const size_t two = smem_bytes<T, true>(d, N, drift);
+size_t td_cta_smem_bytes(int d, int N, bool drift, bool mix) {
+  mix = mix && drift;
+  const size_t two = smem_bytes<T, true>(d, N, drift, mix);
   if (two <= 227u * 1024u) return two;
-  const size_t one = smem_bytes<T, false>(d, N, drift);
+  const size_t one = smem_bytes<T, false>(d, N, drift, mix);
   return one <= 227u * 1024u ? one : 0;
 }
 
@@ -370,8 +447,9 @@ template <typename T>
 hj_status launch_td_cta_solver(const SolveArgs<T>& a, bool drift, cudaStream_t s) {
   if (a.d < 1 || a.d > kMaxD || a.N < 1 || a.N > kMaxN || a.inner_steps != 1)
     return HJ_ERR_UNSUPPORTED;
+  const bool mix = drift && a.scheme != HJ_SCHEME_BE;   // the tiled kernel: backward Euler
   if constexpr (sizeof(T) == 4) {
-    if (drift) {
+    if (drift && !mix) {
       const hj_status r = launch_td_tile_solver(a, s);
       if (r != HJ_ERR_UNSUPPORTED) return r;
     }
@@ -380,15 +458,15 @@ hj_status launch_td_cta_solver(const SolveArgs<T>& a, bool drift, cudaStream_t s
     const size_t sm = smem_bytes<T, false>(a.d, a.N, false);
     return sm <= 227u * 1024u ? launch<T, false, false>(a, s, sm) : HJ_ERR_UNSUPPORTED;
   }
-  const size_t two = smem_bytes<T, true>(a.d, a.N, true);
+  const size_t two = smem_bytes<T, true>(a.d, a.N, true, mix);
   if (two <= 227u * 1024u) return launch<T, true, true>(a, s, two);
-  const size_t one = smem_bytes<T, false>(a.d, a.N, true);
+  const size_t one = smem_bytes<T, false>(a.d, a.N, true, mix);
   if (one <= 227u * 1024u) return launch<T, false, true>(a, s, one);
   return HJ_ERR_UNSUPPORTED;
 }
 
-template size_t td_cta_smem_bytes<float>(int, int, bool);
-template size_t td_cta_smem_bytes<double>(int, int, bool);
+template size_t td_cta_smem_bytes<float>(int, int, bool, bool);
+template size_t td_cta_smem_bytes<double>(int, int, bool, bool);
 template hj_status launch_td_cta_solver<float>(const SolveArgs<float>&, bool, cudaStream_t);
 template hj_status launch_td_cta_solver<double>(const SolveArgs<double>&, bool, cudaStream_t);
 

@@ -21,9 +21,10 @@
 //            z_j = x_j + theta (x_j - x_j_old), and the g-prox of x_0 (held by
 //            the threads of the first node tile).
 // x_N stays pinned at the query point.  One group barrier after each phase
-// (__syncwarp when G = 1).  The squared increments are summed in FP32 on test
-// iterations and compared with tol rounded up to FP32; the value's (coordinate,
-// node) terms are FP32 and their sum FP64.  Groups take points from the work
+// (__syncwarp when G = 1).  On test iterations each thread's squared
+// increments (its tile, FP32) are reduced over the warp in FP32, and one lane
+// per warp accumulates the group's warp sums in FP64 and compares with tol; the value's (coordinate, node) terms are FP32 and
+// their sum FP64.  Groups take points from the work
 // counter (persistent grid); the CTA's groups share one copy of A and A^T.
 #include <cuda_runtime.h>
 
@@ -49,7 +50,7 @@ struct TileLayout {
     Ns = kTJ * TJc + 4;                              // row stride of Xs and Ws
     head_bytes = (size_t)((M * 8 + 15) / 16) * 16 + 4 * (size_t)dp * sizeof(float);
     a_floats = 2 * (size_t)d * dp;
-    grp_floats = 2 * (size_t)dp * Ns + 2 * (size_t)TJc * dp + 6 * (size_t)G;
+    grp_floats = 2 * (size_t)dp * Ns + 2 * (size_t)TJc * dp + 6 * (size_t)G;   // + 3G doubles
     grp_floats = (grp_floats + 3) & ~size_t(3);       // keep 16-byte alignment
   }
   __host__ __device__ size_t bytes(int M) const {
@@ -123,8 +124,9 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
   float* Ws = Xs + (size_t)dp * Ns;
   float* Zb = Ws + (size_t)dp * Ns;               // Zb[jt*dp + i]
   float* Pb = Zb + (size_t)L.TJc * dp;            // Pb[jt*dp + i]
-  float* tred = Pb + (size_t)L.TJc * dp;          // [2G]
-  double* vred = reinterpret_cast<double*>(tred + 2 * G + ((2 * G) & 2));   // [G], 8-byte aligned
+  // [2G] doubles (test sums) then [G] (value); Pb + TJc dp floats keeps 16-byte alignment
+  double* tred = reinterpret_cast<double*>(Pb + (size_t)L.TJc * dp);
+  double* vred = tred + 2 * G;
 
   for (int e = threadIdx.x; e < d * dp; e += blockDim.x) {
     const int k = e / dp, i = e - k * dp;
@@ -152,10 +154,15 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
 
   for (;;) {
     group_barrier<G>(grp);
-    if (t == 0) items[grp] = atomicAdd(a.counter, 1ull);
+    if (t == 0) items[grp] = draw_item(a);
     group_barrier<G>(grp);
-    const int64_t item = (int64_t)items[grp];
+    const unsigned long long drawn = items[grp];
+    const int64_t item = (int64_t)(drawn & ~kItemTimedOut);
     if (item >= a.B) break;
+    if (drawn & kItemTimedOut) {                  // the launch's budget ran out: drain
+      if (t == 0) mark_timed_out(a, item);
+      continue;
+    }
     const PointRef<float> ref = point_ref(a, item);
     const int64_t b = ref.id;
     const int N = ref.N;
@@ -289,18 +296,28 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
       float rx = 0.f, rp = 0.f;
       step(std::integral_constant<bool, true>{}, rx, rp);
       k_it += plain + 1;
-      // FP32 sums compared with tol rounded up to FP32: exactly the FP64 test of the sum
-      float sx = warp_sum<float>(rx), sp = warp_sum<float>(rp);
+      // the threads' FP32 partials reduced over each warp in FP32; one lane per
+      // warp accumulates the group's warp sums in FP64 and compares with tol
+      const float wx = warp_sum<float>(rx), wp = warp_sum<float>(rp);
       if constexpr (G > 1) {
-        if (lane == 0) { tred[2 * wig] = sx; tred[2 * wig + 1] = sp; }
+        if (lane == 0) { tred[2 * wig] = (double)wx; tred[2 * wig + 1] = (double)wp; }
         group_barrier<G>(grp);
-        sx = 0.f; sp = 0.f;
-#pragma unroll
-        for (int w = 0; w < G; ++w) { sx += tred[2 * w]; sp += tred[2 * w + 1]; }
-        group_barrier<G>(grp);                    // tred is free for the next test
       }
-      if (!(isfinite(sx) && isfinite(sp))) { st = HJ_POINT_NONFINITE; break; }
-      if (sx < a.tol_t && sp < a.tol_t) { st = HJ_POINT_CONVERGED; break; }
+      int verdict = 0;                            // 1 converged, 2 non-finite
+      if (lane == 0) {
+        double sx = 0.0, sp = 0.0;
+        if constexpr (G > 1) {
+#pragma unroll
+          for (int w = 0; w < G; ++w) { sx += tred[2 * w]; sp += tred[2 * w + 1]; }
+        } else {
+          sx = (double)wx; sp = (double)wp;
+        }
+        verdict = !(isfinite(sx) && isfinite(sp)) ? 2 : (sx < a.tol && sp < a.tol) ? 1 : 0;
+      }
+      verdict = __shfl_sync(kFull, verdict, 0);
+      if constexpr (G > 1) group_barrier<G>(grp); // tred is free for the next test
+      if (verdict == 2) { st = HJ_POINT_NONFINITE; break; }
+      if (verdict == 1) { st = HJ_POINT_CONVERGED; break; }
     }
 
     // ---- value: g(x_0) + sum_j <p_j, x_j - x_{j-1}> - delta sum_j H(x_j, p_j); FP32
@@ -346,6 +363,7 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
       a.V[b] = vacc;
       a.iters[b] = k_it;
       a.status[b] = st;
+      count_iterations(a, k_it);
     }
     if (act) {
 #pragma unroll

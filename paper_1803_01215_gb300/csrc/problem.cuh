@@ -36,6 +36,18 @@ struct hj_problem_s {
   std::mutex mu;
 };
 
+namespace hj {
+// Residual of the discrete characteristic equations from trajectories (kkt.cu):
+// one thread per (point, node) for the register-resident kernel's families and
+// dimensions (kkt_node.cu; HJ_ERR_UNSUPPORTED for others), else one CTA per point.
+bool kkt_family_supported(int family);
+hj_status launch_kkt(const hj_problem_s* p, int64_t B, int32_t N, bool fp64, const double* t,
+                     const void* traj_x, const void* traj_p, double* kkt, cudaStream_t s);
+template <typename T>
+hj_status launch_kkt_nodes(const hj_problem_s* p, int64_t B, int32_t N, const double* t,
+                           const T* X, const T* P, double* kkt, cudaStream_t s);
+}  // namespace hj
+
 namespace hj_detail {
 
 inline bool all_finite(const double* v, int64_t n) {
@@ -80,7 +92,7 @@ hj_status dispatch(hj_problem_s* p, const hj::SolveArgs<T>& a, hj::WarpConfig cf
     const hj_status r = hj::launch_warp_solver<T>(p->family, a, cfg, s);
     if (r != HJ_ERR_UNSUPPORTED) return r;
   }
-  if (a.scheme != HJ_SCHEME_BE || a.value_stop) return HJ_ERR_UNSUPPORTED;   // register kernel only
+  if (a.value_stop) return HJ_ERR_UNSUPPORTED;   // the value test: register kernel only
   if (p->family == HJ_FAMILY_TANH_DRIFT) return hj::launch_td_cta_solver<T>(a, true, s);
   if (p->family == HJ_FAMILY_EIKONAL)
     return a.eik_moving ? HJ_ERR_UNSUPPORTED : hj::launch_eik_cta_solver<T>(a, s);
@@ -126,8 +138,6 @@ hj::SolveArgs<T> make_args(const hj_problem_s* prob, int64_t B, int32_t N,
   a.B = B; a.N = N; a.d = prob->d;
   a.sigma = o.sigma; a.tau = o.tau; a.theta = o.theta; a.tol = o.tol;
   a.sigma_t = T(o.sigma); a.tau_t = T(o.tau); a.theta_t = T(o.theta);
-  a.tol_t = T(o.tol);
-  if ((double)a.tol_t < o.tol) a.tol_t = std::nextafter(a.tol_t, T(INFINITY));
   a.max_iter = o.max_iter; a.check_every = o.check_every; a.inner_steps = o.inner_steps;
   a.seed = o.seed; a.radius = o.init_radius; a.point_offset = o.point_offset;
   a.formulation = o.formulation;
@@ -149,6 +159,8 @@ hj::SolveArgs<T> make_args(const hj_problem_s* prob, int64_t B, int32_t N,
   a.cost_sign = (prob->family == HJ_FAMILY_EIKONAL && prob->eik[0] < 0) ? -1.0 : 1.0;
   a.game_d1 = (prob->family == HJ_FAMILY_GAME_NORMS) ? (int32_t)prob->eik[0] : prob->d;
   a.counter = prob->counter;
+  a.budget_ns = (int64_t)(o.time_budget_ms * 1e6);
+  a.iter_budget = o.iter_budget;
   fill_args<T>(a, prob, B, N, o, xq, t, V, iters, status, traj_x, traj_p, warm_x, warm_p);
   return a;
 }
@@ -164,6 +176,8 @@ inline hj_status check_opts(const hj_solver_opts& o) {
   if (o.scheme != HJ_SCHEME_BE && o.scheme != HJ_SCHEME_FE && o.scheme != HJ_SCHEME_TRAP)
     return HJ_ERR_INVALID_ARG;
   if (!(o.value_tol >= 0.0) || !std::isfinite(o.value_tol)) return HJ_ERR_INVALID_ARG;
+  if (!(o.time_budget_ms >= 0.0) || !(o.time_budget_ms <= 9.0e12) || o.iter_budget < 0)
+    return HJ_ERR_INVALID_ARG;
   if (!(std::isfinite(o.init_radius) && o.init_radius >= 0.0) || o.point_offset < 0)
     return HJ_ERR_INVALID_ARG;
   if (4.0 * o.sigma * o.tau >= 1.0) return HJ_ERR_STEP_SIZE;
@@ -200,11 +214,33 @@ hj_status run_solve(hj_problem_s* prob, int64_t B, int32_t N, const hj_solver_op
                     hj::WarpConfig cfg, const double* xq, const double* t, double* V,
                     int32_t* iters, int8_t* status, void* traj_x, void* traj_p,
                     const void* warm_x, const void* warm_p, cudaStream_t s) {
-  if (cudaMemsetAsync(prob->counter, 0, sizeof(unsigned long long), s) != cudaSuccess)
+  if (cudaMemsetAsync(prob->counter, 0, hj::kCounterWords * sizeof(unsigned long long), s) !=
+      cudaSuccess)
     return HJ_ERR_CUDA;
   const hj::SolveArgs<T> a = make_args<T>(prob, B, N, o, xq, t, V, iters, status, traj_x,
                                           traj_p, warm_x, warm_p);
   return dispatch<T>(prob, a, cfg, s);
+}
+
+// The solve with the per-point residual of the discrete characteristic
+// equations, evaluated after the solve from the trajectories (written to a
+// stream-ordered workspace when the caller passes none).
+template <typename T>
+hj_status run_solve_kkt(hj_problem_s* prob, int64_t B, int32_t N, const hj_solver_opts& o,
+                        hj::WarpConfig cfg, const double* xq, const double* t, double* V,
+                        int32_t* iters, int8_t* status, double* kkt, void* traj_x, void* traj_p,
+                        const void* warm_x, const void* warm_p, cudaStream_t s) {
+  const size_t bytes = (size_t)B * (size_t)(N + 1) * (size_t)prob->d * sizeof(T);
+  unsigned char* ws = nullptr;
+  const int need = (traj_x == nullptr) + (traj_p == nullptr);
+  if (need > 0 && cudaMallocAsync(reinterpret_cast<void**>(&ws), need * bytes, s) != cudaSuccess)
+    return HJ_ERR_OOM;
+  void* tx = traj_x != nullptr ? traj_x : ws;
+  void* tp = traj_p != nullptr ? traj_p : (traj_x != nullptr ? ws : ws + bytes);
+  hj_status r = run_solve<T>(prob, B, N, o, cfg, xq, t, V, iters, status, tx, tp, warm_x, warm_p, s);
+  if (r == HJ_OK) r = hj::launch_kkt(prob, B, N, sizeof(T) == 8, t, tx, tp, kkt, s);
+  if (ws != nullptr && cudaFreeAsync(ws, s) != cudaSuccess && r == HJ_OK) r = HJ_ERR_CUDA;
+  return r;
 }
 
 }  // namespace hj_detail

@@ -94,7 +94,7 @@ hj_status launch_bucket(hj_ragged_plan_s* p, size_t bi, hj::WarpConfig cfg, cons
   a.Nv = p->d_N;
   a.xq_off = p->d_xq_off;
   a.traj_off = p->d_traj_off;
-  a.counter = p->d_counters + bi;
+  a.counter = p->d_counters + (size_t)bi * hj::kCounterWords;
   return dispatch<T>(prob, a, cfg, s);
 }
 
@@ -177,6 +177,7 @@ hj_status hj_ragged_plan_create(hj_ragged_plan* out, int32_t n_prob, const hj_pr
     if (k.cfg.G == 0) {
       // shared-memory kernel: the bucket's largest N must fit its shared memory
       const bool drift = pr->family == HJ_FAMILY_TANH_DRIFT;
+      const bool mix = opts->scheme != HJ_SCHEME_BE;
       if (pr->family == HJ_FAMILY_QUADCOPTER || pr->family == HJ_FAMILY_GAME_NORMS)
         r = HJ_ERR_UNSUPPORTED;
       else if (pr->family == HJ_FAMILY_EIKONAL) {
@@ -184,8 +185,8 @@ hj_status hj_ragged_plan_create(hj_ragged_plan* out, int32_t n_prob, const hj_pr
         if ((f64 ? hj::eik_cta_smem_bytes<double>(pr->d, k.nmax)
                  : hj::eik_cta_smem_bytes<float>(pr->d, k.nmax)) == 0)
           r = HJ_ERR_UNSUPPORTED;
-      } else if ((f64 ? hj::td_cta_smem_bytes<double>(pr->d, k.nmax, drift)
-                    : hj::td_cta_smem_bytes<float>(pr->d, k.nmax, drift)) == 0)
+      } else if ((f64 ? hj::td_cta_smem_bytes<double>(pr->d, k.nmax, drift, mix)
+                    : hj::td_cta_smem_bytes<float>(pr->d, k.nmax, drift, mix)) == 0)
         r = HJ_ERR_UNSUPPORTED;
     }
     if (r == HJ_OK) r = upload(&k.d_ids, k.ids.data(), k.ids.size());
@@ -194,7 +195,8 @@ hj_status hj_ragged_plan_create(hj_ragged_plan* out, int32_t n_prob, const hj_pr
   if (r == HJ_OK) r = upload(&p->d_xq_off, p->xq_off.data(), (size_t)B);
   if (r == HJ_OK) r = upload(&p->d_traj_off, p->traj_off.data(), (size_t)B);
   if (r == HJ_OK && cudaMalloc(reinterpret_cast<void**>(&p->d_counters),
-                               p->buckets.size() * sizeof(unsigned long long)) != cudaSuccess)
+                               p->buckets.size() * hj::kCounterWords *
+                                   sizeof(unsigned long long)) != cudaSuccess)
     r = HJ_ERR_OOM;
   for (int i = 0; i < kSideStreams && r == HJ_OK; ++i) {
     if (cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking) != cudaSuccess ||
@@ -267,7 +269,8 @@ hj_status hj_ragged_solve(hj_ragged_plan plan, const double* xq, const double* t
     hj_status r = HJ_OK;
     const size_t nb = plan->buckets.size();
     const int nside = (int)std::min<size_t>(nb, kSideStreams);
-    if (cudaMemsetAsync(plan->d_counters, 0, nb * sizeof(unsigned long long), c) != cudaSuccess ||
+    if (cudaMemsetAsync(plan->d_counters, 0, nb * hj::kCounterWords * sizeof(unsigned long long),
+                        c) != cudaSuccess ||
         cudaEventRecord(plan->ev_fork, c) != cudaSuccess)
       r = HJ_ERR_CUDA;
     for (int i = 0; i < nside && r == HJ_OK; ++i)
@@ -331,7 +334,8 @@ hj_status hj_ragged_autotune(hj_ragged_plan plan, const double* xq, const double
         b.inner_steps = inner;
         float tot = 0.0f;
         for (int rep = 0; rep <= repeats && r == HJ_OK; ++rep) {
-          if (cudaMemsetAsync(plan->d_counters + bi, 0, sizeof(unsigned long long), s) !=
+          if (cudaMemsetAsync(plan->d_counters + (size_t)bi * hj::kCounterWords, 0,
+                              hj::kCounterWords * sizeof(unsigned long long), s) !=
                   cudaSuccess ||
               cudaEventRecord(e0, s) != cudaSuccess) {
             r = HJ_ERR_CUDA;

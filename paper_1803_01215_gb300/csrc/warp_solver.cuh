@@ -18,7 +18,10 @@
 //   x_0  <- prox_{tau g}(x_0 + tau p_1)
 //   x_j  <- x_j - tau (p_j - p_{j+1}) + tau delta grad_x H(x_j^k, p_j)      j = 1..N-1
 //   z_j  <- x_j^{k+1} + theta (x_j^{k+1} - x_j^k)
-// and, on test iterations, the squared increments summed in FP64 over the group.
+// and, on test iterations, the squared increments: each lane's partial in the
+// iterate type, reduced over the warp by shuffles in that type, then on one
+// lane per warp accumulated over the group's warps in FP64 and compared with
+// tol in FP64.
 //
 // MIX = true runs the forward-Euler and trapezoid schemes (HJ_SCHEME_FE/TRAP):
 // H on interval j is wR H(x_j, .) + wL H(x_{j-1}, .), so the dual step also
@@ -435,19 +438,31 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     T rx = T(0), rp = T(0), vacc = T(0);
     step(std::integral_constant<bool, true>{}, rx, rp, vacc);
     k_it += plain + 1;
-    // lane partials summed across the warp (and the group's warps) in the
-    // iterate type; the test against tol_t is then exactly the FP64 test of
-    // that sum, so the loop needs no FP64 instruction
-    T sx = lanes_sum<G, T>(rx), sp = lanes_sum<G, T>(rp);
+    // each lane's partial (its own nodes, in the iterate type) reduced over the
+    // warp by shuffles in that type (a 5-level tree: relative error <= 5 ulp);
+    // one lane per warp accumulates the group's warp sums in FP64, compares with
+    // tol in FP64 and hands the verdict to its warp (FP64 on one lane only: the
+    // FP64 pipe runs at 1/64 of the FP32 rate)
+    const T wx = lanes_sum<G, T>(rx), wp = lanes_sum<G, T>(rp);
     if constexpr (G > 1) {
-      if (lane == 0) { sh.red[wg][0] = sx; sh.red[wg][1] = sp; }
+      if (lane == 0) { sh.red[wg][0] = wx; sh.red[wg][1] = wp; }
       __syncthreads();
-      sx = T(0); sp = T(0);
-#pragma unroll
-      for (int w = 0; w < G; ++w) { sx += sh.red[w][0]; sp += sh.red[w][1]; }
     }
-    if (!(isfinite(sx) && isfinite(sp))) { st = HJ_POINT_NONFINITE; break; }
-    if (sx < a.tol_t && sp < a.tol_t) { st = HJ_POINT_CONVERGED; break; }
+    int verdict = 0;                                 // 1 converged, 2 non-finite
+    if (lane == 0) {
+      double sx = 0.0, sp = 0.0;
+      if constexpr (G > 1) {
+#pragma unroll
+        for (int w = 0; w < G; ++w) { sx += (double)sh.red[w][0]; sp += (double)sh.red[w][1]; }
+      } else {
+        sx = (double)wx; sp = (double)wp;
+      }
+      verdict = !(isfinite(sx) && isfinite(sp)) ? 2 : (sx < a.tol && sp < a.tol) ? 1 : 0;
+    }
+    if constexpr (G == 0) verdict = __shfl_sync(half_mask(), verdict, (int)(threadIdx.x & 16));
+    else verdict = __shfl_sync(kFull, verdict, 0);
+    if (verdict == 2) { st = HJ_POINT_NONFINITE; break; }
+    if (verdict == 1) { st = HJ_POINT_CONVERGED; break; }
     if constexpr (kValueTest) {
       if (a.value_stop) {                 // the value moved less than value_tol since the last test
         double v = lanes_sum<G, double>((double)vacc);
@@ -535,6 +550,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     a.V[pt.id] = a.cost_sign * acc;
     a.iters[pt.id] = k_it;
     a.status[pt.id] = st;
+    count_iterations(a, k_it);
   }
   if (a.traj_x != nullptr) {
     T* o = a.traj_x + pt.traj;
@@ -578,22 +594,27 @@ lax_warp_kernel(const SolveArgs<T> a) {
   const int lane = (G == 0) ? (int)(threadIdx.x & 15) : (int)(threadIdx.x & 31);
   const int wg = (G <= 1) ? 0 : (int)(threadIdx.x >> 5);
   for (;;) {
-    int64_t item;
+    unsigned long long drawn;
     if constexpr (G == 1) {
       unsigned long long bb = 0;
-      if (lane == 0) bb = atomicAdd(a.counter, 1ull);
-      item = (int64_t)__shfl_sync(kFull, bb, 0);
+      if (lane == 0) bb = draw_item(a);
+      drawn = __shfl_sync(kFull, bb, 0);
     } else if constexpr (G == 0) {           // each half draws its own points
       unsigned long long bb = 0;
-      if (lane == 0) bb = atomicAdd(a.counter, 1ull);
-      item = (int64_t)__shfl_sync(half_mask(), bb, (int)(threadIdx.x & 16));
+      if (lane == 0) bb = draw_item(a);
+      drawn = __shfl_sync(half_mask(), bb, (int)(threadIdx.x & 16));
     } else {
       __syncthreads();                       // the previous point is finished by every warp
-      if (threadIdx.x == 0) sh.item = atomicAdd(a.counter, 1ull);
+      if (threadIdx.x == 0) sh.item = draw_item(a);
       __syncthreads();
-      item = (int64_t)sh.item;
+      drawn = sh.item;
     }
+    const int64_t item = (int64_t)(drawn & ~kItemTimedOut);
     if (item >= a.B) break;
+    if (drawn & kItemTimedOut) {             // the launch's budget ran out: drain
+      if (lane == 0 && wg == 0) mark_timed_out(a, item);
+      continue;
+    }
     solve_point<T, F, D, NPL, G, TH1, HOPF, MIX>(a, fam, item, lane, wg, sh);
   }
 }

@@ -61,9 +61,16 @@ def test_invalid_arguments_rejected_before_device_use(lib):
     opts = binding.make_opts(sigma=1.0, tau=0.24)
     lib.hj_solve_batch.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_int32,
-                                   ctypes.POINTER(binding.SolverOpts)] + [ctypes.c_void_p] * 8
+                                   ctypes.POINTER(binding.SolverOpts)] + [ctypes.c_void_p] * 9
     assert lib.hj_solve_batch(None, 4, None, None, 8, ctypes.byref(opts),
-                              None, None, None, None, None, None, None, None) == 1
+                              None, None, None, None, None, None, None, None, None) == 1
+    lib.hj_kkt_residual.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 4
+    assert lib.hj_kkt_residual(None, 4, None, 8, 0, None, None, None, None) == 1
+    lib.hj_shapes_save.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
+    lib.hj_shapes_load.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_void_p]
+    assert lib.hj_shapes_save(None, b"/tmp/x") == 1
+    assert lib.hj_shapes_load(None, b"/tmp/x", None) == 1
     assert lib.hj_problem_destroy(None) == 0
 
 

@@ -63,18 +63,20 @@ def test_eikonal_fp64_same_stop_and_fp32_value(d, sign):
     same = (g["iters"] == o["iters"]) & conv
     assert np.mean(same) >= 0.8
     assert value_err(g["V"][same], o["V"][same]).max() <= 1e-9
-    # FP32 at the paper's stop (tol 1e-8; with sigma = 100 FP32 rounding keeps
-    # the squared increments near 1e-10) against the converged oracle, on the
-    # points where that stop itself is accurate: the negative equation converges
-    # slowly, and for a few points the FP64 run stopped at tol 1e-8 is still
-    # 1e-3..1e-2 from the converged value, which no precision can meet
-    oc = O.solve(w, tol=1e-22, max_iter=200000, check_every=8)
-    g32 = gpu(w, "fp32")
-    stop_ok = (oc["status"] == O.CONVERGED) & (g["status"] == O.CONVERGED) \
-        & (value_err(g["V"], oc["V"]) <= 1e-5)
-    ok = stop_ok & (g32["status"] == O.CONVERGED)
-    assert np.mean(ok) >= 0.6             # most points, so the bar below is not vacuous
-    assert value_err(g32["V"][ok], oc["V"][ok]).max() <= 1e-4
+    # FP32 against the converged oracle on every point.  The negative equation
+    # converges slowly: at the paper's stop (tol 1e-8) a few points are still
+    # 1e-3..1e-2 from the converged value in FP64 too, so the bar is taken at a
+    # tighter stop where the FP64 path meets 1e-5 on every point (with sigma = 100
+    # FP32 rounding keeps the squared increments near 1e-10, so FP32 stops at 1e-9)
+    oc = O.solve(w, tol=1e-22, max_iter=400000, check_every=8)
+    assert np.all(oc["status"] == O.CONVERGED)
+    t64 = gpu(w, "fp64", tol=1e-16, max_iter=400000, check_every=16)
+    t32 = gpu(w, "fp32", tol=1e-9 if sign < 0 else 1e-11, max_iter=400000, check_every=16)
+    e64 = value_err(t64["V"], oc["V"])
+    e32 = value_err(t32["V"], oc["V"])
+    print(f"eikonal d={d} s={sign:+d} tight stop: FP64 max {e64.max():.2e}, FP32 max {e32.max():.2e}")
+    assert e64.max() <= 1e-5
+    assert e32.max() <= 1e-4
 
 
 @pytest.mark.parametrize("d", [2, 37])

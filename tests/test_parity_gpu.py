@@ -138,6 +138,13 @@ def test_full_size_quadcopter_sampled():
     print(f"quadcopter 4096: converged {conv.sum()}, median iters {np.median(g['iters'])}, "
           f"sampled V rel {ev.max():.2e}")
     assert ev.max() <= 1e-4
+    # trajectories of the sampled points at the tighter stop of the trajectory bar
+    # (the whole batch rerun, so each point keeps its own initial guess)
+    gt = gpu(w, "fp32", tol=1e-10)
+    et = np.max(np.abs(gt["traj_x"][idx] - o["x"]))
+    ep = np.max(np.abs(gt["traj_p"][idx] - o["p"]))
+    print(f"quadcopter 4096 at tol 1e-10: sampled |dx| {et:.2e} |dp| {ep:.2e}")
+    assert et <= 1e-3 and ep <= 1e-3
     # the points the GPU reports as not converged are slow for the oracle too
     bad = np.where(~conv)[0][:2]
     if bad.size:

@@ -33,12 +33,17 @@ def _eik(d, sign, N, B, seed=71):
 
 # the default launch shapes (one node per lane, G = 1, 2, 4 for N = 23, 64, 100,
 # 128) with ragged tails, the four families; every other shape is checked by
-# test_scheme_every_launch_shape_gives_the_same_iterates
+# test_scheme_every_launch_shape_gives_the_same_iterates.  tanh drift at d >= 8
+# (and d = 4 with N = 200, beyond the mixed FP64 register kernel) runs the
+# shared-memory kernel, the eikonal family at d not in {2, 10} the
+# coordinate-parallel one, d not a multiple of 4 included
 CASES = [
     ("quadcopter", 12, 23), ("quadcopter", 12, 64), ("quadcopter", 12, 100),
     ("tanh_drift", 4, 50), ("tanh_drift", 2, 128),
     ("eikonal+", 2, 5), ("eikonal+", 10, 30), ("eikonal-", 2, 10),
     ("game", 2, 5), ("game", 2, 23), ("game", 7, 10),
+    ("tanh_drift", 8, 16), ("tanh_drift", 13, 21), ("tanh_drift", 32, 32),
+    ("tanh_drift", 4, 200), ("eikonal+", 5, 10), ("eikonal-", 37, 10), ("eikonal+", 3, 40),
 ]
 
 
@@ -79,7 +84,8 @@ def test_scheme_fixed_iterations_elementwise(family, d, N, scheme, precision):
 
 
 @pytest.mark.parametrize("family,d,N,B", [
-    ("quadcopter", 12, 32, 24), ("tanh_drift", 4, 40, 40), ("eikonal+", 2, 10, 24)])
+    ("quadcopter", 12, 32, 24), ("tanh_drift", 4, 40, 40), ("eikonal+", 2, 10, 24),
+    ("tanh_drift", 32, 32, 12), ("eikonal+", 5, 10, 24)])
 @pytest.mark.parametrize("scheme", ["fe", "trap"])
 def test_scheme_fp64_same_stop_and_fp32_value(family, d, N, B, scheme):
     w = _case(family, d, N, B, seed=22)
@@ -239,12 +245,14 @@ def test_scheme_argument_errors():
     with pytest.raises(binding.HJError) as e:
         binding.solve_batch(prob, xq, t, 8, bad)
     assert e.value.code == 1                                       # HJ_ERR_INVALID_ARG
-    # no mixed kernel for the shared-memory tanh drift sizes
+    # the shared-memory tanh-drift kernel runs the mixed schemes, but not the Hopf form
     wt = _custom("tanh_drift", 8, 8, B=3)
     pt = binding.Problem.from_workload(wt)
     xt = torch.as_tensor(wt["xq"], device="cuda")
+    binding.solve_batch(pt, xt, t, 8, binding.make_opts(sigma=1.0, tau=0.24, scheme="trap"))
     with pytest.raises(binding.HJError) as e:
-        binding.solve_batch(pt, xt, t, 8, binding.make_opts(sigma=1.0, tau=0.24, scheme="trap"))
+        binding.solve_batch(pt, xt, t, 8, binding.make_opts(sigma=1.0, tau=0.24, scheme="trap",
+                                                            formulation="hopf"))
     assert e.value.code == 2
     # the reverse sweep differentiates the backward-Euler iteration only
     fe = binding.make_opts(sigma=1.0, tau=0.24, scheme="fe", precision="fp64")
