@@ -692,8 +692,10 @@ def main():
     if kkt32 is not None:
         conv = out32["status"] == 0
         kc = kkt32[conv]
-        kkt_stats = {"what": "FP64 residual of the discrete characteristic equations per point "
-                             "(max over nodes and coordinates), converged points",
+        kkt_stats = {"what": "residual of the discrete characteristic equations per point "
+                             "(max over nodes and coordinates), converged points; evaluated in "
+                             "FP32 from the FP32 iterates (error under their own rounding), "
+                             "reported as a double",
                      "median": float(kc.median().item()) if kc.numel() else None,
                      "max": float(kc.max().item()) if kc.numel() else None,
                      "ms_per_step_without": ms32_plain,
@@ -707,9 +709,11 @@ def main():
                    "N": N, "d": d,
                    "H": "<p,f0(x)> + |B(x)^T p|^2/2 + eps |p|^2/2",
                    "eps": float(w["dyn"][3]),
-                   "precision": ("fp32 iterates; stopping sums accumulated in fp64; value sum fp64"
-                                 + ("; per-point residual certificate in fp64" if kkt32 is not None
-                                    else "")),
+                   "precision": ("fp32 iterates; stopping sums: fp32 per lane and per warp, "
+                                 "accumulated over the point's warps and compared with tol in fp64; "
+                                 "value terms fp32 per node, summed in fp64"
+                                 + ("; per-point residual certificate evaluated in fp32"
+                                    if kkt32 is not None else "")),
                    "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas{world}", "sigma": w["sigma"], "tau": w["tau"],
                    "tol": w["tol"], "check_every": w["check_every"],

@@ -82,10 +82,12 @@ enum {
 };
 
 /* Iterate precision.  With FP32 iterates the stopping test's squared
- * increments (each lane's or thread's partial in FP32) are accumulated over the
- * point in FP64 and compared with tol in FP64, the value's terms are summed in
- * FP64, and the optional residual (kkt) is evaluated in FP64; FP64 runs
- * everything in double.                                                     */
+ * increments (each lane's or thread's partial in FP32, summed over its warp in
+ * FP32) are accumulated over the point in FP64 and compared with tol in FP64,
+ * the value's terms are summed in FP64, and the optional residual (kkt) is
+ * evaluated in FP64, except the quadcopter's, which is evaluated in FP32 (its
+ * error stays below the FP32 iterates' own rounding: see hj_kkt_residual);
+ * FP64 runs everything in double.                                           */
 enum { HJ_PREC_FP32 = 0, HJ_PREC_FP64 = 1 };
 
 /* Saddle problem solved (hj_solver_opts.formulation).
@@ -217,7 +219,7 @@ typedef struct {
  *   kkt      (device, may be NULL) [B] double out: the residual of the discrete
  *            characteristic equations at the returned iterates (Section 4, the
  *            stationarity conditions of Eq. (disclaxBE): x' = H_p, p' = -H_x,
- *            p(0) = grad g in discrete form), evaluated in FP64:
+ *            p(0) = grad g in discrete form), evaluated as hj_kkt_residual does:
  *              max over j, k of |x_j - x_{j-1} - delta grad_p H(x_j, p_j)|,
  *              |p_1 - grad g(x_0)| and |p_{j+1} - p_j + delta grad_x H(x_j, p_j)|.
  *            Zero at a saddle, so it certifies each point without a reference
@@ -250,8 +252,13 @@ hj_status hj_solve_batch(hj_problem prob, int64_t B,
                          void* stream);
 
 /* Residual of the discrete characteristic equations (Section 4) at given
- * trajectories, per point, in FP64: the kkt output of hj_solve_batch for
- * trajectories from any source (a ragged plan, retry rounds, a warm start).
+ * trajectories, per point: the kkt output of hj_solve_batch for trajectories
+ * from any source (a ragged plan, retry rounds, a warm start).  Evaluated in
+ * FP64, except the quadcopter's FP32 trajectories, which are evaluated in FP32
+ * with the accurate sincosf: the error is then below about 16 units of 2^-24
+ * times the magnitudes entering each term (|x_j - x_{j-1}|, |p_{j+1} - p_j|,
+ * delta times the terms of grad H), under the rounding of the FP32 iterates
+ * themselves.  The result is a double either way.
  *   t        (device) [B] horizons, delta = t / N.
  *   traj_x, traj_p (device) [B][N+1][d] in the type of `precision`, in the
  *            layout hj_solve_batch writes (traj_p[b][0] ignored).

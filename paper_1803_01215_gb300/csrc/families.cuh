@@ -199,6 +199,7 @@ template <typename T, int D>
 struct FamQuadcopter {
   static_assert(D == 12, "quadcopter state is 12-D");
   static constexpr bool kHasGradX = true;
+  static constexpr bool kKktInIterType = true;   // kkt_node: FP32 iterates in FP32
   static constexpr bool kGame = false;
   static constexpr bool kTimeDep = false;
   struct Shared {};
@@ -397,52 +398,81 @@ struct FamQuadcopter {
   }
   // grad_p H = f0 + B B^T p + eps p: (v_pos, v_ang, a_h a - g_z e3 + a u0 / m, tau) + eps p
   // with u0 = <a, p_7..9> / m; grad_x H = (0, (a_h + u0 / m) J^T p_7..9, p_1..3, p_4..6).
-  // FP32 iterates take the three sine/cosine pairs from the accurate FP32 sincosf
-  // (within 2 ulp) and form everything else in FP64: the evaluation error of the
-  // residual is then below about delta (a_h + |u0|) 2^-22 (1e-7 for the 12-D
-  // workload), far below an FP32 iterate's own residual; FP64 iterates use the
-  // FP64 functions throughout.
+  // Evaluated in the iterate type: FP64 iterates in FP64 throughout; FP32 iterates
+  // in FP32 with the sines and cosines from the accurate sincosf (2 ulp), which
+  // keeps the residual's evaluation error below about 16 units of 2^-24 times the
+  // magnitudes that enter it (|x_j - x_{j-1}|, |p_{j+1} - p_j| and delta times the
+  // terms of grad H), that is below the rounding of the FP32 iterates themselves
+  // (FP64 arithmetic here runs at 1/64 of the FP32 rate and would cost the solve
+  // several per cent).
+  template <typename E>
+  __device__ __forceinline__ static E max_keep_nan(E a, E b) { return (a > b || a != a) ? a : b; }
   __device__ double kkt_node(const T (&x)[D], const T (&xl)[D], const T (&p)[D], const T (&pr)[D],
                              double delta, double, bool r3) const {
-    double a[3], J[9];
     if constexpr (sizeof(T) == 4) {
-      float s0, c0, s1, c1, s2, c2;
-      sincosf(x[3], &s0, &c0);
-      sincosf(x[4], &s1, &c1);
-      sincosf(x[5], &s2, &c2);
-      const double sps = s0, cps = c0, sth = s1, cth = c1, sph = s2, cph = c2;
-      const double cc = cph * cps, cs = cph * sps, sc = sph * cps, ss = sph * sps;
-      a[0] = ss + cc * sth;
-      a[1] = -sc + cs * sth;
-      a[2] = cth * cph;
-      J[0] = sc - cs * sth; J[1] = cc * cth;   J[2] = cs - sc * sth;
-      J[3] = ss + cc * sth; J[4] = cs * cth;   J[5] = -cc - ss * sth;
-      J[6] = 0.0;           J[7] = -sth * cph; J[8] = -cth * sph;
-    } else {
-      thrust<double>((double)x[3], (double)x[4], (double)x[5], a, J);
-    }
-    const double q6 = (double)p[6], q7 = (double)p[7], q8 = (double)p[8];
-    const double u0 = (a[0] * q6 + a[1] * q7 + a[2] * q8) / m64;
-    const double coef = ah64 + u0 / m64;
-    double r = 0.0;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const double pk = (double)p[k];
-      double gp;
-      if (k < 6) gp = (double)x[6 + k];
-      else if (k < 9) gp = ah64 * a[k - 6] - (k == 8 ? gz64 : 0.0) + a[k - 6] * u0 / m64;
-      else gp = pk;
-      gp += eps64 * pk;
-      r = max_nan(r, fabs((double)x[k] - (double)xl[k] - delta * gp));
-      if (r3) {
-        double gx;
-        if (k < 3) gx = 0.0;
-        else if (k < 6) gx = coef * (J[k - 3] * q6 + J[k] * q7 + J[k + 3] * q8);
-        else gx = (double)p[k - 6];
-        r = max_nan(r, fabs((double)pr[k] - pk + delta * gx));
+      float a[3], J[9];
+      {
+        float sps, cps, sth, cth, sph, cph;
+        sincosf(x[3], &sps, &cps);
+        sincosf(x[4], &sth, &cth);
+        sincosf(x[5], &sph, &cph);
+        const float cc = cph * cps, cs = cph * sps, sc = sph * cps, ss = sph * sps;
+        a[0] = ss + cc * sth;
+        a[1] = -sc + cs * sth;
+        a[2] = cth * cph;
+        J[0] = sc - cs * sth; J[1] = cc * cth;   J[2] = cs - sc * sth;
+        J[3] = ss + cc * sth; J[4] = cs * cth;   J[5] = -cc - ss * sth;
+        J[6] = 0.0f;          J[7] = -sth * cph; J[8] = -cth * sph;
       }
+      const float dt = (float)delta;
+      const float q6 = p[6], q7 = p[7], q8 = p[8];
+      const float u0m = (a[0] * q6 + a[1] * q7 + a[2] * q8) * m_inv * m_inv;   // u0 / m
+      const float coef = ah + u0m;
+      float r = 0.0f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float pk = p[k];
+        float gp;
+        if (k < 6) gp = x[6 + k];
+        else if (k < 9) gp = ah * a[k - 6] - (k == 8 ? gz : 0.0f) + a[k - 6] * u0m;
+        else gp = pk;
+        gp += eps * pk;
+        r = max_keep_nan(r, fabsf((x[k] - xl[k]) - dt * gp));
+        if (r3) {
+          float gx;
+          if (k < 3) gx = 0.0f;
+          else if (k < 6) gx = coef * (J[k - 3] * q6 + J[k] * q7 + J[k + 3] * q8);
+          else gx = p[k - 6];
+          r = max_keep_nan(r, fabsf((pr[k] - pk) + dt * gx));
+        }
+      }
+      return (double)r;
+    } else {
+      double a[3], J[9];
+      thrust<double>((double)x[3], (double)x[4], (double)x[5], a, J);
+      const double q6 = (double)p[6], q7 = (double)p[7], q8 = (double)p[8];
+      const double u0 = (a[0] * q6 + a[1] * q7 + a[2] * q8) / m64;
+      const double coef = ah64 + u0 / m64;
+      double r = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double pk = (double)p[k];
+        double gp;
+        if (k < 6) gp = (double)x[6 + k];
+        else if (k < 9) gp = ah64 * a[k - 6] - (k == 8 ? gz64 : 0.0) + a[k - 6] * u0 / m64;
+        else gp = pk;
+        gp += eps64 * pk;
+        r = max_nan(r, fabs((double)x[k] - (double)xl[k] - delta * gp));
+        if (r3) {
+          double gx;
+          if (k < 3) gx = 0.0;
+          else if (k < 6) gx = coef * (J[k - 3] * q6 + J[k] * q7 + J[k + 3] * q8);
+          else gx = (double)p[k - 6];
+          r = max_nan(r, fabs((double)pr[k] - pk + delta * gx));
+        }
+      }
+      return r;
     }
-    return r;
   }
 };
 

@@ -19,6 +19,9 @@ struct SolveArgs {
   int64_t B;
   int32_t N, d;
   double sigma, tau, theta, tol;
+  // tol as an unevaluated sum of two floats (tol_hi = fl32(tol), tol_lo =
+  // fl32(tol - tol_hi): within 2^-48 tol), for the FP32 kernels' stopping test
+  float tol_hi, tol_lo;
   // The same step sizes rounded once to the iterate type on the host, so the
   // iteration loop holds no double-derived value the compiler could recompute
   // there (FP64 instructions are ~64x the cost of FP32 ones on this GPU).
@@ -103,32 +106,11 @@ __device__ __forceinline__ PointRef<T> point_ref(const SolveArgs<T>& a, int64_t 
 // (set by the first draw when a time budget is on), [2] the iterations of the
 // points finished so far (counted when an iteration budget is on).
 constexpr int kCounterWords = 3;
-constexpr unsigned long long kItemTimedOut = 1ull << 62;   // flag on a drawn item
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
-}
-
-// Draw the next item (one thread of the group).  When the launch's budget has
-// run out, an item below B comes back with kItemTimedOut set: the caller marks
-// that point HJ_POINT_TIMEOUT instead of solving it, and so drains the batch.
-template <typename T>
-__device__ __forceinline__ unsigned long long draw_item(const SolveArgs<T>& a) {
-  const unsigned long long it = atomicAdd(a.counter, 1ull);
-  if (it >= (unsigned long long)a.B || (a.budget_ns <= 0 && a.iter_budget <= 0)) return it;
-  bool out = false;
-  if (a.budget_ns > 0) {
-    const unsigned long long now = global_ns();
-    unsigned long long t0 = atomicCAS(a.counter + 1, 0ull, now);
-    if (t0 == 0ull) t0 = now;
-    out = (long long)(now - t0) > (long long)a.budget_ns;
-  }
-  if (a.iter_budget > 0)
-    out = out || *reinterpret_cast<volatile unsigned long long*>(a.counter + 2) >=
-                     (unsigned long long)a.iter_budget;
-  return out ? (it | kItemTimedOut) : it;
 }
 
 // A point drained after the budget ran out: not iterated, V = NaN (one thread).
@@ -138,6 +120,31 @@ __device__ __forceinline__ void mark_timed_out(const SolveArgs<T>& a, int64_t it
   a.status[id] = HJ_POINT_TIMEOUT;
   a.iters[id] = 0;
   a.V[id] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// Draw the next item to solve (one thread of the group); an item >= B ends the
+// launch.  Once the launch's budget has run out, the drawing thread marks each
+// item it draws HJ_POINT_TIMEOUT and draws again, so the batch drains without
+// the solver loop seeing those items (each draw advances the counter: at most
+// B draws).
+template <typename T>
+__device__ __forceinline__ unsigned long long draw_item(const SolveArgs<T>& a) {
+  for (;;) {
+    const unsigned long long it = atomicAdd(a.counter, 1ull);
+    if (it >= (unsigned long long)a.B || (a.budget_ns <= 0 && a.iter_budget <= 0)) return it;
+    bool out = false;
+    if (a.budget_ns > 0) {
+      const unsigned long long now = global_ns();
+      unsigned long long t0 = atomicCAS(a.counter + 1, 0ull, now);
+      if (t0 == 0ull) t0 = now;
+      out = (long long)(now - t0) > (long long)a.budget_ns;
+    }
+    if (a.iter_budget > 0)
+      out = out || *reinterpret_cast<volatile unsigned long long*>(a.counter + 2) >=
+                       (unsigned long long)a.iter_budget;
+    if (!out) return it;
+    mark_timed_out(a, (int64_t)it);
+  }
 }
 
 // A finished point's iterations, for the iteration budget (one thread).
@@ -214,6 +221,100 @@ __device__ __forceinline__ U warp_sum(U v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
+}
+
+// The stopping test's accumulation over a point's warps with FP32 iterates: the
+// warps' FP32 sums added as a double-float (an unevaluated sum hi + lo of two
+// floats) by Knuth's error-free TwoSum, so the accumulated sum of up to 32
+// partials carries about 48 significant bits (relative error a small multiple of
+// 2^-48; an FP64 accumulation of the same partials has up to n 2^-53), while
+// every instruction runs on the FP32 pipe (an FP64
+// instruction holds this GPU's FP64 pipe for about 64 cycles per warp, active
+// lanes or not: the FP64 form measured 4 % of the 12-D quadcopter solve).
+struct SumF2 {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float b) {
+    const float s = hi + b;                 // TwoSum(hi, b) = s + e exactly
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (b - bb);
+    const float l = lo + e;
+    hi = s + l;                             // renormalise: |s| >= |l| (FastTwoSum)
+    lo = l - (hi - s);
+  }
+  __device__ __forceinline__ void add(const SumF2& o) {   // the same with a double-float
+    const float s = hi + o.hi;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (o.hi - bb);
+    const float l = (lo + o.lo) + e;
+    hi = s + l;
+    lo = l - (hi - s);
+  }
+  // hi + lo < th + tl, up to the rounding of the final difference (2^-48 relative)
+  __device__ __forceinline__ bool less(float th, float tl) const {
+    return (hi - th) + (lo - tl) < 0.f;
+  }
+  __device__ __forceinline__ bool finite() const { return isfinite(hi) && isfinite(lo); }
+};
+
+// Verdict of a stopping test from n <= 32 per-warp sums (red2[2 w], red2[2 w + 1]:
+// warp w's sums of the squared x and p increments), computed by every lane of
+// the calling warp: 1 converged (both below tol), 2 non-finite, 0 otherwise.
+// FP32: lane w takes warp w's sums and the warp adds them as double-floats by a
+// butterfly (TwoSum is exact and symmetric, so every lane ends with the same
+// total); FP64: the same butterfly in FP64.
+template <typename T>
+__device__ __forceinline__ int stop_verdict(const SolveArgs<T>& a, const T* red2, int n, int lane) {
+  if constexpr (sizeof(T) == 4) {
+    SumF2 x, p;
+    if (lane < n) { x.hi = red2[2 * lane]; p.hi = red2[2 * lane + 1]; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      SumF2 ox, op;
+      ox.hi = __shfl_xor_sync(kFull, x.hi, o); ox.lo = __shfl_xor_sync(kFull, x.lo, o);
+      op.hi = __shfl_xor_sync(kFull, p.hi, o); op.lo = __shfl_xor_sync(kFull, p.lo, o);
+      x.add(ox);
+      p.add(op);
+    }
+    if (!(x.finite() && p.finite())) return 2;
+    return (x.less(a.tol_hi, a.tol_lo) && p.less(a.tol_hi, a.tol_lo)) ? 1 : 0;
+  } else {
+    double x = lane < n ? red2[2 * lane] : 0.0, p = lane < n ? red2[2 * lane + 1] : 0.0;
+    x = warp_sum<double>(x);
+    p = warp_sum<double>(p);
+    if (!(isfinite(x) && isfinite(p))) return 2;
+    return (x < a.tol && p < a.tol) ? 1 : 0;
+  }
+}
+
+// The same for a compile-time number of warps G (every lane adds the G sums in order).
+template <int G, typename T>
+__device__ __forceinline__ int stop_verdict_g(const SolveArgs<T>& a, const T* red2) {
+  if constexpr (sizeof(T) == 4) {
+    SumF2 x, p;
+#pragma unroll
+    for (int w = 0; w < G; ++w) { x.add(red2[2 * w]); p.add(red2[2 * w + 1]); }
+    if (!(x.finite() && p.finite())) return 2;
+    return (x.less(a.tol_hi, a.tol_lo) && p.less(a.tol_hi, a.tol_lo)) ? 1 : 0;
+  } else {
+    double x = 0.0, p = 0.0;
+#pragma unroll
+    for (int w = 0; w < G; ++w) { x += red2[2 * w]; p += red2[2 * w + 1]; }
+    if (!(isfinite(x) && isfinite(p))) return 2;
+    return (x < a.tol && p < a.tol) ? 1 : 0;
+  }
+}
+
+// The same verdict for a point held by one warp (or half-warp): its own sums.
+template <typename T>
+__device__ __forceinline__ int stop_verdict1(const SolveArgs<T>& a, T x, T p) {
+  if (!(isfinite(x) && isfinite(p))) return 2;
+  if constexpr (sizeof(T) == 4) {
+    SumF2 sx, sp;
+    sx.hi = x; sp.hi = p;
+    return (sx.less(a.tol_hi, a.tol_lo) && sp.less(a.tol_hi, a.tol_lo)) ? 1 : 0;
+  } else {
+    return (x < a.tol && p < a.tol) ? 1 : 0;
+  }
 }
 
 template <typename T>
@@ -319,6 +420,11 @@ template <typename T>
 hj_status launch_eik_cta_solver(const SolveArgs<T>& a, cudaStream_t s);
 template <typename T>
 size_t eik_cta_smem_bytes(int d, int N);
+// The same with the state in registers (backward Euler, static bump, d <= 1024 in
+// FP32 with N <= 10 above d = 512 and N <= 16 below, d <= 512 and N <= 10 in
+// FP64); HJ_ERR_UNSUPPORTED elsewhere (the shared-memory kernel then runs).
+template <typename T>
+hj_status launch_eik_reg_solver(const SolveArgs<T>& a, cudaStream_t s);
 
 // Register-tiled FP32 tanh-drift kernel; HJ_ERR_UNSUPPORTED where it does not
 // apply (the shared-memory kernel then runs).  td_tile_group_warps: warps per

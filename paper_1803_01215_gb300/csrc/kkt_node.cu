@@ -4,7 +4,8 @@
 //
 // Thread (b, j), j = 1..N, loads x_j, x_{j-1}, p_j, p_{j+1} of point b from the
 // trajectories (a node's d values are contiguous, so consecutive threads read
-// consecutive blocks) and evaluates the family's FP64 node residual
+// consecutive blocks) and evaluates the family's node residual (in FP64, except
+// the quadcopter's for FP32 iterates, which is evaluated in FP32)
 // (families.cuh kkt_node: max_k |x_j - x_{j-1} - delta grad_p H(x_j, p_j)| and
 // |p_{j+1} - p_j + delta grad_x H(x_j, p_j)|; the thread of node 1 adds
 // |p_1 - grad g(x_0)|).  The lanes of a warp that hold nodes of the same point
@@ -16,6 +17,8 @@
 // equation is solved as psi = -phi with initial data -g, Section 6.1).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "families.cuh"
 #include "hj_internal.cuh"
 #include "problem.cuh"
@@ -24,7 +27,14 @@ namespace hj {
 
 namespace {
 
-// the FP64 residual of node j of point b (and, for j = 1, of x_0's equation)
+// whether the family evaluates its node residual in the iterate type (F::kKktInIterType)
+template <class F, class = void>
+struct kkt_in_iter_type : std::false_type {};
+template <class F>
+struct kkt_in_iter_type<F, std::void_t<decltype(F::kKktInIterType)>>
+    : std::integral_constant<bool, F::kKktInIterType> {};
+
+// the residual of node j of point b (and, for j = 1, of x_0's equation)
 template <typename T, class F, int D>
 __device__ __forceinline__ double node_residual(const SolveArgs<T>& a, const F& fam,
                                                      const T* __restrict__ X,
@@ -42,7 +52,9 @@ __device__ __forceinline__ double node_residual(const SolveArgs<T>& a, const F& 
       p[k] = T(sgn) * pb[(size_t)j * D + k];
       pr[k] = j < N ? T(sgn) * pb[(size_t)(j + 1) * D + k] : T(0);
     }
-    const double delta = a.t[b] / N;
+    // families that evaluate FP32 iterates in FP32 take delta = t / N in FP32
+    const double delta = (sizeof(T) == 4 && kkt_in_iter_type<F>::value)
+                             ? (double)((float)a.t[b] / (float)N) : a.t[b] / N;
     double r = fam.kkt_node(x, xl, p, pr, delta, (double)j * delta, j < N);
     if (j == 1) {                            // r2 = p_1 - grad g(x_0) (g with the cost sign)
 #pragma unroll

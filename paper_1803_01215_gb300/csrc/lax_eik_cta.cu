@@ -107,13 +107,8 @@ __global__ void __launch_bounds__(512) lax_eik_kernel(const SolveArgs<T> a, T* w
     __syncthreads();
     if (tid == 0) s_point = draw_item(a);
     __syncthreads();
-    const unsigned long long drawn = s_point;
-    const int64_t item = (int64_t)(drawn & ~kItemTimedOut);
+    const int64_t item = (int64_t)s_point;
     if (item >= a.B) break;
-    if (drawn & kItemTimedOut) {                  // the launch's budget ran out: drain
-      if (tid == 0) mark_timed_out(a, item);
-      continue;
-    }
     const PointRef<T> ref = point_ref(a, item);
     const int64_t b = ref.id;
     const int N = ref.N;
@@ -292,19 +287,14 @@ __global__ void __launch_bounds__(512) lax_eik_kernel(const SolveArgs<T> a, T* w
         }
       }
       if (chk) {
-        // each thread's partial (iterate type) reduced over its warp in that type,
-        // accumulated over the CTA's warps in FP64
+        // each thread's partial (iterate type) reduced over its warp in that type;
+        // the CTA's warp sums accumulated as double-floats (FP32 iterates: as
+        // accurate as FP64, on the FP32 pipe) or in FP64, and compared with tol
+        T* tsum = reinterpret_cast<T*>(tred);
         const T wx = warp_sum<T>(rx), wp = warp_sum<T>(rp);
-        if (lane == 0) { tred[2 * warp] = (double)wx; tred[2 * warp + 1] = (double)wp; }
+        if (lane == 0) { tsum[2 * warp] = wx; tsum[2 * warp + 1] = wp; }
         __syncthreads();
-        // one lane per warp accumulates the warps' sums in FP64 and compares
-        int verdict = 0;                                  // 1 converged, 2 non-finite
-        if (lane == 0) {
-          double tx = 0.0, tp = 0.0;
-          for (int w = 0; w < nwarps; ++w) { tx += tred[2 * w]; tp += tred[2 * w + 1]; }
-          verdict = !(isfinite(tx) && isfinite(tp)) ? 2 : (tx < a.tol && tp < a.tol) ? 1 : 0;
-        }
-        verdict = __shfl_sync(kFull, verdict, 0);
+        const int verdict = stop_verdict<T>(a, tsum, nwarps, lane);   // 1 converged, 2 non-finite
         if (verdict == 2) { st = HJ_POINT_NONFINITE; break; }
         if (verdict == 1) { st = HJ_POINT_CONVERGED; break; }
       }
@@ -395,6 +385,11 @@ hj_status launch_eik_cta_solver(const SolveArgs<T>& a, cudaStream_t s) {
   if (a.d < 1 || a.d > kMaxDEik || a.N < 1 || a.N > kMaxN) return HJ_ERR_UNSUPPORTED;
   if (a.xb == nullptr || a.inner_steps != 1 || a.formulation != HJ_FORM_LAX)
     return HJ_ERR_UNSUPPORTED;
+  // the state in registers when it fits (backward Euler, d <= 1024, N <= 16)
+  {
+    const hj_status r = launch_eik_reg_solver<T>(a, s);
+    if (r != HJ_ERR_UNSUPPORTED) return r;
+  }
   int dev = 0, nsm = 0, max_optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return HJ_ERR_CUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||

@@ -14,7 +14,7 @@
 //            gradient step x_j <- x_j - tau (p_j - p_{j+1}) + tau delta G_j, the
 //            over-relaxation z_j, and the g-prox of x_0.
 // The squared increments are reduced on test iterations only (over each warp in
-// the iterate type, over the warps in FP64).  CTAs
+// the iterate type, over the warps as double-floats or in FP64).  CTAs
 // draw points from a work counter (persistent grid).
 //
 // MIX = true runs the forward-Euler and trapezoid schemes (HJ_SCHEME_FE/TRAP),
@@ -116,13 +116,8 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
     __syncthreads();
     if (tid == 0) s_point = draw_item(a);
     __syncthreads();
-    const unsigned long long drawn = s_point;
-    const int64_t item = (int64_t)(drawn & ~kItemTimedOut);
+    const int64_t item = (int64_t)s_point;
     if (item >= a.B) break;
-    if (drawn & kItemTimedOut) {                  // the launch's budget ran out: drain
-      if (tid == 0) mark_timed_out(a, item);
-      continue;
-    }
     const PointRef<T> ref = point_ref(a, item);
     const int64_t b = ref.id;
     const int N = ref.N;
@@ -291,22 +286,17 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
         Z[e] = xn + th * (xn - xo);
         X[e] = xn;
       }
-      // each thread's partial (iterate type) reduced over its warp in that type,
-      // accumulated over the CTA's warps in FP64 and compared with tol in FP64
+      // each thread's partial (iterate type) reduced over its warp in that type;
+      // the CTA's warp sums accumulated as double-floats (FP32 iterates: as
+      // accurate as FP64, on the FP32 pipe) or in FP64, and compared with tol
+      T* tsum = reinterpret_cast<T*>(tred);
       if (chk) {
         const T wx = warp_sum<T>(rx), wp = warp_sum<T>(rp);
-        if (lane == 0) { tred[2 * warp] = (double)wx; tred[2 * warp + 1] = (double)wp; }
+        if (lane == 0) { tsum[2 * warp] = wx; tsum[2 * warp + 1] = wp; }
       }
       __syncthreads();
       if (chk) {
-        // one lane per warp accumulates the warps' sums in FP64 and compares
-        int verdict = 0;                                  // 1 converged, 2 non-finite
-        if (lane == 0) {
-          double sx = 0.0, sp = 0.0;
-          for (int w = 0; w < nwarps; ++w) { sx += tred[2 * w]; sp += tred[2 * w + 1]; }
-          verdict = !(isfinite(sx) && isfinite(sp)) ? 2 : (sx < a.tol && sp < a.tol) ? 1 : 0;
-        }
-        verdict = __shfl_sync(kFull, verdict, 0);
+        const int verdict = stop_verdict<T>(a, tsum, nwarps, lane);   // 1 converged, 2 non-finite
         if (verdict == 2) { st = HJ_POINT_NONFINITE; break; }
         if (verdict == 1) { st = HJ_POINT_CONVERGED; break; }
       }

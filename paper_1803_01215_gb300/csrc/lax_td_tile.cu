@@ -2,7 +2,9 @@
 // H = <p, tanh(A x)> + |p|^2/2 (Algorithm 1 with the Section 5.3 updates).
 //
 // A group of G warps solves one query point.  Each thread owns a fixed tile of
-// 4 coordinates x 8 time nodes and keeps that tile's x, p and z in registers
+// 4 coordinates x TJ time nodes (TJ = 8; 4 for d <= 32, where a point then fits
+// two warps and twice the warps fit an SM: 9 % faster at d = 32, while at
+// d = 100 the doubled group measured 25 % slower) and keeps that tile's x, p and z in registers
 // for the whole solve (thread t of the group: within each block of 4*TIc
 // threads, i-tile = u / 4 and j-tile = 4 * block + u % 4, so a quarter-warp
 // covers 2 i-tiles x 4 j-tiles and its 16-byte operand loads stay cheap).  Only
@@ -22,9 +24,10 @@
 //            the threads of the first node tile).
 // x_N stays pinned at the query point.  One group barrier after each phase
 // (__syncwarp when G = 1).  On test iterations each thread's squared
-// increments (its tile, FP32) are reduced over the warp in FP32, and one lane
-// per warp accumulates the group's warp sums in FP64 and compares with tol; the value's (coordinate, node) terms are FP32 and
-// their sum FP64.  Groups take points from the work
+// increments (its tile, FP32) are reduced over the warp in FP32, and the
+// group's warp sums are accumulated as double-floats (error-free TwoSum: as
+// accurate as FP64) and compared with tol; the value's (coordinate, node) terms
+// are FP32 and their sum FP64.  Groups take points from the work
 // counter (persistent grid); the CTA's groups share one copy of A and A^T.
 #include <cuda_runtime.h>
 
@@ -35,8 +38,8 @@ namespace hj {
 namespace {
 
 constexpr int kTI = 4;   // coordinates per tile
-constexpr int kTJ = 8;   // time nodes per tile
 
+template <int TJ>
 struct TileLayout {
   int d, dp, TIc, TJc, Ns;
   size_t head_bytes;     // per-group item slots, g-prox and Hopf node-1 constants
@@ -46,8 +49,8 @@ struct TileLayout {
     d = d_;
     dp = (d + 3) & ~3;
     TIc = dp / kTI;
-    TJc = (Nmax + kTJ - 1) / kTJ;
-    Ns = kTJ * TJc + 4;                              // row stride of Xs and Ws
+    TJc = (Nmax + TJ - 1) / TJ;
+    Ns = TJ * TJc + 4;                               // row stride of Xs and Ws
     head_bytes = (size_t)((M * 8 + 15) / 16) * 16 + 4 * (size_t)dp * sizeof(float);
     a_floats = 2 * (size_t)d * dp;
     grp_floats = 2 * (size_t)dp * Ns + 2 * (size_t)TJc * dp + 6 * (size_t)G;   // + 3G doubles
@@ -58,9 +61,9 @@ struct TileLayout {
   }
 };
 
-// warps a point needs: tiles laid out in blocks of 4 j-tiles
-__host__ __device__ inline int tile_slots(int d, int Nmax) {
-  const int TIc = ((d + 3) & ~3) / kTI, TJc = (Nmax + kTJ - 1) / kTJ;
+// threads a point needs: tiles laid out in blocks of 4 j-tiles
+__host__ __device__ inline int tile_slots(int d, int Nmax, int TJ) {
+  const int TIc = ((d + 3) & ~3) / kTI, TJc = (Nmax + TJ - 1) / TJ;
   return 4 * TIc * ((TJc + 3) / 4);
 }
 
@@ -73,44 +76,50 @@ __device__ __forceinline__ void group_barrier(int grp) {
   }
 }
 
-__device__ __forceinline__ void load8(const float* p, float (&v)[kTJ]) {
-  const float4 a = *reinterpret_cast<const float4*>(p);
-  const float4 b = *reinterpret_cast<const float4*>(p + 4);
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+template <int TJ>
+__device__ __forceinline__ void loadv(const float* p, float (&v)[TJ]) {
+#pragma unroll
+  for (int q = 0; q < TJ / 4; ++q) {
+    const float4 a = *reinterpret_cast<const float4*>(p + 4 * q);
+    v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+  }
 }
-__device__ __forceinline__ void store8(float* p, const float (&v)[kTJ]) {
-  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  *reinterpret_cast<float4*>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
+template <int TJ>
+__device__ __forceinline__ void storev(float* p, const float (&v)[TJ]) {
+#pragma unroll
+  for (int q = 0; q < TJ / 4; ++q)
+    *reinterpret_cast<float4*>(p + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
 // acc[r][c] = sum_k M[k][i0 + r] * S[k][c0 + c], k < d (M k-major with stride dp)
+template <int TJ>
 __device__ __forceinline__ void tile_product(const float* M, const float* S, int d, int dp,
                                              int Ns, int i0, int c0,
-                                             float (&acc)[kTI][kTJ]) {
+                                             float (&acc)[kTI][TJ]) {
 #pragma unroll
   for (int r = 0; r < kTI; ++r)
 #pragma unroll
-    for (int c = 0; c < kTJ; ++c) acc[r][c] = 0.f;
+    for (int c = 0; c < TJ; ++c) acc[r][c] = 0.f;
   const float* mp = M + i0;
   const float* sp = S + c0;
 #pragma unroll 2
   for (int k = 0; k < d; ++k) {
     const float4 a = *reinterpret_cast<const float4*>(mp + (size_t)k * dp);
-    float s[kTJ];
-    load8(sp + (size_t)k * Ns, s);
+    float s[TJ];
+    loadv<TJ>(sp + (size_t)k * Ns, s);
     const float av[kTI] = {a.x, a.y, a.z, a.w};
 #pragma unroll
     for (int r = 0; r < kTI; ++r)
 #pragma unroll
-      for (int c = 0; c < kTJ; ++c) acc[r][c] = fmaf(av[r], s[c], acc[r][c]);
+      for (int c = 0; c < TJ; ++c) acc[r][c] = fmaf(av[r], s[c], acc[r][c]);
   }
 }
 
-template <int G, bool TH1, bool HOPF>
+template <int TJ, int G, bool TH1, bool HOPF>
 __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float> a, int M) {
+  constexpr int kTJ = TJ;
   extern __shared__ __align__(16) unsigned char smem[];
-  const TileLayout L(a.d, a.N, G, M);
+  const TileLayout<TJ> L(a.d, a.N, G, M);
   const int d = L.d, dp = L.dp, Ns = L.Ns;
   unsigned long long* items = reinterpret_cast<unsigned long long*>(smem);
   float* goff = reinterpret_cast<float*>(smem + (size_t)((M * 8 + 15) / 16) * 16);
@@ -124,9 +133,10 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
   float* Ws = Xs + (size_t)dp * Ns;
   float* Zb = Ws + (size_t)dp * Ns;               // Zb[jt*dp + i]
   float* Pb = Zb + (size_t)L.TJc * dp;            // Pb[jt*dp + i]
-  // [2G] doubles (test sums) then [G] (value); Pb + TJc dp floats keeps 16-byte alignment
-  double* tred = reinterpret_cast<double*>(Pb + (size_t)L.TJc * dp);
-  double* vred = tred + 2 * G;
+  // [2G] floats (test sums, in the space of 2G doubles) then [G] doubles (value);
+  // Pb + TJc dp floats keeps 16-byte alignment
+  float* tred = Pb + (size_t)L.TJc * dp;
+  double* vred = reinterpret_cast<double*>(tred) + 2 * G;
 
   for (int e = threadIdx.x; e < d * dp; e += blockDim.x) {
     const int k = e / dp, i = e - k * dp;
@@ -149,20 +159,15 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
   const int u = t % blk, jg = t / blk;
   const int it = u >> 2, jt = 4 * jg + (u & 3);
   const bool tile_ok = it < L.TIc && jt < L.TJc;
-  const int i0 = it * kTI, c0 = jt * kTJ, j0 = 1 + c0;   // nodes j0..j0+7 <-> Xs columns c0..c0+7
+  const int i0 = it * kTI, c0 = jt * kTJ, j0 = 1 + c0;   // nodes j0..j0+TJ-1 <-> Xs columns c0..c0+TJ-1
   const float sig = a.sigma_t, tau = a.tau_t, th = a.theta_t;
 
   for (;;) {
     group_barrier<G>(grp);
     if (t == 0) items[grp] = draw_item(a);
     group_barrier<G>(grp);
-    const unsigned long long drawn = items[grp];
-    const int64_t item = (int64_t)(drawn & ~kItemTimedOut);
+    const int64_t item = (int64_t)items[grp];
     if (item >= a.B) break;
-    if (drawn & kItemTimedOut) {                  // the launch's budget ran out: drain
-      if (t == 0) mark_timed_out(a, item);
-      continue;
-    }
     const PointRef<float> ref = point_ref(a, item);
     const int64_t b = ref.id;
     const int N = ref.N;
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
     if (act) {
 #pragma unroll
       for (int r = 0; r < kTI; ++r) {
-        store8(Xs + (size_t)(i0 + r) * Ns + c0, x[r]);
+        storev<kTJ>(Xs + (size_t)(i0 + r) * Ns + c0, x[r]);
         Zb[jt * dp + i0 + r] = z[r][kTJ - 1];
       }
     }
@@ -223,7 +228,7 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
         float zL[kTI];
 #pragma unroll
         for (int r = 0; r < kTI; ++r) zL[r] = (jt == 0) ? z0[r] : Zb[(jt - 1) * dp + i0 + r];
-        tile_product(At, Xs, d, dp, Ns, i0, c0, acc);
+        tile_product<kTJ>(At, Xs, d, dp, Ns, i0, c0, acc);
 #pragma unroll
         for (int r = 0; r < kTI; ++r) {
           const bool row = i0 + r < d;
@@ -243,7 +248,7 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
               w[c] = (1.f - av * av) * pn;
             }
           }
-          store8(Ws + (size_t)(i0 + r) * Ns + c0, w);
+          storev<kTJ>(Ws + (size_t)(i0 + r) * Ns + c0, w);
           Pb[jt * dp + i0 + r] = p[r][0];
         }
       }
@@ -254,7 +259,7 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
 #pragma unroll
         for (int r = 0; r < kTI; ++r)
           pR[r] = (c0 + kTJ < N) ? Pb[(jt + 1) * dp + i0 + r] : 0.f;
-        tile_product(Am, Ws, d, dp, Ns, i0, c0, acc);
+        tile_product<kTJ>(Am, Ws, d, dp, Ns, i0, c0, acc);
 #pragma unroll
         for (int r = 0; r < kTI; ++r) {
           const int i = i0 + r;
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
               x0[r] = xn;
             }
           }
-          store8(Xs + (size_t)i * Ns + c0, x[r]);
+          storev<kTJ>(Xs + (size_t)i * Ns + c0, x[r]);
           Zb[jt * dp + i] = z[r][kTJ - 1];
         }
       }
@@ -296,26 +301,19 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
       float rx = 0.f, rp = 0.f;
       step(std::integral_constant<bool, true>{}, rx, rp);
       k_it += plain + 1;
-      // the threads' FP32 partials reduced over each warp in FP32; one lane per
-      // warp accumulates the group's warp sums in FP64 and compares with tol
+      // the threads' FP32 partials reduced over each warp in FP32; the group's
+      // warp sums accumulated as double-floats (as accurate as FP64, on the
+      // FP32 pipe) and compared with tol
       const float wx = warp_sum<float>(rx), wp = warp_sum<float>(rp);
+      int verdict;                                // 1 converged, 2 non-finite
       if constexpr (G > 1) {
-        if (lane == 0) { tred[2 * wig] = (double)wx; tred[2 * wig + 1] = (double)wp; }
+        if (lane == 0) { tred[2 * wig] = wx; tred[2 * wig + 1] = wp; }
         group_barrier<G>(grp);
+        verdict = stop_verdict_g<G, float>(a, tred);
+        group_barrier<G>(grp);                    // tred is free for the next test
+      } else {
+        verdict = stop_verdict1<float>(a, wx, wp);
       }
-      int verdict = 0;                            // 1 converged, 2 non-finite
-      if (lane == 0) {
-        double sx = 0.0, sp = 0.0;
-        if constexpr (G > 1) {
-#pragma unroll
-          for (int w = 0; w < G; ++w) { sx += tred[2 * w]; sp += tred[2 * w + 1]; }
-        } else {
-          sx = (double)wx; sp = (double)wp;
-        }
-        verdict = !(isfinite(sx) && isfinite(sp)) ? 2 : (sx < a.tol && sp < a.tol) ? 1 : 0;
-      }
-      verdict = __shfl_sync(kFull, verdict, 0);
-      if constexpr (G > 1) group_barrier<G>(grp); // tred is free for the next test
       if (verdict == 2) { st = HJ_POINT_NONFINITE; break; }
       if (verdict == 1) { st = HJ_POINT_CONVERGED; break; }
     }
@@ -325,7 +323,7 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
     double vacc = 0.0;
     if (act) {
       float acc[kTI][kTJ];
-      tile_product(At, Xs, d, dp, Ns, i0, c0, acc);
+      tile_product<kTJ>(At, Xs, d, dp, Ns, i0, c0, acc);
 #pragma unroll
       for (int r = 0; r < kTI; ++r) {
         const int i = i0 + r;
@@ -388,9 +386,9 @@ __global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float>
   }
 }
 
-template <int G, bool TH1, bool HOPF>
+template <int TJ, int G, bool TH1, bool HOPF>
 hj_status launch_g(const SolveArgs<float>& a, int M, size_t smem, cudaStream_t s) {
-  auto kern = lax_td_tile_kernel<G, TH1, HOPF>;
+  auto kern = lax_td_tile_kernel<TJ, G, TH1, HOPF>;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return HJ_ERR_CUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -410,13 +408,34 @@ hj_status launch_g(const SolveArgs<float>& a, int M, size_t smem, cudaStream_t s
   return cudaGetLastError() == cudaSuccess ? HJ_OK : HJ_ERR_CUDA;
 }
 
+template <int TJ, bool TH1, bool HOPF>
+hj_status launch_tj(const SolveArgs<float>& a, int G, int M, size_t smem, cudaStream_t s) {
+  if (G == 1) return launch_g<TJ, 1, TH1, HOPF>(a, M, smem, s);
+  if (G == 2) return launch_g<TJ, 2, TH1, HOPF>(a, M, smem, s);
+  if constexpr (TJ == 8) {           // four-node tiles are taken only for one or two warps
+    if (G == 4) return launch_g<TJ, 4, TH1, HOPF>(a, M, smem, s);
+    return launch_g<TJ, 8, TH1, HOPF>(a, M, smem, s);
+  }
+  return HJ_ERR_UNSUPPORTED;
+}
+
+int group_warps(int d, int N, int TJ) {
+  const int w = (tile_slots(d, N, TJ) + 31) / 32;
+  return w <= 1 ? 1 : w <= 2 ? 2 : w <= 4 ? 4 : w <= 8 ? 8 : 0;
+}
+
+// time nodes per tile: 4 where d <= 32 and a point still fits two warps, else 8
+int tile_nodes(int d, int N) {
+  const int g4 = group_warps(d, N, 4);
+  return (d <= 32 && g4 >= 1 && g4 <= 2) ? 4 : 8;
+}
+
 }  // namespace
 
 // Warps per point of the register-tiled kernel for (d, N), 0 when it does not apply.
 int td_tile_group_warps(int d, int N) {
   if (d < 1 || d > kMaxD || N < 1 || N > kMaxN) return 0;
-  const int w = (tile_slots(d, N) + 31) / 32;
-  return w <= 1 ? 1 : w <= 2 ? 2 : w <= 4 ? 4 : w <= 8 ? 8 : 0;
+  return group_warps(d, N, tile_nodes(d, N));
 }
 
 // Runs the register-tiled kernel when it applies (FP32, tanh drift, a point in
@@ -426,33 +445,30 @@ hj_status launch_td_tile_solver(const SolveArgs<float>& a, cudaStream_t s) {
   if (a.inner_steps != 1 || a.A == nullptr || a.At == nullptr) return HJ_ERR_UNSUPPORTED;
   const int G = td_tile_group_warps(a.d, a.N);
   if (G == 0) return HJ_ERR_UNSUPPORTED;
+  const int TJ = tile_nodes(a.d, a.N);
   int dev = 0, max_optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return HJ_ERR_CUDA;
   if (cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
       cudaSuccess)
     return HJ_ERR_CUDA;
+  auto bytes = [&](int m) {
+    return TJ == 4 ? TileLayout<4>(a.d, a.N, G, m).bytes(m) : TileLayout<8>(a.d, a.N, G, m).bytes(m);
+  };
   int M = G == 1 ? 4 : G == 2 ? 2 : 1;
-  size_t smem = TileLayout(a.d, a.N, G, M).bytes(M);
+  size_t smem = bytes(M);
   while (M > 1 && smem > (size_t)max_optin) {
     M /= 2;
-    smem = TileLayout(a.d, a.N, G, M).bytes(M);
+    smem = bytes(M);
   }
   if (smem > (size_t)max_optin) return HJ_ERR_UNSUPPORTED;
   const bool th1 = a.theta == 1.0;
-  if (a.formulation == HJ_FORM_HOPF) {
-    switch (G) {
-      case 1: return th1 ? launch_g<1, true, true>(a, M, smem, s) : launch_g<1, false, true>(a, M, smem, s);
-      case 2: return th1 ? launch_g<2, true, true>(a, M, smem, s) : launch_g<2, false, true>(a, M, smem, s);
-      case 4: return th1 ? launch_g<4, true, true>(a, M, smem, s) : launch_g<4, false, true>(a, M, smem, s);
-      default: return th1 ? launch_g<8, true, true>(a, M, smem, s) : launch_g<8, false, true>(a, M, smem, s);
-    }
+  const bool hopf = a.formulation == HJ_FORM_HOPF;
+  if (TJ == 4) {                     // d <= 32: G is 1 or 2
+    if (hopf) return th1 ? launch_tj<4, true, true>(a, G, M, smem, s) : launch_tj<4, false, true>(a, G, M, smem, s);
+    return th1 ? launch_tj<4, true, false>(a, G, M, smem, s) : launch_tj<4, false, false>(a, G, M, smem, s);
   }
-  switch (G) {
-    case 1: return th1 ? launch_g<1, true, false>(a, M, smem, s) : launch_g<1, false, false>(a, M, smem, s);
-    case 2: return th1 ? launch_g<2, true, false>(a, M, smem, s) : launch_g<2, false, false>(a, M, smem, s);
-    case 4: return th1 ? launch_g<4, true, false>(a, M, smem, s) : launch_g<4, false, false>(a, M, smem, s);
-    default: return th1 ? launch_g<8, true, false>(a, M, smem, s) : launch_g<8, false, false>(a, M, smem, s);
-  }
+  if (hopf) return th1 ? launch_tj<8, true, true>(a, G, M, smem, s) : launch_tj<8, false, true>(a, G, M, smem, s);
+  return th1 ? launch_tj<8, true, false>(a, G, M, smem, s) : launch_tj<8, false, false>(a, G, M, smem, s);
 }
 
 }  // namespace hj

@@ -137,6 +137,8 @@ hj::SolveArgs<T> make_args(const hj_problem_s* prob, int64_t B, int32_t N,
   hj::SolveArgs<T> a{};
   a.B = B; a.N = N; a.d = prob->d;
   a.sigma = o.sigma; a.tau = o.tau; a.theta = o.theta; a.tol = o.tol;
+  a.tol_hi = (float)o.tol;
+  a.tol_lo = (float)(o.tol - (double)a.tol_hi);
   a.sigma_t = T(o.sigma); a.tau_t = T(o.tau); a.theta_t = T(o.theta);
   a.max_iter = o.max_iter; a.check_every = o.check_every; a.inner_steps = o.inner_steps;
   a.seed = o.seed; a.radius = o.init_radius; a.point_offset = o.point_offset;

@@ -2,7 +2,8 @@
 // steps N, solved by one CUDA-graph launch.
 //
 // A plan sorts the points into buckets of (problem, N class) with N classes
-// 1-32, 33-64, 65-128, 129-256.  Each bucket runs one persistent kernel (the
+// 1-32, 33-64, 65-128, 129-256, each bucket's points ordered by decreasing N.
+// Each bucket runs one persistent kernel (the
 // register-resident kernel with the bucket's launch shape, or the shared-memory
 // kernel) that draws the bucket's point ids from its own work counter and
 // reads each point's N, xq offset and trajectory offset from device arrays the
@@ -167,6 +168,11 @@ hj_status hj_ragged_plan_create(hj_ragged_plan* out, int32_t n_prob, const hj_pr
     k.nmax = std::max(k.nmax, (int)N_of[b]);
     k.work += (double)N_of[b] * probs[prob_of[b]]->d;
   }
+  // within a bucket the kernel draws ids in order: longest N first, so the
+  // bucket's tail holds its shortest points
+  for (auto& k : p->buckets)
+    std::stable_sort(k.ids.begin(), k.ids.end(),
+                     [&](int32_t x, int32_t y) { return N_of[x] > N_of[y]; });
   std::sort(p->buckets.begin(), p->buckets.end(),
             [](const Bucket& x, const Bucket& y) { return x.work > y.work; });
   const bool f64 = opts->precision == HJ_PREC_FP64;

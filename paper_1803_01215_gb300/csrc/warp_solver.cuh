@@ -19,9 +19,9 @@
 //   x_j  <- x_j - tau (p_j - p_{j+1}) + tau delta grad_x H(x_j^k, p_j)      j = 1..N-1
 //   z_j  <- x_j^{k+1} + theta (x_j^{k+1} - x_j^k)
 // and, on test iterations, the squared increments: each lane's partial in the
-// iterate type, reduced over the warp by shuffles in that type, then on one
-// lane per warp accumulated over the group's warps in FP64 and compared with
-// tol in FP64.
+// iterate type, reduced over the warp by shuffles in that type, then
+// accumulated over the group's warps (FP32 iterates: as double-floats, as
+// accurate as FP64 on the FP32 pipe; FP64: in FP64) and compared with tol.
 //
 // MIX = true runs the forward-Euler and trapezoid schemes (HJ_SCHEME_FE/TRAP):
 // H on interval j is wR H(x_j, .) + wL H(x_{j-1}, .), so the dual step also
@@ -440,27 +440,17 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
     k_it += plain + 1;
     // each lane's partial (its own nodes, in the iterate type) reduced over the
     // warp by shuffles in that type (a 5-level tree: relative error <= 5 ulp);
-    // one lane per warp accumulates the group's warp sums in FP64, compares with
-    // tol in FP64 and hands the verdict to its warp (FP64 on one lane only: the
-    // FP64 pipe runs at 1/64 of the FP32 rate)
+    // the group's warp sums accumulated as double-floats (stop_verdict: as
+    // accurate as FP64, on the FP32 pipe) and compared with tol
     const T wx = lanes_sum<G, T>(rx), wp = lanes_sum<G, T>(rp);
+    int verdict;                                     // 1 converged, 2 non-finite
     if constexpr (G > 1) {
       if (lane == 0) { sh.red[wg][0] = wx; sh.red[wg][1] = wp; }
       __syncthreads();
+      verdict = stop_verdict_g<G, T>(a, &sh.red[0][0]);
+    } else {
+      verdict = stop_verdict1<T>(a, wx, wp);
     }
-    int verdict = 0;                                 // 1 converged, 2 non-finite
-    if (lane == 0) {
-      double sx = 0.0, sp = 0.0;
-      if constexpr (G > 1) {
-#pragma unroll
-        for (int w = 0; w < G; ++w) { sx += (double)sh.red[w][0]; sp += (double)sh.red[w][1]; }
-      } else {
-        sx = (double)wx; sp = (double)wp;
-      }
-      verdict = !(isfinite(sx) && isfinite(sp)) ? 2 : (sx < a.tol && sp < a.tol) ? 1 : 0;
-    }
-    if constexpr (G == 0) verdict = __shfl_sync(half_mask(), verdict, (int)(threadIdx.x & 16));
-    else verdict = __shfl_sync(kFull, verdict, 0);
     if (verdict == 2) { st = HJ_POINT_NONFINITE; break; }
     if (verdict == 1) { st = HJ_POINT_CONVERGED; break; }
     if constexpr (kValueTest) {
@@ -609,12 +599,8 @@ lax_warp_kernel(const SolveArgs<T> a) {
       __syncthreads();
       drawn = sh.item;
     }
-    const int64_t item = (int64_t)(drawn & ~kItemTimedOut);
+    const int64_t item = (int64_t)drawn;
     if (item >= a.B) break;
-    if (drawn & kItemTimedOut) {             // the launch's budget ran out: drain
-      if (lane == 0 && wg == 0) mark_timed_out(a, item);
-      continue;
-    }
     solve_point<T, F, D, NPL, G, TH1, HOPF, MIX>(a, fam, item, lane, wg, sh);
   }
 }

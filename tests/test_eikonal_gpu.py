@@ -19,9 +19,14 @@ from test_oracle_eikonal_pins import _ball_min
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# d = 2, 10: register kernel; d = 3, 100: coordinate-parallel kernel with the
-# state in shared memory; d = 2000: its state in the workspace (L2)
-SHAPES = [(2, 10), (2, 23), (10, 10), (3, 7), (100, 10), (2000, 10)]
+# d = 2, 10: the warp kernel.  Coordinate-parallel kernels: d = 3, 100 (N <= 10)
+# with the state in registers, one coordinate per thread (FP32 and FP64); d = 37,
+# N = 13: in registers in FP32 (up to 16 nodes), in shared memory in FP64; d = 700
+# (two coordinates per thread, ragged last warp): in registers in FP32, in shared
+# memory in FP64; d = 1100, N = 12: in shared memory in FP32, in the workspace in
+# FP64; d = 2000: in the workspace (L2) in both
+SHAPES = [(2, 10), (2, 23), (10, 10), (3, 7), (100, 10), (37, 13), (700, 10), (1100, 12),
+          (2000, 10)]
 
 
 def _w(d, sign, N, B, seed=51):
@@ -35,7 +40,7 @@ def _w(d, sign, N, B, seed=51):
 @pytest.mark.parametrize("sign", [1, -1])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_eikonal_fixed_iterations_elementwise(d, N, sign, precision):
-    B = 3 if d >= 1000 else 21
+    B = 3 if d >= 1000 else (9 if d >= 500 else 21)
     w = _w(d, sign, N, B)
     K = 150
     g = gpu(w, precision, tol=0.0, max_iter=K, check_every=K)
