@@ -82,7 +82,7 @@ __device__ __forceinline__ bool warp_reduce_scatter(T (&v)[M], int lane, T& out,
   return cnt >= 1;
 }
 
-template <typename T, int CPT, int NM>
+template <typename T, int CPT, int NM, bool EXACT>
 __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const SolveArgs<T> a) {
   __shared__ T red[kRegMaxWarps][2 * NM];        // per-warp node sums: |x_j - x_b|^2, |v_j|^2
   __shared__ T keep_s[NM + 1], coef_s[NM + 1];
@@ -115,8 +115,9 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
     if (item >= a.B) break;
     const PointRef<T> ref = point_ref(a, item);
     const int64_t b = ref.id;
-    const int N = ref.N;
-    if (N < 1 || N > NM) {                        // the host never routes such a point here
+    // EXACT: every point has N = NM (a uniform batch), so the node guards fold away
+    const int N = EXACT ? NM : ref.N;
+    if (ref.N != N || N < 1 || N > NM) {          // the host never routes such a point here
       if (tid == 0) { a.status[b] = HJ_POINT_INVALID; a.iters[b] = 0; a.V[b] = 0.0; }
       continue;
     }
@@ -172,12 +173,9 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
       if (warp_reduce_scatter<T, 2 * NM>(s, lane, tot, idx)) red[warp][idx] = tot;
     };
 
-    int k_it = 0;
-    int8_t st = HJ_POINT_MAX_ITER;
-    node_sums(true);                              // the first iteration's node scalars
-    while (k_it < a.max_iter) {
-      ++k_it;
-      const bool chk = (k_it % a.check_every == 0) || (k_it == a.max_iter);
+    // one iteration; CHK adds the squared increments (test iterations only)
+    auto step = [&](auto chk_tag, T& rx, T& rp) {
+      constexpr bool CHK = decltype(chk_tag)::value;
       __syncthreads();                            // red complete
       if (tid < N) {                              // node j = tid + 1: shrink and x-step coefficient
         const int j = tid + 1;
@@ -189,7 +187,6 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
         coef_s[j] = taud * ((n > thr) ? n - thr : T(0)) * (T(-2) * c1 * c2 * e);
       }
       __syncthreads();                            // keep, coef ready; red free
-      T rx = T(0), rp = T(0);
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
         // dual step of every node with the old z
@@ -197,7 +194,7 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
         for (int j = NM; j >= 1; --j) {
           if (j <= N) {
             const T pn = keep_s[j] * (p[c][j] + sig * (z[c][j] - z[c][j - 1]));
-            if (chk) { const T df = pn - p[c][j]; rp += df * df; }
+            if constexpr (CHK) { const T df = pn - p[c][j]; rp += df * df; }
             p[c][j] = pn;
           }
         }
@@ -205,7 +202,7 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
         {
           const T xo = x[c][0];
           const T xn = (xo + tau * p[c][1] + goff[c]) * ginv[c];
-          if (chk) { const T df = xn - xo; rx += df * df; }
+          if constexpr (CHK) { const T df = xn - xo; rx += df * df; }
           z[c][0] = xn + th * (xn - xo);
           x[c][0] = xn;
         }
@@ -214,21 +211,34 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
           if (j < N) {
             const T xo = x[c][j];
             const T xn = xo - tau * (p[c][j] - p[c][j + 1]) + coef_s[j] * (xo - xbk[c]);
-            if (chk) { const T df = xn - xo; rx += df * df; }
+            if constexpr (CHK) { const T df = xn - xo; rx += df * df; }
             z[c][j] = xn + th * (xn - xo);
             x[c][j] = xn;
           }
         }
       }
       node_sums(true);                            // the next iteration's node scalars
-      if (chk) {
-        const T wx = warp_sum<T>(rx), wp = warp_sum<T>(rp);
-        if (lane == 0) { tred[warp][0] = wx; tred[warp][1] = wp; }
-        __syncthreads();
-        const int verdict = stop_verdict<T>(a, &tred[0][0], nwarps, lane);   // 1 converged, 2 non-finite
-        if (verdict == 2) { st = HJ_POINT_NONFINITE; break; }
-        if (verdict == 1) { st = HJ_POINT_CONVERGED; break; }
-      }
+    };
+
+    int k_it = 0;
+    int8_t st = HJ_POINT_MAX_ITER;
+    node_sums(true);                              // the first iteration's node scalars
+    const int max_iter = a.max_iter, check_every = a.check_every;
+    while (k_it < max_iter) {
+      // check_every - 1 plain iterations (fewer before max_iter), then a test
+      const int left = max_iter - k_it;
+      const int plain = (check_every - 1 < left - 1) ? check_every - 1 : left - 1;
+      T dx = T(0), dp = T(0);
+      for (int r = 0; r < plain; ++r) step(std::integral_constant<bool, false>{}, dx, dp);
+      T rx = T(0), rp = T(0);
+      step(std::integral_constant<bool, true>{}, rx, rp);
+      k_it += plain + 1;
+      const T wx = warp_sum<T>(rx), wp = warp_sum<T>(rp);
+      if (lane == 0) { tred[warp][0] = wx; tred[warp][1] = wp; }
+      __syncthreads();
+      const int verdict = stop_verdict<T>(a, &tred[0][0], nwarps, lane);   // 1 converged, 2 non-finite
+      if (verdict == 2) { st = HJ_POINT_NONFINITE; break; }
+      if (verdict == 1) { st = HJ_POINT_CONVERGED; break; }
     }
 
     // ---- value: g(x_0) + sum_j <p_j, x_j - x_{j-1}> - delta sum_j c(x_j) |p_j|
@@ -286,7 +296,9 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
 
 template <typename T, int CPT, int NM>
 hj_status launch_reg(const SolveArgs<T>& a, int threads, cudaStream_t s) {
-  auto kern = lax_eik_reg_kernel<T, CPT, NM>;
+  // a uniform batch with N = NM takes the instantiation without node guards
+  const bool exact = a.Nv == nullptr && a.N == NM;
+  auto kern = exact ? lax_eik_reg_kernel<T, CPT, NM, true> : lax_eik_reg_kernel<T, CPT, NM, false>;
   int dev = 0, nsm = 0, bps = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
