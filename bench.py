@@ -52,8 +52,9 @@ def eikonal_flops_per_node_iter(d):
 FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the timed FP32
 # kernel (lax_warp_kernel<float, FamQuadcopter, 12, 1, 2>) from the ncu capture
-# of that kernel; None whenever the kernel has changed since the capture.
-QC_TRAFFIC_BYTES = None
+# of that kernel (475 392 read, 0 written: V, iters and status stay in L2 within
+# the launch); None whenever the kernel has changed since the capture.
+QC_TRAFFIC_BYTES = 475392
 
 
 def workload_config():
@@ -168,8 +169,8 @@ def measure_other_configs(dev, flush, stream, peak, only=None):
     import torch
     from paper_1803_01215_gb300 import binding
     out = {}
-    rows = None if not only else set(only.split(","))
-    want = lambda name: rows is None or name in rows      # noqa: E731
+    only_rows = None if not only else set(only.split(","))
+    want = lambda name: only_rows is None or name in only_rows      # noqa: E731
 
     def run_uniform(w, precision, tag, npts=None, formulation="lax", tune=False, scheme="be",
                     tol=None):
@@ -396,7 +397,7 @@ def measure_other_configs(dev, flush, stream, peak, only=None):
         # sits from the 12-D config's H without it: the same 4096 points solved in
         # FP64 at smaller eps; converged fraction within the iteration cap, and the
         # change of V against eps = 1 on the points converged at both.
-        rows, v1 = {}, None
+        eps_rows, v1 = {}, None
         for eps in (1.0, 0.3, 0.1):
             we = W.quadcopter()
             we["dyn"] = np.array(we["dyn"], dtype=float)
@@ -415,8 +416,8 @@ def measure_other_configs(dev, flush, stream, peak, only=None):
                            median_abs_dV_vs_eps1=float(np.median(dv)) if both.any() else None,
                            median_rel_dV_vs_eps1=float(np.median(dv / np.maximum(1.0, np.abs(v1[0][both]))))
                            if both.any() else None)
-            rows[f"eps{eps}"] = row
-        out["eps_departure_quadcopter12d_B4096_N64_fp64"] = rows
+            eps_rows[f"eps{eps}"] = row
+        out["eps_departure_quadcopter12d_B4096_N64_fp64"] = eps_rows
 
     if want("ragged"):
         rw = W.ragged_mix()
@@ -682,7 +683,9 @@ def main():
     value = n_ok32 / (ms32 * 1e-3)
     value64 = n_ok64 / (ms64 * 1e-3)
     flops = iters_sum / world * N * QC_FLOPS_PER_NODE_ITER           # per launch, per rank
-    achieved_tflops = flops / (ms32 * 1e-3) / 1e12
+    # the solver kernel's own duration: the step without the certificate (the
+    # solver launch and a 24-byte counter memset)
+    achieved_tflops = flops / (ms32_plain * 1e-3) / 1e12
     clocks = _clock_summary(clocks_path, local)
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
@@ -732,8 +735,12 @@ def main():
                      "peak_measured": fma_peak, "frac_of_measured": achieved_tflops / fma_peak,
                      "peak_measured_basis": "hj_probe_fp32_fma: 8 independent fmaf chains per "
                                             "thread, 8 CTAs x 256 threads per SM, ~50 ms",
-                     "packed_fma_chain_tflops": fma2_peak},
-        "gpu_launches": args.steps,
+                     "packed_fma_chain_tflops": fma2_peak,
+                     "duration_ms": ms32_plain,
+                     "duration_basis": "CUDA events around the solver launch alone (the step "
+                                       "without the residual certificate), same stream"},
+        # per timed step: the solver kernel, and the residual kernel when requested
+        "gpu_launches": args.steps * (2 if kkt32 is not None else 1),
         "e2e": {"value": n_ok32 / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(xq_h.numel() * 8 + t_h.numel() * 8),
                 "d2h_bytes_per_step": int(V_h.numel() * 8 + st_h.numel()

@@ -102,11 +102,13 @@ __device__ __forceinline__ void tile_product(const float* M, const float* S, int
     for (int c = 0; c < TJ; ++c) acc[r][c] = 0.f;
   const float* mp = M + i0;
   const float* sp = S + c0;
-#pragma unroll 2
+#pragma unroll 4
   for (int k = 0; k < d; ++k) {
-    const float4 a = *reinterpret_cast<const float4*>(mp + (size_t)k * dp);
+    const float4 a = *reinterpret_cast<const float4*>(mp);
     float s[TJ];
-    loadv<TJ>(sp + (size_t)k * Ns, s);
+    loadv<TJ>(sp, s);
+    mp += dp;
+    sp += Ns;
     const float av[kTI] = {a.x, a.y, a.z, a.w};
 #pragma unroll
     for (int r = 0; r < kTI; ++r)

@@ -9,8 +9,8 @@ kernel did solve must equal the unbudgeted solve of that point exactly (the
 budget only decides which points are drawn for solving).  The batches are
 larger than one wave of the persistent grid, so that points are still drawn
 after the first ones finish; every kernel family takes part: the register-resident kernel, the tiled and the
-shared-memory tanh-drift kernels, the coordinate-parallel eikonal kernel, and a
-ragged plan.  Nothing here waits on the device beyond an ordinary
+shared-memory tanh-drift kernels, the coordinate-parallel eikonal kernel (one
+CTA, and a cluster of two CTAs per point), and a ragged plan.  Nothing here waits on the device beyond an ordinary
 synchronisation; no kernel spins.
 """
 import numpy as np
@@ -44,6 +44,7 @@ CASES = [
     ("tanh_d32_tiled", lambda: W.tanh_drift(32, B=2048, seed=82), "fp32"),
     ("tanh_d32_shared", lambda: W.tanh_drift(32, B=1024, seed=83), "fp64"),
     ("eikonal_d37", lambda: W.eikonal(d=37, sign=1, t=0.2, B=8192, seed=84), "fp32"),
+    ("eikonal_d1500_cluster", lambda: W.eikonal(d=1500, sign=1, t=0.2, B=400, seed=87), "fp32"),
 ]
 
 

@@ -24,9 +24,10 @@ pytestmark = pytest.mark.gpu
 # N = 13: in registers in FP32 (up to 16 nodes), in shared memory in FP64; d = 700
 # (two coordinates per thread, ragged last warp): in registers in FP32, in shared
 # memory in FP64; d = 1100, N = 12: in shared memory in FP32, in the workspace in
-# FP64; d = 2000: in the workspace (L2) in both
+# FP64; d = 1300 (N = 7) and 2000: in registers on a cluster of two CTAs in
+# FP32 (each CTA half of the coordinates), in the workspace (L2) in FP64
 SHAPES = [(2, 10), (2, 23), (10, 10), (3, 7), (100, 10), (37, 13), (700, 10), (1100, 12),
-          (2000, 10)]
+          (1300, 7), (2000, 10)]
 
 
 def _w(d, sign, N, B, seed=51):
