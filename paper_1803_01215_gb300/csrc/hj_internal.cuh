@@ -263,10 +263,19 @@ struct SumF2 {
 // butterfly (TwoSum is exact and symmetric, so every lane ends with the same
 // total); FP64: the same butterfly in FP64.
 template <typename T>
+__device__ __forceinline__ int stop_verdict_lanes(const SolveArgs<T>& a, T vx, T vp);
+
+template <typename T>
 __device__ __forceinline__ int stop_verdict(const SolveArgs<T>& a, const T* red2, int n, int lane) {
+  return stop_verdict_lanes<T>(a, lane < n ? red2[2 * lane] : T(0), lane < n ? red2[2 * lane + 1] : T(0));
+}
+
+// The same with each lane holding one warp's pair of sums (zeros past the last).
+template <typename T>
+__device__ __forceinline__ int stop_verdict_lanes(const SolveArgs<T>& a, T vx, T vp) {
   if constexpr (sizeof(T) == 4) {
     SumF2 x, p;
-    if (lane < n) { x.hi = red2[2 * lane]; p.hi = red2[2 * lane + 1]; }
+    x.hi = vx; p.hi = vp;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       SumF2 ox, op;
@@ -278,7 +287,7 @@ __device__ __forceinline__ int stop_verdict(const SolveArgs<T>& a, const T* red2
     if (!(x.finite() && p.finite())) return 2;
     return (x.less(a.tol_hi, a.tol_lo) && p.less(a.tol_hi, a.tol_lo)) ? 1 : 0;
   } else {
-    double x = lane < n ? red2[2 * lane] : 0.0, p = lane < n ? red2[2 * lane + 1] : 0.0;
+    double x = vx, p = vp;
     x = warp_sum<double>(x);
     p = warp_sum<double>(p);
     if (!(isfinite(x) && isfinite(p))) return 2;

@@ -25,9 +25,12 @@
 // as double-floats (FP32 iterates: as accurate as FP64, on the FP32 pipe) or in
 // FP64 (stop_verdict).  The negative equation (cost_sign = -1) runs the
 // positive one with -g and returns -V and -p, as in Section 6.1.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "hj_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hj {
 
@@ -82,9 +85,22 @@ __device__ __forceinline__ bool warp_reduce_scatter(T (&v)[M], int lane, T& out,
   return cnt >= 1;
 }
 
-template <typename T, int CPT, int NM, bool EXACT>
+// barrier of the CTA, or of the cluster (with release / acquire of shared memory)
+template <int CL>
+__device__ __forceinline__ void csync() {
+  if constexpr (CL > 1) cg::this_cluster().sync();
+  else __syncthreads();
+}
+
+// CL = 2: a cluster of two CTAs solves each point, CTA r owning the coordinates
+// r T CPT + (t + c T); every barrier of the iteration is then a cluster
+// barrier, the node sums are double-buffered (the other CTA reads them through
+// distributed shared memory while this one fills the next buffer), and both
+// CTAs form the node scalars from both CTAs' sums.
+template <typename T, int CPT, int NM, bool EXACT, int CL>
 __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const SolveArgs<T> a) {
-  __shared__ T red[kRegMaxWarps][2 * NM];        // per-warp node sums: |x_j - x_b|^2, |v_j|^2
+  constexpr int NB = CL > 1 ? 2 : 1;
+  __shared__ T red[NB][kRegMaxWarps][2 * NM];    // per-warp node sums: |x_j - x_b|^2, |v_j|^2
   __shared__ T keep_s[NM + 1], coef_s[NM + 1];
   __shared__ T tred[kRegMaxWarps][2];              // per-warp stopping sums
   __shared__ double vred[kRegMaxWarps];
@@ -92,14 +108,28 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
   const int d = a.d;
   const int T_ = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = T_ >> 5;
+  unsigned rank = 0;
+  const T* peer_red = nullptr;                     // the other CTA's red, tred, vred, s_point
+  const T* peer_tred = nullptr;
+  const double* peer_vred = nullptr;
+  const unsigned long long* peer_point = nullptr;
+  if constexpr (CL > 1) {
+    cg::cluster_group cl = cg::this_cluster();
+    rank = cl.block_rank();
+    peer_red = cl.map_shared_rank(&red[0][0][0], rank ^ 1u);
+    peer_tred = cl.map_shared_rank(&tred[0][0], rank ^ 1u);
+    peer_vred = cl.map_shared_rank(&vred[0], rank ^ 1u);
+    peer_point = cl.map_shared_rank(&s_point, 0u);
+  }
   const T sig = a.sigma_t, tau = a.tau_t, th = a.theta_t;
   const T c0 = T(a.eik_c0), c1 = T(a.eik_c1), c2 = T(a.eik_c2);
+  const int kbase = (int)rank * T_ * CPT;          // first coordinate of this CTA's span
   // the thread's coordinates: bump centre and the g-prox (with the cost sign)
   bool own[CPT];
   T xbk[CPT], goff[CPT], ginv[CPT];
 #pragma unroll
   for (int c = 0; c < CPT; ++c) {
-    const int k = tid + c * T_;
+    const int k = kbase + tid + c * T_;
     own[c] = k < d;
     const double w2 = own[c] ? a.cost_sign * a.W2[k] : 0.0, cc = own[c] ? a.c[k] : 0.0;
     xbk[c] = own[c] ? a.xb[k] : T(0);
@@ -108,17 +138,17 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
   }
 
   for (;;) {
-    __syncthreads();
-    if (tid == 0) s_point = draw_item(a);
-    __syncthreads();
-    const int64_t item = (int64_t)s_point;
+    csync<CL>();                                  // the previous point is done in every CTA
+    if (tid == 0 && rank == 0) s_point = draw_item(a);
+    csync<CL>();
+    const int64_t item = (int64_t)(CL > 1 ? *peer_point : s_point);
     if (item >= a.B) break;
     const PointRef<T> ref = point_ref(a, item);
     const int64_t b = ref.id;
     // EXACT: every point has N = NM (a uniform batch), so the node guards fold away
     const int N = EXACT ? NM : ref.N;
     if (ref.N != N || N < 1 || N > NM) {          // the host never routes such a point here
-      if (tid == 0) { a.status[b] = HJ_POINT_INVALID; a.iters[b] = 0; a.V[b] = 0.0; }
+      if (tid == 0 && rank == 0) { a.status[b] = HJ_POINT_INVALID; a.iters[b] = 0; a.V[b] = 0.0; }
       continue;
     }
     const T delta_t = T(a.t[b]) / T(N);
@@ -131,7 +161,7 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
       const InitGuess<T> ig(a.radius);
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
-        const int k = tid + c * T_;
+        const int k = kbase + tid + c * T_;
         const double xq = own[c] ? ref.xq[k] : 0.0;
 #pragma unroll
         for (int j = 0; j <= NM; ++j) {
@@ -150,9 +180,24 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
       }
     }
 
+    int buf = 0;                                  // red buffer being filled (CL = 2)
+    // node j's two sums over every warp of the point; for CL = 2 both CTAs add
+    // CTA 0's warps, then CTA 1's, so they form bitwise the same node scalars
+    auto node_total = [&](int j, T& r2, T& n2) {
+      const T* own_b = &red[buf][0][0];
+      if constexpr (CL > 1) {
+        const T* peer_b = peer_red + (size_t)buf * kRegMaxWarps * 2 * NM;
+        const T* r0 = rank == 0 ? own_b : peer_b;
+        const T* r1 = rank == 0 ? peer_b : own_b;
+        for (int w = 0; w < nwarps; ++w) { r2 += r0[w * 2 * NM + 2 * (j - 1)]; n2 += r0[w * 2 * NM + 2 * (j - 1) + 1]; }
+        for (int w = 0; w < nwarps; ++w) { r2 += r1[w * 2 * NM + 2 * (j - 1)]; n2 += r1[w * 2 * NM + 2 * (j - 1) + 1]; }
+      } else {
+        for (int w = 0; w < nwarps; ++w) { r2 += own_b[w * 2 * NM + 2 * (j - 1)]; n2 += own_b[w * 2 * NM + 2 * (j - 1) + 1]; }
+      }
+    };
     // this thread's parts of the 2N node scalars at the current iterate
     // (dual = true: |v_j|^2 with v_j = p_j + sigma (z_j - z_{j-1}); else |p_j|^2),
-    // summed over the warp and parked in red[warp]
+    // summed over the warp and parked in red[buf][warp]
     auto node_sums = [&](bool dual) {
       T s[2 * NM];
 #pragma unroll
@@ -170,23 +215,24 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
       }
       T tot;
       int idx;
-      if (warp_reduce_scatter<T, 2 * NM>(s, lane, tot, idx)) red[warp][idx] = tot;
+      if (warp_reduce_scatter<T, 2 * NM>(s, lane, tot, idx)) red[buf][warp][idx] = tot;
     };
 
     // one iteration; CHK adds the squared increments (test iterations only)
     auto step = [&](auto chk_tag, T& rx, T& rp) {
       constexpr bool CHK = decltype(chk_tag)::value;
-      __syncthreads();                            // red complete
+      csync<CL>();                                // red[buf] complete (in every CTA)
       if (tid < N) {                              // node j = tid + 1: shrink and x-step coefficient
         const int j = tid + 1;
         T r2 = T(0), n2 = T(0);
-        for (int w = 0; w < nwarps; ++w) { r2 += red[w][2 * (j - 1)]; n2 += red[w][2 * (j - 1) + 1]; }
+        node_total(j, r2, n2);
         const T e = expr<T>(-c2 * r2);
         const T n = sqrtr<T>(n2), thr = lam * (c0 + c1 * e);
         keep_s[j] = (n > thr) ? (n - thr) / n : T(0);
         coef_s[j] = taud * ((n > thr) ? n - thr : T(0)) * (T(-2) * c1 * c2 * e);
       }
-      __syncthreads();                            // keep, coef ready; red free
+      __syncthreads();                            // keep, coef ready; red free (CL = 1)
+      if constexpr (CL > 1) buf ^= 1;             // the next sums go to the other buffer
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
         // dual step of every node with the old z
@@ -235,21 +281,33 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
       k_it += plain + 1;
       const T wx = warp_sum<T>(rx), wp = warp_sum<T>(rp);
       if (lane == 0) { tred[warp][0] = wx; tred[warp][1] = wp; }
-      __syncthreads();
-      const int verdict = stop_verdict<T>(a, &tred[0][0], nwarps, lane);   // 1 converged, 2 non-finite
+      csync<CL>();
+      // lane w < nwarps: CTA 0's warp w, then CTA 1's warps (CL = 2), the same
+      // inputs in the same order in both CTAs, so both take the same verdict
+      T vx = T(0), vp = T(0);
+      {
+        const T* t0 = (CL > 1 && rank != 0) ? peer_tred : &tred[0][0];
+        const T* t1 = (CL > 1 && rank == 0) ? peer_tred : &tred[0][0];
+        if (lane < nwarps) {
+          vx = t0[2 * lane]; vp = t0[2 * lane + 1];
+        } else if (CL > 1 && lane < 2 * nwarps) {
+          vx = t1[2 * (lane - nwarps)]; vp = t1[2 * (lane - nwarps) + 1];
+        }
+      }
+      const int verdict = stop_verdict_lanes<T>(a, vx, vp);   // 1 converged, 2 non-finite
       if (verdict == 2) { st = HJ_POINT_NONFINITE; break; }
       if (verdict == 1) { st = HJ_POINT_CONVERGED; break; }
     }
 
     // ---- value: g(x_0) + sum_j <p_j, x_j - x_{j-1}> - delta sum_j c(x_j) |p_j|
     // (the positive equation's; times cost_sign), node terms in T, sums in FP64
-    __syncthreads();                              // every read of red is done
+    csync<CL>();                                  // every read of red is done (every CTA)
     node_sums(false);
     double acc = 0.0;
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       if (own[c]) {
-        const int k = tid + c * T_;
+        const int k = kbase + tid + c * T_;
         const double w2 = a.cost_sign * a.W2[k];
         const double e0 = (double)x[c][0] - a.c[k];
         acc += 0.5 * w2 * e0 * e0;
@@ -260,19 +318,21 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
         acc += (double)s;
       }
     }
-    __syncthreads();
-    if (tid < N) {
+    csync<CL>();
+    if (tid < N && rank == 0) {                   // the node terms, once per point
       const int j = tid + 1;
       T r2 = T(0), n2 = T(0);
-      for (int w = 0; w < nwarps; ++w) { r2 += red[w][2 * (j - 1)]; n2 += red[w][2 * (j - 1) + 1]; }
+      node_total(j, r2, n2);
       acc -= (double)(delta_t * (c0 + c1 * expr<T>(-c2 * r2)) * sqrtr<T>(n2));
     }
     acc = warp_sum<double>(acc);
     if (lane == 0) vred[warp] = acc;
-    __syncthreads();
-    if (tid == 0) {
+    csync<CL>();
+    if (tid == 0 && rank == 0) {
       double v = 0.0;
       for (int w = 0; w < nwarps; ++w) v += vred[w];
+      if constexpr (CL > 1)
+        for (int w = 0; w < nwarps; ++w) v += peer_vred[w];
       a.V[b] = a.cost_sign * v;
       a.iters[b] = k_it;
       a.status[b] = st;
@@ -282,7 +342,7 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       if (!own[c]) continue;
-      const int k = tid + c * T_;
+      const int k = kbase + tid + c * T_;
 #pragma unroll
       for (int j = 0; j <= NM; ++j) {
         if (j <= N) {
@@ -292,44 +352,78 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
       }
     }
   }
+  // no CTA of a cluster leaves while the other may still read its shared memory
+  if constexpr (CL > 1) csync<CL>();
 }
 
-template <typename T, int CPT, int NM>
+template <typename T, int CPT, int NM, int CL>
 hj_status launch_reg(const SolveArgs<T>& a, int threads, cudaStream_t s) {
   // a uniform batch with N = NM takes the instantiation without node guards
   const bool exact = a.Nv == nullptr && a.N == NM;
-  auto kern = exact ? lax_eik_reg_kernel<T, CPT, NM, true> : lax_eik_reg_kernel<T, CPT, NM, false>;
-  int dev = 0, nsm = 0, bps = 0;
+  auto kern = exact ? lax_eik_reg_kernel<T, CPT, NM, true, CL>
+                    : lax_eik_reg_kernel<T, CPT, NM, false, CL>;
+  int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return HJ_ERR_CUDA;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, threads, 0) != cudaSuccess)
-    return HJ_ERR_CUDA;
-  if (bps < 1) return HJ_ERR_UNSUPPORTED;
-  int64_t grid = (int64_t)bps * nsm;
-  if (a.B < grid) grid = a.B;
-  kern<<<(int)grid, threads, 0, s>>>(a);
-  return cudaGetLastError() == cudaSuccess ? HJ_OK : HJ_ERR_CUDA;
+  if constexpr (CL == 1) {
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, threads, 0) != cudaSuccess)
+      return HJ_ERR_CUDA;
+    if (bps < 1) return HJ_ERR_UNSUPPORTED;
+    int64_t grid = (int64_t)bps * nsm;
+    if (a.B < grid) grid = a.B;
+    kern<<<(int)grid, threads, 0, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? HJ_OK : HJ_ERR_CUDA;
+  } else {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nsm / CL * CL));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;                           // clusters resident at once: the persistent grid
+    if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess) return HJ_ERR_CUDA;
+    if (clusters < 1) return HJ_ERR_UNSUPPORTED;
+    int64_t nc = clusters;
+    if (a.B < nc) nc = a.B;
+    cfg.gridDim = dim3((unsigned)(nc * CL));
+    if (cudaLaunchKernelEx(&cfg, kern, a) != cudaSuccess) return HJ_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? HJ_OK : HJ_ERR_CUDA;
+  }
 }
 
 }  // namespace
 
 // Runs the register-resident eikonal kernel when it applies (static bump,
-// backward Euler, d <= 1024, N <= 16); HJ_ERR_UNSUPPORTED otherwise, and the
-// caller takes the shared-memory kernel.
+// backward Euler; FP32: d <= 512 with N <= 16, d <= 1024 with N <= 10 and, on a
+// cluster of two CTAs, d <= 2048 with N <= 10; FP64: d <= 512 with N <= 10);
+// HJ_ERR_UNSUPPORTED otherwise, and the caller takes the shared-memory kernel.
 template <typename T>
 hj_status launch_eik_reg_solver(const SolveArgs<T>& a, cudaStream_t s) {
   if (a.eik_moving || a.scheme != HJ_SCHEME_BE || a.formulation != HJ_FORM_LAX ||
       a.inner_steps != 1 || a.xb == nullptr)
     return HJ_ERR_UNSUPPORTED;
-  if (a.d < 1 || a.d > 2 * kRegMaxThreads || a.N < 1 || a.N > 16) return HJ_ERR_UNSUPPORTED;
-  const int cpt = a.d <= kRegMaxThreads ? 1 : 2;
-  const int threads = ((a.d + cpt - 1) / cpt + 31) / 32 * 32;
+  if (a.d < 1 || a.N < 1 || a.N > 16) return HJ_ERR_UNSUPPORTED;
+  auto threads_for = [](int coords) { return (coords + 31) / 32 * 32; };
   if constexpr (sizeof(T) == 8) {             // FP64 state fits the registers at one coordinate, N <= 10
-    return (cpt == 1 && a.N <= 10) ? launch_reg<T, 1, 10>(a, threads, s) : HJ_ERR_UNSUPPORTED;
+    if (a.d > kRegMaxThreads || a.N > 10) return HJ_ERR_UNSUPPORTED;
+    return launch_reg<T, 1, 10, 1>(a, threads_for(a.d), s);
   } else {
-    if (cpt == 1) return a.N <= 10 ? launch_reg<T, 1, 10>(a, threads, s) : launch_reg<T, 1, 16>(a, threads, s);
-    return a.N <= 10 ? launch_reg<T, 2, 10>(a, threads, s) : HJ_ERR_UNSUPPORTED;
+    if (a.d <= kRegMaxThreads)
+      return a.N <= 10 ? launch_reg<T, 1, 10, 1>(a, threads_for(a.d), s)
+                       : launch_reg<T, 1, 16, 1>(a, threads_for(a.d), s);
+    if (a.N > 10) return HJ_ERR_UNSUPPORTED;
+    if (a.d <= 2 * kRegMaxThreads) return launch_reg<T, 2, 10, 1>(a, threads_for((a.d + 1) / 2), s);
+    if (a.d <= 4 * kRegMaxThreads)              // two CTAs, each half of the coordinates
+      return launch_reg<T, 2, 10, 2>(a, threads_for(((a.d + 1) / 2 + 1) / 2), s);
+    return HJ_ERR_UNSUPPORTED;
   }
 }
 

@@ -91,34 +91,52 @@ __device__ __forceinline__ void storev(float* p, const float (&v)[TJ]) {
     *reinterpret_cast<float4*>(p + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
-// acc[r][c] = sum_k M[k][i0 + r] * S[k][c0 + c], k < d (M k-major with stride dp)
+// acc[r][c] = sum_k M[k][i0 + r] * S[k][c0 + c], k < d (M k-major with stride dp).
+// The accumulators are updated in pairs of nodes by the packed FP32 fma
+// (__ffma2_rn: each lane rounded once, bitwise the same as two fmaf), half the
+// issue slots of scalar fmaf.
 template <int TJ>
 __device__ __forceinline__ void tile_product(const float* M, const float* S, int d, int dp,
                                              int Ns, int i0, int c0,
                                              float (&acc)[kTI][TJ]) {
+  float2 acc2[kTI][TJ / 2];
 #pragma unroll
   for (int r = 0; r < kTI; ++r)
 #pragma unroll
-    for (int c = 0; c < TJ; ++c) acc[r][c] = 0.f;
+    for (int q = 0; q < TJ / 2; ++q) acc2[r][q] = make_float2(0.f, 0.f);
   const float* mp = M + i0;
   const float* sp = S + c0;
 #pragma unroll 4
   for (int k = 0; k < d; ++k) {
     const float4 a = *reinterpret_cast<const float4*>(mp);
-    float s[TJ];
-    loadv<TJ>(sp, s);
+    float2 s2[TJ / 2];
+#pragma unroll
+    for (int q = 0; q < TJ / 4; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(sp + 4 * q);
+      s2[2 * q] = make_float2(v.x, v.y);
+      s2[2 * q + 1] = make_float2(v.z, v.w);
+    }
     mp += dp;
     sp += Ns;
     const float av[kTI] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-    for (int r = 0; r < kTI; ++r)
+    for (int r = 0; r < kTI; ++r) {
+      const float2 ar = make_float2(av[r], av[r]);
 #pragma unroll
-      for (int c = 0; c < TJ; ++c) acc[r][c] = fmaf(av[r], s[c], acc[r][c]);
+      for (int q = 0; q < TJ / 2; ++q) acc2[r][q] = __ffma2_rn(ar, s2[q], acc2[r][q]);
+    }
   }
+#pragma unroll
+  for (int r = 0; r < kTI; ++r)
+#pragma unroll
+    for (int q = 0; q < TJ / 2; ++q) { acc[r][2 * q] = acc2[r][q].x; acc[r][2 * q + 1] = acc2[r][q].y; }
 }
 
+// Four-node tiles launch 128-thread CTAs (one group of two warps, or four of
+// one) and are held to 128 registers, four CTAs (16 warps) per SM.
 template <int TJ, int G, bool TH1, bool HOPF>
-__global__ void __launch_bounds__(256) lax_td_tile_kernel(const SolveArgs<float> a, int M) {
+__global__ void __launch_bounds__(TJ == 4 ? 128 : 256, TJ == 4 ? 4 : 1)
+lax_td_tile_kernel(const SolveArgs<float> a, int M) {
   constexpr int kTJ = TJ;
   extern __shared__ __align__(16) unsigned char smem[];
   const TileLayout<TJ> L(a.d, a.N, G, M);
