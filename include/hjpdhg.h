@@ -208,7 +208,13 @@ typedef struct {
 } hj_solver_opts;
 
 /* Solve B independent points with a common N (Algorithm 1, Eq. (disclaxBE); with
- * opts->formulation = HJ_FORM_HOPF, Algorithm 2, Eq. (dischopf)).
+ * opts->formulation = HJ_FORM_HOPF, Algorithm 2, Eq. (dischopf)).  Points with
+ * their own N, or their own problem, go through a ragged plan
+ * (hj_ragged_plan_create) instead of per-point N and trajectory offsets here:
+ * the plan sorts them into buckets by N class once, gives each bucket its own
+ * launch shape, and replays the buckets as one CUDA graph, which a single call
+ * with a common launch shape could not do without running every point at the
+ * largest N's shape.
  *   xq       (device) [B][d] double: query points x (x_N is pinned to them).
  *   t        (device) [B] double: horizons t > 0; delta = t / N per point.
  *   N        number of time steps, 1..256 (nodes j = 0..N).
