@@ -510,10 +510,10 @@ hj_status hj_solve_batch_retry(hj_problem prob, int64_t B, const double* xq, con
  *                                 as hj_solve_batch (no warm start; the launch
  *                                 shape is the default for (precision, N)).
  * The first call on a device looks up the array's device address (set-up, once
- * per device, with that device current): make that first call before any
- * stream capture.  Every call shares the one array and overwrites it (the work
- * counter is cleared on each call): calls that overlap on the GPU, from any
- * stream or thread, race and must be serialised by the caller.
+ * per device, with that device current).  Every call shares the one array and
+ * overwrites it (the work counter is cleared on each call): calls that overlap
+ * on the GPU, from any stream or thread, race and must be serialised by the
+ * caller.
  * Errors: as hj_solve_batch; HJ_ERR_UNSUPPORTED when the parameters do not fit
  * the array (tanh drift: 3d + 3d^2 doubles for FP64, 3d + 2d^2 doubles for
  * FP32, plus alignment: d <= 51 in FP64, d <= 62 in FP32).                   */

@@ -132,10 +132,16 @@ __device__ __forceinline__ void tile_product(const float* M, const float* S, int
     for (int q = 0; q < TJ / 2; ++q) { acc[r][2 * q] = acc2[r][q].x; acc[r][2 * q + 1] = acc2[r][q].y; }
 }
 
-// Four-node tiles launch 128-thread CTAs (one group of two warps, or four of
-// one) and are held to 128 registers, four CTAs (16 warps) per SM.
+// Four-node tiles are held to 128 registers: CTAs of max(128, 32 G) threads,
+// 65536 / (128 x threads) of them per SM (16 warps).  Eight-node tiles: up to
+// 256 threads, about 240 registers.
+template <int TJ, int G>
+constexpr int tile_cta_threads() { return TJ == 4 ? (32 * G > 128 ? 32 * G : 128) : 256; }
+template <int TJ, int G>
+constexpr int tile_min_ctas() { return TJ == 4 ? 65536 / (128 * tile_cta_threads<TJ, G>()) : 1; }
+
 template <int TJ, int G, bool TH1, bool HOPF>
-__global__ void __launch_bounds__(TJ == 4 ? 128 : 256, TJ == 4 ? 4 : 1)
+__global__ void __launch_bounds__(tile_cta_threads<TJ, G>(), tile_min_ctas<TJ, G>())
 lax_td_tile_kernel(const SolveArgs<float> a, int M) {
   constexpr int kTJ = TJ;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -432,22 +438,27 @@ template <int TJ, bool TH1, bool HOPF>
 hj_status launch_tj(const SolveArgs<float>& a, int G, int M, size_t smem, cudaStream_t s) {
   if (G == 1) return launch_g<TJ, 1, TH1, HOPF>(a, M, smem, s);
   if (G == 2) return launch_g<TJ, 2, TH1, HOPF>(a, M, smem, s);
-  if constexpr (TJ == 8) {           // four-node tiles are taken only for one or two warps
-    if (G == 4) return launch_g<TJ, 4, TH1, HOPF>(a, M, smem, s);
-    return launch_g<TJ, 8, TH1, HOPF>(a, M, smem, s);
+  if (G == 4) return launch_g<TJ, 4, TH1, HOPF>(a, M, smem, s);
+  if (G == 8) return launch_g<TJ, 8, TH1, HOPF>(a, M, smem, s);
+  if constexpr (TJ == 4) {           // 16 warps: four-node tiles only (128 registers)
+    if (G == 16) return launch_g<TJ, 16, TH1, HOPF>(a, M, smem, s);
   }
   return HJ_ERR_UNSUPPORTED;
 }
 
+// warps per point: a power of two up to 8 (eight-node tiles, about 240
+// registers) or 16 (four-node tiles, 128 registers); 0 if it does not fit
 int group_warps(int d, int N, int TJ) {
   const int w = (tile_slots(d, N, TJ) + 31) / 32;
-  return w <= 1 ? 1 : w <= 2 ? 2 : w <= 4 ? 4 : w <= 8 ? 8 : 0;
+  const int g = w <= 1 ? 1 : w <= 2 ? 2 : w <= 4 ? 4 : w <= 8 ? 8 : w <= 16 ? 16 : 0;
+  return (g == 16 && TJ != 4) ? 0 : g;
 }
 
-// time nodes per tile: 4 where d <= 32 and a point still fits two warps, else 8
+// time nodes per tile: 4 where d <= 32 (four-node tiles hold twice the warps
+// per SM), else 8
 int tile_nodes(int d, int N) {
   const int g4 = group_warps(d, N, 4);
-  return (d <= 32 && g4 >= 1 && g4 <= 2) ? 4 : 8;
+  return (d <= 32 && g4 >= 1) ? 4 : 8;
 }
 
 }  // namespace

@@ -127,8 +127,9 @@ def test_quadratic_closed_form_on_gpu():
 
 
 def test_full_size_quadcopter_sampled():
-    """The 4096-point quadcopter workload in the configuration the benchmark times;
-    sampled points against the converged oracle."""
+    """The 4096-point quadcopter workload in the configuration the benchmark times:
+    sampled points against the converged oracle, and every point's trajectory
+    against the discrete characteristic equations."""
     w = W.quadcopter()
     g = gpu(w, "fp32")
     conv = g["status"] == O.CONVERGED
@@ -143,11 +144,22 @@ def test_full_size_quadcopter_sampled():
     assert ev.max() <= 1e-4
     # trajectories of the sampled points at the tighter stop of the trajectory bar
     # (the whole batch rerun, so each point keeps its own initial guess)
-    gt = gpu(w, "fp32", tol=1e-10)
+    gt = gpu(w, "fp32", tol=1e-10, kkt=True)
     et = np.max(np.abs(gt["traj_x"][idx] - o["x"]))
     ep = np.max(np.abs(gt["traj_p"][idx] - o["p"]))
     print(f"quadcopter 4096 at tol 1e-10: sampled |dx| {et:.2e} |dp| {ep:.2e}")
     assert et <= 1e-3 and ep <= 1e-3
+    # every point of the batch: the oracle's residual of the discrete
+    # characteristic equations (Section 4) on the GPU's own trajectory, and the
+    # GPU's certificate of it (evaluated in FP32 for FP32 iterates)
+    xt, pt = gt["traj_x"].astype(np.float64), gt["traj_p"].astype(np.float64)
+    r = O.kkt_residual(w, xt, pt)
+    ok = gt["status"] == O.CONVERGED
+    print(f"quadcopter 4096 at tol 1e-10: oracle KKT of the GPU trajectories, converged "
+          f"points: median {np.median(r[ok]):.2e}, max {r[ok].max():.2e}")
+    assert np.mean(ok) >= 0.995 and r[ok].max() <= 2e-4
+    from test_kkt_gpu import _qc_fp32_scale     # the FP32 evaluation's derived bar
+    assert np.all(np.abs(gt["kkt"] - r) <= 2.0 ** -19 * _qc_fp32_scale(w, xt, pt))
     # the points the GPU reports as not converged are slow for the oracle too
     bad = np.where(~conv)[0][:2]
     if bad.size:
