@@ -51,8 +51,8 @@ __device__ __forceinline__ float sqrtk<float>(float y) { return sqrtf(y); }
 // shared memory past the state: red[nwarps][2 (Nmax + 1)] partial sums,
 // keep[Nmax + 1], coef[Nmax + 1] node scalars (and, for the mixed schemes,
 // the speed c, the gradient factor and |p| of every node: 3 (Nmax + 1)),
-// xbs[d], goff[d], ginv[d], then tred[2 nwarps] doubles (the stopping sums) at
-// the next 8-byte boundary
+// xbs[d], goff[d], ginv[d], then room for 2 nwarps doubles at the next 8-byte
+// boundary (tred: the warps' stopping sums, held in the iterate type)
 struct EikLayout {
   size_t state;       // elements of one state array: (Nmax + 1) d
   size_t scal;        // elements past the state arrays

@@ -2,9 +2,9 @@
 // H = <p, tanh(A x)> + |p|^2/2 (Algorithm 1 with the Section 5.3 updates).
 //
 // A group of G warps solves one query point.  Each thread owns a fixed tile of
-// 4 coordinates x TJ time nodes (TJ = 8; 4 for d <= 32, where a point then fits
-// two warps and twice the warps fit an SM: 9 % faster at d = 32, while at
-// d = 100 the doubled group measured 25 % slower) and keeps that tile's x, p and z in registers
+// 4 coordinates x TJ time nodes (TJ = 4 for d <= 64: 128 registers, twice the
+// warps per SM, groups of up to 16 warps; TJ = 8 above, where the larger groups
+// measured slower) and keeps that tile's x, p and z in registers
 // for the whole solve (thread t of the group: within each block of 4*TIc
 // threads, i-tile = u / 4 and j-tile = 4 * block + u % 4, so a quarter-warp
 // covers 2 i-tiles x 4 j-tiles and its 16-byte operand loads stay cheap).  Only
@@ -454,11 +454,11 @@ int group_warps(int d, int N, int TJ) {
   return (g == 16 && TJ != 4) ? 0 : g;
 }
 
-// time nodes per tile: 4 where d <= 32 (four-node tiles hold twice the warps
+// time nodes per tile: 4 where d <= 64 (four-node tiles hold twice the warps
 // per SM), else 8
 int tile_nodes(int d, int N) {
   const int g4 = group_warps(d, N, 4);
-  return (d <= 32 && g4 >= 1) ? 4 : 8;
+  return (d <= 64 && g4 >= 1) ? 4 : 8;
 }
 
 }  // namespace

@@ -47,14 +47,16 @@ def TRAJ_TOL(d):
 # shapes that cover every kernel variant: warp kernel NPL 1/2/4 with ragged N,
 # the shared-memory kernel with d not a multiple of 4, and B not a multiple of
 # the warps per CTA; the FP32 tiled tanh-drift kernel with four-node tiles
-# (d = 8, 13, 32: one and two warps per point) and eight-node tiles (d = 24 at
-# N = 70, d = 64, 100: two to four warps)
+# (d = 8, 13, 32, 64 at N = 7, 24 at N = 70, 64 at N = 64, 32 at N = 200: one,
+# two, four, eight and sixteen warps per point) and eight-node tiles (d = 100 at
+# N = 32, 80 at N = 40: four and eight warps)
 SHAPES = [
     ("quadratic", 2, 20), ("quadratic", 3, 37), ("quadratic", 4, 100), ("quadratic", 1, 5),
     ("quadcopter", 12, 64), ("quadcopter", 12, 23),
     ("tanh_drift", 4, 50), ("tanh_drift", 8, 16), ("tanh_drift", 2, 128),
     ("tanh_drift", 32, 32), ("tanh_drift", 13, 21), ("tanh_drift", 100, 32), ("tanh_drift", 64, 7),
-    ("tanh_drift", 24, 70),
+    ("tanh_drift", 24, 70), ("tanh_drift", 32, 200), ("tanh_drift", 80, 40),
+    ("tanh_drift", 64, 64),
 ]
 
 
