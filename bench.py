@@ -53,7 +53,8 @@ FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the timed FP32
 # kernel (lax_warp_kernel<float, FamQuadcopter, 12, 1, 2>) from the ncu capture
 # of that kernel (475 392 read, 0 written: V, iters and status stay in L2 within
-# the launch); None whenever the kernel has changed since the capture.
+# the launch; the same in a capture of the current source); None whenever the
+# kernel has changed since the capture.
 QC_TRAFFIC_BYTES = 475392
 
 

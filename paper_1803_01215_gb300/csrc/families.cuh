@@ -208,7 +208,7 @@ struct FamQuadcopter {
   double m64, ah64, gz64, eps64;
   __device__ static void load_shared(const SolveArgs<T>&, Shared&) {}
   __device__ FamQuadcopter(const SolveArgs<T>& s, const Shared&)
-      : m_inv(T(1.0 / s.qc_m)), ah(T(s.qc_ah)), gz(T(s.qc_gz)), eps(T(s.qc_eps)),
+      : m_inv(s.qc_t[0]), ah(s.qc_t[1]), gz(s.qc_t[2]), eps(s.qc_t[3]),
         m64(s.qc_m), ah64(s.qc_ah), gz64(s.qc_gz), eps64(s.qc_eps) {}
 
   template <typename U>
@@ -614,8 +614,8 @@ struct FamEikonalT {
     }
   }
   __device__ FamEikonalT(const SolveArgs<T>& s, const Shared& sh)
-      : xb(sh.xb), vb(sh.vb), xb64(s.xb64), vb64(s.vb64), c0(T(s.eik_c0)), c1(T(s.eik_c1)),
-        c2(T(s.eik_c2)), c0d(s.eik_c0), c1d(s.eik_c1), c2d(s.eik_c2) {}
+      : xb(sh.xb), vb(sh.vb), xb64(s.xb64), vb64(s.vb64), c0(s.eik_t[0]), c1(s.eik_t[1]),
+        c2(s.eik_t[2]), c0d(s.eik_c0), c1d(s.eik_c1), c2d(s.eik_c2) {}
   __device__ __forceinline__ PC point(T lam) const { return PC{lam}; }
   // the bump centre at time s
   __device__ __forceinline__ T centre(int k, T s) const {
@@ -745,8 +745,8 @@ struct FamGame {
     for (int i = threadIdx.x; i < D; i += blockDim.x) sh.zb[i] = s.xb[i];
   }
   __device__ FamGame(const SolveArgs<T>& s, const Shared& sh)
-      : zb(sh.zb), zb64(s.xb64), d1(s.game_d1), c0(T(s.eik_c0)), am(T(s.eik_c1)),
-        bw(T(s.eik_c2)), c0d(s.eik_c0), amd(s.eik_c1), bwd(s.eik_c2) {}
+      : zb(sh.zb), zb64(s.xb64), d1(s.game_d1), c0(s.eik_t[0]), am(s.eik_t[1]),
+        bw(s.eik_t[2]), c0d(s.eik_c0), amd(s.eik_c1), bwd(s.eik_c2) {}
   __device__ __forceinline__ PC point(T lam) const { return PC{lam}; }
   __device__ __forceinline__ void context(const T (&z)[D], Ctx& c) const {
     T r1 = T(0), r2 = T(0);

@@ -56,6 +56,11 @@ struct SolveArgs {
   const double* A64;     // tanh drift: [d][d] row-major in double (value epilogue)
   double qc_m, qc_ah, qc_gz, qc_eps;   // quadcopter parameters
   double eik_c0, eik_c1, eik_c2;       // eikonal speed c(x) = c0 + c1 exp(-c2 |x - x_b|^2)
+  // the same in the iterate type, rounded once on the host (fill_family_consts):
+  // 1/m, a_h, g_z, eps and c0, c1, c2.  A kernel that rematerialises one of them
+  // under register pressure then loads it instead of converting a double (an
+  // FP64-pipe instruction at 1/64 rate)
+  T qc_t[4], eik_t[3];
   const double* xb64;                  // [d] eikonal bump centre x_b
   const T* xb;                         // [d] the same in T
   // eikonal bump moving with velocity v_b: c(x - s v_b) at node time s = j delta
@@ -82,6 +87,17 @@ struct SolveArgs {
   const int64_t* xq_off;
   const int64_t* traj_off;
 };
+
+template <typename T>
+inline void fill_family_consts(SolveArgs<T>& a) {
+  a.qc_t[0] = a.qc_m != 0.0 ? T(1.0 / a.qc_m) : T(0);
+  a.qc_t[1] = T(a.qc_ah);
+  a.qc_t[2] = T(a.qc_gz);
+  a.qc_t[3] = T(a.qc_eps);
+  a.eik_t[0] = T(a.eik_c0);
+  a.eik_t[1] = T(a.eik_c1);
+  a.eik_t[2] = T(a.eik_c2);
+}
 
 template <typename T>
 struct PointRef {
@@ -429,9 +445,10 @@ template <typename T>
 hj_status launch_eik_cta_solver(const SolveArgs<T>& a, cudaStream_t s);
 template <typename T>
 size_t eik_cta_smem_bytes(int d, int N);
-// The same with the state in registers (backward Euler, static bump, d <= 1024 in
-// FP32 with N <= 10 above d = 512 and N <= 16 below, d <= 512 and N <= 10 in
-// FP64); HJ_ERR_UNSUPPORTED elsewhere (the shared-memory kernel then runs).
+// The same with the state in registers (backward Euler, static bump; FP32:
+// d <= 2048 with N <= 10, on a cluster of two CTAs above d = 1024, and d <= 512
+// with N <= 16; FP64: d <= 512 with N <= 10); HJ_ERR_UNSUPPORTED elsewhere (the
+// shared-memory kernel then runs).
 template <typename T>
 hj_status launch_eik_reg_solver(const SolveArgs<T>& a, cudaStream_t s);
 

@@ -121,6 +121,7 @@ hj_status launch_kkt_nodes(const hj_problem_s* p, int64_t B, int32_t N, const do
   a.W2 = p->W2; a.c = p->c; a.A64 = p->Ad;
   a.qc_m = p->qc[0]; a.qc_ah = p->qc[1]; a.qc_gz = p->qc[2]; a.qc_eps = p->qc[3];
   a.eik_c0 = p->eik[1]; a.eik_c1 = p->eik[2]; a.eik_c2 = p->eik[3];
+  fill_family_consts(a);
   a.xb64 = p->xbd; a.vb64 = p->vbd;
   a.cost_sign = (p->family == HJ_FAMILY_EIKONAL && p->eik[0] < 0) ? -1.0 : 1.0;
   switch (p->family) {

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(512) lax_eik_kernel(const SolveArgs<T> a, T* w
     ginv[k] = T(1.0 / (1.0 + a.tau * w2));
   }
   const T sig = a.sigma_t, tau = a.tau_t, th = a.theta_t;
-  const T c0 = T(a.eik_c0), c1 = T(a.eik_c1), c2 = T(a.eik_c2);
+  const T c0 = a.eik_t[0], c1 = a.eik_t[1], c2 = a.eik_t[2];
   const T wr = a.mix_wr_t, wl = a.mix_wl_t;
   __syncthreads();
 

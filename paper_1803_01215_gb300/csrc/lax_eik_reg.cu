@@ -1,8 +1,8 @@
 // Coordinate-parallel batched PDHG for the eikonal family with the state in
 // registers (Section 6.1: H = c(x)|p|_2, c(x) = c0 + c1 exp(-c2 |x - x_b|^2),
-// Algorithm 1 with the shrink_2 dual step and one gradient step in x), for
-// d <= 1024 and N <= 16, static bump, backward Euler: the paper's
-// dimensional-scaling runs (N = 10) up to d = 1000.
+// Algorithm 1 with the shrink_2 dual step and one gradient step in x), static
+// bump, backward Euler, N <= 16, d up to 2048 (a cluster of two CTAs above
+// 1024): the paper's dimensional-scaling runs (N = 10) up to d = 2000.
 //
 // One CTA solves one query point.  Thread t owns the coordinates
 // k = t + c T (c < CPT) and keeps x_j, p_j, z_j of every node j = 0..N of those
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kRegMaxThreads) lax_eik_reg_kernel(const Solve
     peer_point = cl.map_shared_rank(&s_point, 0u);
   }
   const T sig = a.sigma_t, tau = a.tau_t, th = a.theta_t;
-  const T c0 = T(a.eik_c0), c1 = T(a.eik_c1), c2 = T(a.eik_c2);
+  const T c0 = a.eik_t[0], c1 = a.eik_t[1], c2 = a.eik_t[2];
   const int kbase = (int)rank * T_ * CPT;          // first coordinate of this CTA's span
   // the thread's coordinates: bump centre and the g-prox (with the cost sign)
   bool own[CPT];
@@ -416,6 +416,10 @@ hj_status launch_eik_reg_solver(const SolveArgs<T>& a, cudaStream_t s) {
     if (a.d > kRegMaxThreads || a.N > 10) return HJ_ERR_UNSUPPORTED;
     return launch_reg<T, 1, 10, 1>(a, threads_for(a.d), s);
   } else {
+    // two coordinates per thread from d = 64 (half the threads per point, the
+    // same work per barrier: d = 100 ran 13.5 against 15.2 ms), one below
+    if (a.d >= 64 && a.d <= 2 * kRegMaxThreads && a.N <= 10)
+      return launch_reg<T, 2, 10, 1>(a, threads_for((a.d + 1) / 2), s);
     if (a.d <= kRegMaxThreads)
       return a.N <= 10 ? launch_reg<T, 1, 10, 1>(a, threads_for(a.d), s)
                        : launch_reg<T, 1, 16, 1>(a, threads_for(a.d), s);

@@ -155,6 +155,7 @@ hj::SolveArgs<T> make_args(const hj_problem_s* prob, int64_t B, int32_t N,
   a.W2 = prob->W2; a.c = prob->c; a.A64 = prob->Ad;
   a.qc_m = prob->qc[0]; a.qc_ah = prob->qc[1]; a.qc_gz = prob->qc[2]; a.qc_eps = prob->qc[3];
   a.eik_c0 = prob->eik[1]; a.eik_c1 = prob->eik[2]; a.eik_c2 = prob->eik[3];
+  hj::fill_family_consts(a);
   a.xb64 = prob->xbd;
   a.vb64 = prob->vbd;
   a.eik_moving = prob->eik_moving ? 1 : 0;
