@@ -350,6 +350,47 @@ struct FamQuadcopter {
     for (int r = 0; r < 3; ++r) v[6 + r] = y[r] - f * q[r];
   }
 
+  // The Hopf form with one code path for every lane: each row k of the prox
+  // takes an offset off_k and a reciprocal diagonal dinv_k from a per-lane table,
+  //   rows 0-5:  p_k = (v_k - off_k - lam x_{6+k}) dinv_k,
+  //   rows 9-11: p_k = (v_k - off_k) dinv_k,
+  //   rows 6-8:  L^-1 = diag(dinv_6..8), w = v - off - lam (a_h a - g_z e3),
+  //              p = L^-1 w - L^-1 b (lam b^T L^-1 w) / (1 + lam b^T L^-1 b), b = a / m,
+  // which is prox (off = 0, dinv = 1 / al, 1 / (al + lam) on rows 9-11) for a
+  // plain node and prox_first (off = hc, dinv = 1 / (al + hs), 1 / (al + lam + hs)
+  // on rows 9-11) for node 1, so the lane of node 1 no longer runs its own code.
+  static constexpr bool kHopfTable = true;
+  __device__ __forceinline__ void hopf_row(const PC& pc, const T* hs, const T* hc, int k,
+                                           T& off_plain, T& dinv_plain, T& off_first,
+                                           T& dinv_first) const {
+    const bool torque = k >= 9;
+    off_plain = T(0);
+    dinv_plain = torque ? pc.irate : pc.ial;
+    off_first = hc[k];
+    dinv_first = T(1) / (pc.al + (torque ? pc.lam : T(0)) + hs[k]);
+  }
+  __device__ __forceinline__ void prox_hopf(const Ctx& c, const PC& pc, const T (&x)[D], T (&v)[D],
+                                            const T* off, const T* dinv) const {
+    const T lam = pc.lam;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = (v[k] - off[k] - lam * x[6 + k]) * dinv[k];
+#pragma unroll
+    for (int k = 9; k < 12; ++k) v[k] = (v[k] - off[k]) * dinv[k];
+    T y[3], q[3], b[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const T w = v[6 + r] - off[6 + r] - (pc.lam_ah * c.a[r] - (r == 2 ? pc.lam_gz : T(0)));
+      b[r] = c.a[r] * m_inv;
+      y[r] = dinv[6 + r] * w;
+      q[r] = dinv[6 + r] * b[r];
+    }
+    const T by = b[0] * y[0] + b[1] * y[1] + b[2] * y[2];
+    const T bq = b[0] * q[0] + b[1] * q[1] + b[2] * q[2];
+    const T f = fdiv<T>(lam * by, T(1) + lam * bq);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) v[6 + r] = y[r] - f * q[r];
+  }
+
   __device__ __forceinline__ void gradx(const Ctx& c, const T (&)[D], const T (&p)[D],
                                         T (&g)[D]) const {
     const T u0 = (c.a[0] * p[6] + c.a[1] * p[7] + c.a[2] * p[8]) * m_inv;

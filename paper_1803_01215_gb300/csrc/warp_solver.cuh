@@ -57,7 +57,7 @@ constexpr int padded_dim() { return ((D * (int)sizeof(T) + 15) / 16) * 16 / (int
 // (x_0 <- (v + tau W^2 c) / (1 + tau W^2) as offset and reciprocal), the
 // per-lane exchange slots of the CTA's groups, and for G > 1 the reduction
 // scratch of the CTA's one group.
-template <typename T, class F, int D, int G, bool MIX = false>
+template <typename T, class F, int D, int G, bool MIX = false, bool HOPF = false>
 struct WarpShared {
   static constexpr int kGroups = groups_per_cta<G>();
   static constexpr int kL = group_lanes<G>();
@@ -74,10 +74,21 @@ struct WarpShared {
   // MIX only: x^k of each lane's last node, and x_0^k
   alignas(16) T xs[MIX ? kGroups : 1][MIX ? kL : 1][MIX ? DP : 1];
   alignas(16) T x0x[MIX ? kGroups : 1][MIX ? DP : 1];
+  // Hopf form, families with a tabled node-1 prox: per group, [0] the plain
+  // nodes' and [1] node 1's row offsets and row reciprocals (set per point)
+  alignas(16) T htab[HOPF ? kGroups : 1][2][2][HOPF ? DP : 1];
   T red[G > 0 ? G : 1][2];
   double vred[G > 0 ? G : 1];
   unsigned long long item;
 };
+
+// whether the family's Hopf node-1 prox runs from per-lane tables (F::kHopfTable):
+// every lane then takes the same code path, node 1 only other table values
+template <class F, class = void>
+struct hopf_table : std::false_type {};
+template <class F>
+struct hopf_table<F, std::void_t<decltype(F::kHopfTable)>>
+    : std::integral_constant<bool, F::kHopfTable> {};
 
 // lanes of this thread's 16-lane half
 __device__ __forceinline__ unsigned half_mask() { return 0xFFFFu << (threadIdx.x & 16); }
@@ -170,7 +181,7 @@ __device__ __forceinline__ T relax(T xn, T xo, T th) {
 
 template <typename T, class F, int D, int NPL, int G, bool TH1, bool HOPF, bool MIX>
 __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam, int64_t item,
-                                            int lane, int wg, WarpShared<T, F, D, G, MIX>& sh) {
+                                            int lane, int wg, WarpShared<T, F, D, G, MIX, HOPF>& sh) {
   static_assert(!(MIX && HOPF), "the mixed schemes are Lax-form problems");
   const PointRef<T> pt = point_ref(a, item);
   const int N = pt.N;
@@ -186,6 +197,17 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   const T wr = a.mix_wr_t, wl = a.mix_wl_t;      // MIX: weights of H at x_j and x_{j-1}
   const typename F::PC pc = fam.point(lam);
   const uint64_t gid = (uint64_t)(a.point_offset + pt.id);
+  if constexpr (HOPF && hopf_table<F>::value) {
+    // this point's row tables (read after the first iteration's group barrier)
+    const int tg = (G == 1) ? (int)(threadIdx.x >> 5) : (G == 0 ? (int)(threadIdx.x >> 4) : 0);
+    constexpr int TDP = WarpShared<T, F, D, G, MIX, HOPF>::DP;
+    for (int k = gl; k < TDP; k += group_lanes<G>()) {
+      T op = T(0), dp = T(0), of = T(0), df = T(0);
+      if (k < D) fam.hopf_row(pc, sh.hs, sh.hc, k, op, dp, of, df);
+      sh.htab[tg][0][0][k] = op; sh.htab[tg][0][1][k] = dp;
+      sh.htab[tg][1][0][k] = of; sh.htab[tg][1][1][k] = df;
+    }
+  }
 
   T x[NPL][D], p[NPL][D], z[NPL][D];
   // x_0: lane gl < D holds coordinate gl (x0 = x_0[gl], z0 = z_0[gl])
@@ -238,7 +260,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   T* xslot = &sh.xs[grp][0][0];
   T* x0xslot = &sh.x0x[grp][0];
   if constexpr (MIX) { if (own0) x0xslot[k0] = x0; }
-  constexpr int DP = WarpShared<T, F, D, G, MIX>::DP;
+  constexpr int DP = WarpShared<T, F, D, G, MIX, HOPF>::DP;
   constexpr int kLanes = group_lanes<G>();
 
   // One iteration; CHK adds the squared increments (test iterations only, so
@@ -281,8 +303,13 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         else v_sub<T, D>(dz, z[i], z[i > 0 ? i - 1 : 0]);
         v_fma<T, D>(v, sig, dz, p[i]);                       // p + sigma (z_j - z_{j-1})
         if constexpr (HOPF) {                                // Hopf: node 1 also carries g*
-          if (i == 0 && gl == 0) fam.prox_first(ctx[i], pc, x[i], v, sh.hs, sh.hc);
-          else fam.prox(ctx[i], pc, x[i], v);
+          if constexpr (hopf_table<F>::value) {
+            const T* tb = &sh.htab[grp][(i == 0 && gl == 0) ? 1 : 0][0][0];
+            fam.prox_hopf(ctx[i], pc, x[i], v, tb, tb + DP);
+          } else {
+            if (i == 0 && gl == 0) fam.prox_first(ctx[i], pc, x[i], v, sh.hs, sh.hc);
+            else fam.prox(ctx[i], pc, x[i], v);
+          }
         } else if constexpr (MIX) {                          // prox of lam (wR H(x_j) + wL H(x_{j-1}))
           if (i == 0) fam.prox_mix(ctx[i], ctxl, pc, wr, wl, x[i], xlv, v);
           else fam.prox_mix(ctx[i], ctx[i > 0 ? i - 1 : 0], pc, wr, wl, x[i], x[i > 0 ? i - 1 : 0], v);
@@ -565,9 +592,9 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
 template <typename T, class F, int D, int NPL, int G, bool TH1, bool HOPF, bool MIX>
 __global__ void __launch_bounds__(warp_block_threads<G>())
 lax_warp_kernel(const SolveArgs<T> a) {
-  __shared__ WarpShared<T, F, D, G, MIX> sh;
+  __shared__ WarpShared<T, F, D, G, MIX, HOPF> sh;
   F::load_shared(a, sh.fam);
-  for (int k = threadIdx.x; k < WarpShared<T, F, D, G, MIX>::DP; k += blockDim.x) {
+  for (int k = threadIdx.x; k < WarpShared<T, F, D, G, MIX, HOPF>::DP; k += blockDim.x) {
     // cost_sign = -1 (negative eikonal): the positive equation with initial data -g
     const double w2 = k < D ? a.cost_sign * a.W2[k] : 0.0, c = k < D ? a.c[k] : 0.0;
     if (k < D) { sh.w2d[k] = w2; sh.cd[k] = c; }
