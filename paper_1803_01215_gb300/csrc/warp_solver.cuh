@@ -74,6 +74,8 @@ struct WarpShared {
   // MIX only: x^k of each lane's last node, and x_0^k
   alignas(16) T xs[MIX ? kGroups : 1][MIX ? kL : 1][MIX ? DP : 1];
   alignas(16) T x0x[MIX ? kGroups : 1][MIX ? DP : 1];
+  // MIX only: grad_x H(x_0^k, p_1^{k+1}) for the x_0 step, from node 1's lane
+  alignas(16) T g0s[MIX ? kGroups : 1][MIX ? DP : 1];
   // Hopf form, families with a tabled node-1 prox: per group, [0] the plain
   // nodes' and [1] node 1's row offsets and row reciprocals (set per point)
   alignas(16) T htab[HOPF ? kGroups : 1][2][2][HOPF ? DP : 1];
@@ -259,6 +261,7 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
   if (own0) x0slot[k0] = z0;                  // read by lane 0 after the first barrier
   T* xslot = &sh.xs[grp][0][0];
   T* x0xslot = &sh.x0x[grp][0];
+  T* g0slot = &sh.g0s[grp][0];
   if constexpr (MIX) { if (own0) x0xslot[k0] = x0; }
   constexpr int DP = WarpShared<T, F, D, G, MIX, HOPF>::DP;
   constexpr int kLanes = group_lanes<G>();
@@ -325,6 +328,16 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
         for (int k = 0; k < D; ++k) p[i][k] = v[k];
       }
     }
+    // MIX (not the game): node 1's lane holds x_0^k's context (its left
+    // neighbour's) and p_1^{k+1}: it forms grad_x H(x_0^k, p_1) once for the
+    // x_0 lanes, which read it after the barrier below
+    if constexpr (MIX && !F::kGame && F::kHasGradX) {
+      if (gl == 0) {
+        T g0[D];
+        fam.gradx(ctxl, xlv, p[0], g0);
+        slot_store<T, D>(g0slot, g0);
+      }
+    }
     // ---- primal step: p_{j+1} of the last owned node from the right lane's slot
     slot_store<T, D>(pslot + gl * DP, p[0]);
     group_sync<G>();
@@ -349,16 +362,8 @@ __device__ __forceinline__ void solve_point(const SolveArgs<T>& a, const F& fam,
       } else {
         T v0 = x0 + tau * pslot[k0];                          // (D^T p)_0 = -p_1
         if constexpr (MIX) {
-          // + tau delta wL grad_x H(x_0^k, p_1): the whole gradient, coordinate k0 kept
-          T p1[D], g0[D];
-          slot_load<T, D>(pslot, p1);
-          typename F::Ctx c0;
-          fam.context(x0v, c0);
-          fam.gradx(c0, x0v, p1, g0);
-          T gk = T(0);
-#pragma unroll
-          for (int k = 0; k < D; ++k) gk = (k == k0) ? g0[k] : gk;
-          v0 += taud * wl * gk;
+          // + tau delta wL grad_x H(x_0^k, p_1), coordinate k0 (from node 1's lane)
+          if constexpr (F::kHasGradX) v0 += taud * wl * g0slot[k0];
         }
         xn = (v0 + goff) * ginv;
       }
