@@ -38,7 +38,8 @@ struct kkt_in_iter_type<F, std::void_t<decltype(F::kKktInIterType)>>
 template <typename T, class F, int D>
 __device__ __forceinline__ double node_residual(const SolveArgs<T>& a, const F& fam,
                                                      const T* __restrict__ X,
-                                                     const T* __restrict__ P, int64_t b, int j) {
+                                                     const T* __restrict__ P, int64_t b, int j,
+                                                     const T* __restrict__ gsh) {
   const int N = a.N;
   const double sgn = a.cost_sign;
   {
@@ -57,9 +58,21 @@ __device__ __forceinline__ double node_residual(const SolveArgs<T>& a, const F& 
                              ? (double)((float)a.t[b] / (float)N) : a.t[b] / N;
     double r = fam.kkt_node(x, xl, p, pr, delta, (double)j * delta, j < N);
     if (j == 1) {                            // r2 = p_1 - grad g(x_0) (g with the cost sign)
+      if constexpr (sizeof(T) == 4 && kkt_in_iter_type<F>::value) {
+        // in FP32 like the node's terms, W^2 and c staged as floats (gsh): FP64
+        // here ran on one lane per point at the 1/64-rate pipe
+        float rf = 0.f;
 #pragma unroll
-      for (int k = 0; k < D; ++k)
-        r = max_nan(r, fabs((double)p[k] - sgn * a.W2[k] * ((double)xl[k] - a.c[k])));
+        for (int k = 0; k < D; ++k) {
+          const float e = fabsf(p[k] - float(sgn) * gsh[k] * (xl[k] - gsh[D + k]));
+          rf = (e > rf || e != e) ? e : rf;
+        }
+        r = max_nan(r, (double)rf);
+      } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          r = max_nan(r, fabs((double)p[k] - sgn * a.W2[k] * ((double)xl[k] - a.c[k])));
+      }
     }
     return r;
   }
@@ -69,8 +82,11 @@ template <typename T, class F, int D>
 __global__ void __launch_bounds__(256)
 kkt_node_kernel(const SolveArgs<T> a, const T* __restrict__ X, const T* __restrict__ P,
                 double* __restrict__ kkt) {
-  typename F::Shared unused;                 // the FP64 node residual reads no shared data
+  typename F::Shared unused;                 // the node residual reads no family data
   const F fam(a, unused);
+  __shared__ T gsh[2 * D];                   // W^2 and c in the iterate type
+  for (int k = threadIdx.x; k < D; k += blockDim.x) { gsh[k] = T(a.W2[k]); gsh[D + k] = T(a.c[k]); }
+  __syncthreads();
   const int N = a.N;
   const int64_t total = a.B * (int64_t)N;
   const int lane = threadIdx.x & 31;
@@ -82,7 +98,7 @@ kkt_node_kernel(const SolveArgs<T> a, const T* __restrict__ X, const T* __restri
     const bool valid = idx < total;
     const int64_t b = valid ? idx / N : -1;
     double r = 0.0;
-    if (valid) r = node_residual<T, F, D>(a, fam, X, P, b, 1 + (int)(idx - b * N));
+    if (valid) r = node_residual<T, F, D>(a, fam, X, P, b, 1 + (int)(idx - b * N), gsh);
     unsigned long long v = (unsigned long long)__double_as_longlong(r);
     // maximum over the run of lanes holding the same point (b is nondecreasing in the lane)
 #pragma unroll
