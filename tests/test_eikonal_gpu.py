@@ -182,3 +182,33 @@ def test_moving_bump_same_stop_value_test_and_errors():
         binding.solve_batch(p3, torch.as_tensor(w3["xq"], device="cuda"), t[:3], 10,
                             binding.make_opts(sigma=0.5, tau=0.48))
     assert e.value.code == 2
+
+
+@pytest.mark.parametrize("d,N,sign", [(37, 10, -1), (100, 10, 1), (1300, 7, -1), (2000, 10, 1)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_warm_start_from_oracle_iterate(d, N, sign, precision):
+    """Resume from an oracle iterate (costates in the traj_p convention, the
+    negative equation's included).  FP32 runs the register-resident kernels
+    (one and two coordinates per thread, the two-CTA cluster above d = 1024);
+    FP64 the register kernel up to d = 512, the workspace kernel above."""
+    from paper_1803_01215_gb300 import binding
+    w = _w(d, sign, N, 3 if d >= 1000 else 9, seed=57)
+    K = 40
+    o = O.solve(w, tol=0.0, max_iter=K, check_every=K)
+    prob = binding.Problem.from_workload(w)
+    opts = binding.make_opts(sigma=w["sigma"], tau=w["tau"], tol=0.0, max_iter=60, check_every=60,
+                             precision=precision, seed=w["seed"], init_radius=w["init_radius"])
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    out = binding.solve_batch(prob, torch.as_tensor(w["xq"], device="cuda"),
+                              torch.as_tensor(w["t"], device="cuda"), N, opts, return_traj=True,
+                              warm_x=torch.as_tensor(o["x"], device="cuda", dtype=dt).contiguous(),
+                              warm_p=torch.as_tensor(o["p"], device="cuda", dtype=dt).contiguous())
+    o2 = O.solve(w, tol=0.0, max_iter=60, check_every=60, x_init=o["x"], p_init=o["p"])
+    ex = np.max(np.abs(out["traj_x"].cpu().numpy() - o2["x"]))
+    ep = np.max(np.abs(out["traj_p"].cpu().numpy() - o2["p"]))
+    ev = np.max(value_err(out["V"].cpu().numpy(), o2["V"]))
+    print(f"eikonal d={d} N={N} s={sign:+d} {precision} warm start: |dx| {ex:.2e} |dp| {ep:.2e} V {ev:.2e}")
+    if precision == "fp64":
+        assert ex <= 1e-10 and ep <= 1e-10 and ev <= 1e-9
+    else:                   # the fixed-iteration bars (p scaled by sigma / 25, see above)
+        assert ex <= 1e-4 and ep <= 1e-4 * max(1.0, w["sigma"] / 25.0) and ev <= 1e-4
