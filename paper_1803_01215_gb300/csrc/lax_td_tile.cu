@@ -106,7 +106,9 @@ __device__ __forceinline__ void tile_product(const float* M, const float* S, int
     for (int q = 0; q < TJ / 2; ++q) acc2[r][q] = make_float2(0.f, 0.f);
   const float* mp = M + i0;
   const float* sp = S + c0;
-#pragma unroll 4
+  // k-steps unrolled 4 (four-node tiles, at 128 registers) or 8 (eight-node
+  // tiles: d = 100 ran 290.7 against 297.7 ms; four-node tiles lost at 8)
+#pragma unroll(TJ == 4 ? 4 : 8)
   for (int k = 0; k < d; ++k) {
     const float4 a = *reinterpret_cast<const float4*>(mp);
     float2 s2[TJ / 2];
