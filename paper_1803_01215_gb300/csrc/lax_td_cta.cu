@@ -188,8 +188,7 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
 #pragma unroll
             for (int c = 0; c < kTJ; ++c)
               if (i0 + r < d && j0 + c <= N) Asv[(i0 + r) * Np + j0 + c] = tanh_c<T>(acc[r][c]);
-          continue;
-        }
+        } else {
 #pragma unroll
         for (int r = 0; r < kTI; ++r) {
           const int i = i0 + r;
@@ -208,6 +207,7 @@ lax_td_cta_kernel(const SolveArgs<T> a) {
               Wk[e] = (T(1) - av * av) * pn;
             }
           }
+        }
         }
       }
       if constexpr (MIX) {
