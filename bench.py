@@ -6,8 +6,9 @@ all-FP64 GPU path.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One step = one hj_solve_batch call over the whole batch (initial guess, the
-PDHG iterations to convergence, the FP64 value, the FP64 residual of the discrete
-characteristic equations per point, trajectories written to HBM).
+PDHG iterations to convergence, the value summed in FP64, the residual of the
+discrete characteristic equations per point (evaluated in FP32 for these FP32
+iterates), trajectories written to HBM).
 A solve counts when its status is CONVERGED and |V - V_fp64| <= 1e-4 max(1, |V_fp64|),
 V_fp64 from the all-FP64 GPU path on the same inputs (computed once, untimed).
 Between timed steps a 512 MB buffer is written to flush L2.  Under torchrun

@@ -307,8 +307,9 @@ def solve_batch(problem, xq, t, N, opts, *, return_traj=False, warm_x=None, warm
 
 
 def kkt_residual(problem, t, N, precision, traj_x, traj_p, stream=None):
-    """hj_kkt_residual: FP64 residual of the discrete characteristic equations at
-    the given trajectories ([B, N+1, d] in the precision's type), [B] device tensor."""
+    """hj_kkt_residual: residual of the discrete characteristic equations at the
+    given trajectories ([B, N+1, d] in the precision's type; FP64 evaluation, FP32
+    for the quadcopter's FP32 trajectories), [B] float64 device tensor."""
     B = t.shape[0]
     out = torch.empty(B, dtype=torch.float64, device=t.device)
     s = stream if stream is not None else torch.cuda.current_stream(t.device)
