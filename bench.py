@@ -1,7 +1,7 @@
 """Benchmark: converged Hamilton-Jacobi solves per second on the 12-D quadcopter
-workload (4096 query points, N = 64, t = 1), FP32 iterations with the stopping
-sums, the value and a per-point residual certificate in FP64, next to the
-all-FP64 GPU path.
+workload (4096 query points, N = 64, t = 1), FP32 iterations (stopping sums
+accumulated over a point's warps as double-floats, value summed in FP64,
+per-point residual certificate), next to the all-FP64 GPU path.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
